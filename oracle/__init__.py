@@ -1,0 +1,310 @@
+"""FP64 CPU oracle for the QED event generator (arXiv:2008.10468).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The CUDA library never calls it and shares no code with it.
+
+What it computes (each function cites the passage it follows):
+
+* ``F1``/``F2``: the synchrotron functions F(x) = x int_x^inf K_{5/3} and
+  G(x) = x K_{2/3}(x) of Sec. 3.2.1, by trapezoidal quadrature of the integral
+  representation of K_nu (C code in ``qed_oracle.c``).
+* ``philox``/``draw``/``child_ids``: Philox4x32-10 (Salmon et al., SC'11) and
+  the per-sub-step draw x, y of Algorithms 1 and 2.
+* ``chi``/``plan``: the quantum parameter of Sec. 2.2 and the sub-step count
+  from the rate bounds of Sec. 3.1.1.
+* ``Pm``/``Pp``: the acceptance functions 3x^2 P(x^3) (Eq. 1, Algorithm 1) and
+  P_p (Eq. 2 with the bracket sign corrected, Algorithm 2).
+* ``total_per_c``: the per-sub-step event probability divided by c
+  (the integral bounded by f(b) in Sec. 3.1.1).
+* ``event_step``: Algorithms 1 and 2 for a particle store over one global step.
+
+Parity is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the oracle shared library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        d, u32, u64, i64, i32 = C.c_double, C.c_uint32, C.c_uint64, C.c_int64, C.c_int
+        P = C.POINTER
+        L.orc_F1.restype = d; L.orc_F1.argtypes = [d]
+        L.orc_F2.restype = d; L.orc_F2.argtypes = [d]
+        L.orc_F1F2.restype = None
+        L.orc_F1F2.argtypes = [i64, P(d), P(d), P(d), i32]
+        L.orc_philox4x32_10.restype = None
+        L.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+        L.orc_uniform.restype = d; L.orc_uniform.argtypes = [u32]
+        L.orc_draw.restype = None
+        L.orc_draw.argtypes = [u64, u64, u32, u32, P(d), P(d)]
+        L.orc_child_ids.restype = None
+        L.orc_child_ids.argtypes = [u64, u64, u32, u32, P(u64)]
+        L.orc_chi.restype = d
+        L.orc_chi.argtypes = [i32] + [d] * 10 + [P(d)]
+        L.orc_bound_emission.restype = d; L.orc_bound_emission.argtypes = [d, d]
+        L.orc_bound_pair.restype = d; L.orc_bound_pair.argtypes = [d, d, d]
+        L.orc_Pm.restype = d; L.orc_Pm.argtypes = [d, d, d]
+        L.orc_Pp.restype = d; L.orc_Pp.argtypes = [d, d, d]
+        L.orc_total_per_c.restype = d; L.orc_total_per_c.argtypes = [i32, d, i32, i32]
+        L.orc_rate_unit.restype = d; L.orc_rate_unit.argtypes = [d]
+        L.orc_schwinger_field.restype = d; L.orc_schwinger_field.argtypes = [d]
+        L.orc_event_step.restype = i32
+        L.orc_event_step.argtypes = [P(Config), P(Particles), u32, P(Stats), P(Log)]
+        L.orc_event_step_mt.restype = i32
+        L.orc_event_step_mt.argtypes = [P(Config), P(Particles), u32, P(Stats)]
+        L.orc_log_free.restype = None; L.orc_log_free.argtypes = [P(Log)]
+        L.orc_plan.restype = u32
+        L.orc_plan.argtypes = [P(Config), i32] + [d] * 10 + [P(d), P(d), P(d)]
+        _lib = L
+    return _lib
+
+
+class Config(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("dt", C.c_double), ("R", C.c_double),
+                ("E_s", C.c_double), ("p_max", C.c_double), ("pair_coeff", C.c_double),
+                ("tie_draw", C.c_double), ("tie_plan", C.c_double),
+                ("process_mask", C.c_uint32), ("cascade", C.c_int32),
+                ("recoil", C.c_int32), ("threads", C.c_int32)]
+
+
+class Particles(C.Structure):
+    _fields_ = [(n, C.POINTER(C.c_float)) for n in
+                ("px", "py", "pz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "w")] + [
+                ("id", C.POINTER(C.c_uint64)), ("type", C.POINTER(C.c_uint8)),
+                ("count", C.c_int64), ("capacity", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("substeps", C.c_uint64), ("emissions", C.c_uint64), ("pairs", C.c_uint64),
+                ("children", C.c_uint64), ("guard_hits", C.c_uint64), ("plans", C.c_uint64),
+                ("max_N", C.c_uint32), ("status", C.c_int32),
+                ("required_capacity", C.c_int64)]
+
+
+class Event(C.Structure):
+    _fields_ = [("parent_id", C.c_uint64), ("child_id", C.c_uint64 * 2), ("s", C.c_uint32),
+                ("kind", C.c_uint32), ("delta", C.c_double), ("chi", C.c_double)]
+
+
+class Tie(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("s", C.c_uint32), ("kind", C.c_uint32)]
+
+
+class Log(C.Structure):
+    _fields_ = [("ev", C.POINTER(Event)), ("n_ev", C.c_int64), ("cap_ev", C.c_int64),
+                ("tie", C.POINTER(Tie)), ("n_tie", C.c_int64), ("cap_tie", C.c_int64)]
+
+
+FIELDS = ("px", "py", "pz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "w")
+
+# Tie bands (the benchmark spec: a draw within 1e-5 of the acceptance probability is
+# exempt from the event-count comparison; the plan band is derived from the
+# binary32 error of the bound f computed by the kernel).
+TIE_DRAW = 1e-5
+TIE_PLAN = 4e-6
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def rate_unit(lambda_m=1e-6):
+    """R = alpha m c^2 / hbar in 1/laser period (the bracket of Eq. 1 is R dt)."""
+    return lib().orc_rate_unit(lambda_m)
+
+
+def schwinger_field(lambda_m=1e-6):
+    """Schwinger field m^2 c^3/(e hbar) in units of m c omega / e."""
+    return lib().orc_schwinger_field(lambda_m)
+
+
+def F1F2(x, threads=None):
+    """F(x) = x int_x^inf K_{5/3} and G(x) = x K_{2/3}(x) (Sec. 3.2.1), FP64."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+    f1 = np.empty_like(x)
+    f2 = np.empty_like(x)
+    if threads is None:
+        threads = min(os.cpu_count() or 1, max(1, x.size // 256))
+    lib().orc_F1F2(x.size, _dp(x), _dp(f1), _dp(f2), int(threads))
+    return f1, f2
+
+
+def F1(x):
+    return F1F2(x)[0]
+
+
+def F2(x):
+    return F1F2(x)[1]
+
+
+def philox(ctr, key):
+    """Philox4x32-10 of one 128-bit counter under one 64-bit key."""
+    c = (C.c_uint32 * 4)(*[int(v) & 0xffffffff for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xffffffff for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def uniform(r):
+    return lib().orc_uniform(int(r) & 0xffffffff)
+
+
+def draw(seed, pid, step, s):
+    """(x, y) of sub-step s of particle pid in global step `step`."""
+    x = C.c_double()
+    y = C.c_double()
+    lib().orc_draw(int(seed), int(pid), int(step), int(s), C.byref(x), C.byref(y))
+    return x.value, y.value
+
+
+def child_ids(seed, pid, step, s):
+    o = (C.c_uint64 * 2)()
+    lib().orc_child_ids(int(seed), int(pid), int(step), int(s), o)
+    return int(o[0]), int(o[1])
+
+
+def chi(p, E, B, photon=False, E_s=None):
+    """chi (Sec. 2.2) and gamma (or |k| for a photon) of one particle."""
+    if E_s is None:
+        E_s = schwinger_field()
+    g = C.c_double()
+    v = lib().orc_chi(int(photon), *[float(a) for a in (*p, *E, *B)], float(E_s), C.byref(g))
+    return v, g.value
+
+
+def bound_emission(b, c):
+    """f(b) of Sec. 3.1.1 for photon emission."""
+    return lib().orc_bound_emission(float(b), float(c))
+
+
+def bound_pair(b, c, coeff=0.1):
+    """f = 0.1 c b of Sec. 3.1.1 for pair production."""
+    return lib().orc_bound_pair(float(b), float(c), float(coeff))
+
+
+def Pm(b, c, x):
+    """3 x^2 P(x^3) of Algorithm 1 (Eq. 1)."""
+    return lib().orc_Pm(float(b), float(c), float(x))
+
+
+def Pp(b, c, delta):
+    """P_p(delta) of Algorithm 2 (Eq. 2, bracket sign corrected)."""
+    return lib().orc_Pp(float(b), float(c), float(delta))
+
+
+def total_per_c(kind, b, panels=64, order=16):
+    """int_0^1 of the acceptance function divided by c: kind 0 emission, 1 pair."""
+    return lib().orc_total_per_c(int(kind), float(b), int(panels), int(order))
+
+
+def make_config(seed, dt=0.1, lambda_m=1e-6, p_max=0.01, pair_coeff=0.1,
+                process_mask=3, cascade=1, recoil=1, threads=1,
+                tie_draw=TIE_DRAW, tie_plan=TIE_PLAN):
+    cf = Config()
+    cf.seed = int(seed)
+    cf.dt = float(dt)
+    cf.R = rate_unit(lambda_m)
+    cf.E_s = schwinger_field(lambda_m)
+    cf.p_max = float(p_max)
+    cf.pair_coeff = float(pair_coeff)
+    cf.tie_draw = float(tie_draw)
+    cf.tie_plan = float(tie_plan)
+    cf.process_mask = int(process_mask)
+    cf.cascade = int(cascade)
+    cf.recoil = int(recoil)
+    cf.threads = int(threads)
+    return cf
+
+
+def plan(cf, p, E, B, t_rem, photon=False):
+    """Sub-step count N of Algorithms 1/2, line 1, with chi, gamma and f."""
+    ch, g, f = C.c_double(), C.c_double(), C.c_double()
+    N = lib().orc_plan(C.byref(cf), int(photon), *[float(a) for a in (*p, *E, *B)],
+                       float(t_rem), C.byref(ch), C.byref(g), C.byref(f))
+    return int(N), ch.value, g.value, f.value
+
+
+def _store(arrs, capacity):
+    """Copy a particle dict into capacity-sized contiguous arrays."""
+    n = int(arrs["px"].shape[0])
+    out = {}
+    for k in FIELDS:
+        a = np.zeros(capacity, dtype=np.float32)
+        a[:n] = arrs[k]
+        out[k] = a
+    out["id"] = np.zeros(capacity, dtype=np.uint64)
+    out["id"][:n] = arrs["id"]
+    out["type"] = np.full(capacity, 3, dtype=np.uint8)
+    out["type"][:n] = arrs["type"]
+    P = Particles()
+    for k in FIELDS:
+        setattr(P, k, out[k].ctypes.data_as(C.POINTER(C.c_float)))
+    P.id = out["id"].ctypes.data_as(C.POINTER(C.c_uint64))
+    P.type = out["type"].ctypes.data_as(C.POINTER(C.c_uint8))
+    P.count = n
+    P.capacity = int(capacity)
+    return out, P
+
+
+def _stats_dict(st):
+    return {k: int(getattr(st, k)) for k, _ in Stats._fields_}
+
+
+def event_step(cf, arrs, step, capacity=None, log=True):
+    """One global step of Algorithms 1 and 2 on a copy of `arrs`.
+
+    Returns (arrays, stats, events, ties): arrays truncated to the final count,
+    stats as a dict, events as a structured array (parent_id, child0, child1,
+    s, kind, delta, chi) and ties as a structured array (id, s, kind).
+    """
+    n = int(arrs["px"].shape[0])
+    if capacity is None:
+        capacity = 4 * n + 1024
+    out, P = _store(arrs, capacity)
+    st = Stats()
+    L = Log()
+    if log:
+        lib().orc_event_step(C.byref(cf), C.byref(P), int(step), C.byref(st), C.byref(L))
+    else:
+        lib().orc_event_step(C.byref(cf), C.byref(P), int(step), C.byref(st), None)
+    cnt = int(P.count)
+    res = {k: v[:cnt].copy() for k, v in out.items()}
+    ev_dt = np.dtype([("parent_id", np.uint64), ("child0", np.uint64), ("child1", np.uint64),
+                      ("s", np.uint32), ("kind", np.uint32), ("delta", np.float64),
+                      ("chi", np.float64)])
+    tie_dt = np.dtype([("id", np.uint64), ("s", np.uint32), ("kind", np.uint32)])
+    ev = np.zeros(int(L.n_ev), dtype=ev_dt)
+    for j in range(int(L.n_ev)):
+        e = L.ev[j]
+        ev[j] = (e.parent_id, e.child_id[0], e.child_id[1], e.s, e.kind, e.delta, e.chi)
+    ties = np.zeros(int(L.n_tie), dtype=tie_dt)
+    for j in range(int(L.n_tie)):
+        t = L.tie[j]
+        ties[j] = (t.id, t.s, t.kind)
+    if log:
+        lib().orc_log_free(C.byref(L))
+    return res, _stats_dict(st), ev, ties
+
+
+def event_step_mt(cf, arrs, step, capacity=None):
+    """Multi-threaded event step (no log); used to time the oracle."""
+    n = int(arrs["px"].shape[0])
+    if capacity is None:
+        capacity = 4 * n + 1024
+    out, P = _store(arrs, capacity)
+    st = Stats()
+    lib().orc_event_step_mt(C.byref(cf), C.byref(P), int(step), C.byref(st))
+    cnt = int(P.count)
+    return {k: v[:cnt].copy() for k, v in out.items()}, _stats_dict(st)
