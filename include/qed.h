@@ -1,0 +1,182 @@
+/*
+ * qed.h - C ABI of the GB300 QED Monte Carlo event generator.
+ *
+ * Implements the per-particle event generator of "Optimized routines for
+ * event generators in QED-PIC codes" (Volokitin et al., arXiv:2008.10468):
+ * hard-photon emission by electrons/positrons (Eq. 1, Algorithm 1) and
+ * photon decay into pairs (Eq. 2, Algorithm 2), with local sub-stepping
+ * planned from the rate bounds of Sec. 3.1.1 and the synchrotron functions
+ * of Sec. 3.2.1.
+ *
+ * Conventions
+ *   - Code units: momentum in m c, fields in m c omega / e (omega = 2 pi c /
+ *     lambda), time in laser periods T = lambda / c.
+ *   - Particle storage is structure-of-arrays in device memory, owned by the
+ *     caller.  Row i of every array describes one macroparticle.  Types:
+ *     0 electron, 1 positron, 2 photon, 3 removed (a photon that decayed).
+ *   - All calls are asynchronous on the context's CUDA stream unless stated.
+ *     Pointers documented as "device" must be device (or managed) memory.
+ *   - Errors are return codes; nothing is thrown across the ABI.  A CUDA
+ *     error is QED_ERR_CUDA and its text is kept for qed_last_error().
+ *     Problems found inside a kernel (capacity exceeded, a bounded wait that
+ *     gave up) are written to a device status word and reported by the next
+ *     call that reads statistics back.
+ *   - A context is not thread safe; use one per host thread.
+ */
+#ifndef QED_H
+#define QED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QED_OK = 0,
+    QED_ERR_ARG = 1,       /* invalid argument (null pointer, bad size, ...)  */
+    QED_ERR_CUDA = 2,      /* a CUDA runtime call failed                       */
+    QED_ERR_CAPACITY = 3,  /* children did not fit; see required_capacity     */
+    QED_ERR_TIMEOUT = 4,   /* a bounded device-side wait gave up              */
+    QED_ERR_STATE = 5      /* call out of order (e.g. launch before capture)  */
+} qed_status;
+
+enum { QED_PROC_EMISSION = 1u, QED_PROC_PAIR = 2u };
+
+enum { QED_ELECTRON = 0, QED_POSITRON = 1, QED_PHOTON = 2, QED_REMOVED = 3 };
+
+/* Run configuration.  qed_config_default() fills the values the paper
+ * recommends (P_max = 0.01, Sec. 3.1.2) and the synthetic workloads use. */
+typedef struct {
+    uint64_t seed;             /* key of the Philox4x32-10 streams              */
+    double dt_periods;         /* global PIC step in laser periods (0.1)        */
+    double lambda_m;           /* laser wavelength in metres (1e-6)             */
+    float p_max;               /* max per-sub-step event probability (0.01)     */
+    float pair_bound_coeff;    /* photon bound f = coeff * c * b (0.1, Sec. 3.1.1) */
+    uint32_t process_mask;     /* QED_PROC_EMISSION | QED_PROC_PAIR             */
+    int32_t cascade_in_step;   /* 1: children are processed in the same step    */
+    int32_t recoil;            /* 1: events change/remove the parent; 0 is a
+                                  validation mode in which they do not          */
+    int32_t max_passes;        /* cascade generations per step (0 -> 64)        */
+} qed_config;
+
+/* Particle store (device pointers, caller-owned). */
+typedef struct {
+    float *px, *py, *pz;       /* momentum (m c); photon: |k| is its energy     */
+    float *Ex, *Ey, *Ez;       /* electric field at the particle                */
+    float *Bx, *By, *Bz;       /* magnetic field at the particle                */
+    float *w;                  /* macroparticle weight                          */
+    uint64_t *id;              /* unique id; children get ids with bit 63 set   */
+    uint8_t *type;             /* 0 e-, 1 e+, 2 photon, 3 removed               */
+    int64_t *count;            /* device int64: rows in use (updated by steps)  */
+    int64_t capacity;          /* rows allocated in every array                 */
+} qed_particles;
+
+/* Statistics of the last step (host struct). */
+typedef struct {
+    uint64_t substeps;         /* sub-steps executed (loop iterations of Alg. 1/2) */
+    uint64_t emissions;        /* photon emission events                        */
+    uint64_t pairs;            /* pair production events                        */
+    uint64_t children;         /* rows appended                                 */
+    uint64_t guard_hits;       /* plans raised by the validity guard            */
+    uint64_t plans;            /* sub-step plans made (1 + one per event)       */
+    uint64_t candidates;       /* sub-steps whose acceptance function was evaluated */
+    uint32_t max_N;            /* largest planned sub-step count                */
+    int32_t status;            /* qed_status of the step                        */
+    int64_t required_capacity; /* rows needed when status == QED_ERR_CAPACITY   */
+    int64_t count;             /* rows in use after the step                    */
+    int32_t passes;            /* cascade generations processed                 */
+    int32_t reserved;
+} qed_step_stats;
+
+/* One event, written to the optional device event log (validation). */
+typedef struct {
+    uint64_t parent_id;
+    uint64_t child_id0;        /* photon (emission) or electron (pair)          */
+    uint64_t child_id1;        /* positron (pair), 0 for emission               */
+    uint32_t s;                /* sub-step index of the event in this step      */
+    uint32_t kind;             /* 1 emission, 2 pair                            */
+    float delta;               /* energy fraction: photon (1) or electron (2)   */
+    float chi;                 /* parent chi at the event                       */
+} qed_event_record;
+
+typedef struct qed_ctx qed_ctx;
+
+/* Fill *cfg with the defaults listed in qed_config.  Never fails. */
+void qed_config_default(qed_config* cfg);
+
+/* Create a context on the current CUDA device.  `stream` is a cudaStream_t
+ * (NULL: the legacy default stream) on which every later call is ordered.
+ * Copies *cfg.  Allocates nothing large; the per-step scratch is sized on
+ * the first qed_event_step.  Errors: QED_ERR_ARG (null out/cfg, p_max not
+ * in (0, 1], dt <= 0, lambda <= 0), QED_ERR_CUDA. */
+qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream);
+
+/* Release the context and its device scratch (synchronises its stream). */
+qed_status qed_destroy(qed_ctx* ctx);
+
+/* Text of the last error of this context (static storage of the context). */
+const char* qed_last_error(const qed_ctx* ctx);
+
+/* Synchrotron functions, Sec. 3.2.1:
+ *   F1[i] = F(y[i]) = y int_y^inf K_{5/3}(t) dt,
+ *   F2[i] = G(y[i]) = y K_{2/3}(y),
+ * in binary32 (relative error <= 4e-6 for y in [1e-4, 50]; 0 for y <= 0 or
+ * y >= 88).  y, F1, F2 are device arrays of n floats; F1 or F2 may be NULL to
+ * skip that output.  Errors: QED_ERR_ARG (null ctx or y, n < 0). */
+qed_status qed_synchrotron_F1F2(qed_ctx* ctx, const float* y, float* F1, float* F2, int64_t n);
+
+/* The same functions on arguments generated in the kernel:
+ *   y_i = lo * (hi/lo)^u_i,  u_i the open-interval uniform of word (i mod 4)
+ *   of Philox4x32-10 at counter (i/4 low, i/4 high, 0, 0), key `seed`.
+ * Moves no argument bytes through memory (the arithmetic-bound mode of the
+ * sweep).  *checksum (device float, may be NULL) receives sum(F1 + F2) by
+ * atomic adds (order-dependent rounding).  y_out/F1_out/F2_out (device,
+ * nullable) store the values for validation.  Errors: QED_ERR_ARG. */
+qed_status qed_synchrotron_generate(qed_ctx* ctx, uint64_t seed, int64_t n, float lo, float hi,
+                                    float* checksum, float* y_out, float* F1_out, float* F2_out);
+
+/* Algorithms 1/2, line 1 only: for rows [0, n) compute chi (Sec. 2.2) and
+ * the sub-step count N of a full global step (bound f(b) of Sec. 3.1.1,
+ * N = max(1, ceil(f / P_max)), validity guard for e+-).  chi and N are
+ * device arrays of n entries (either may be NULL).  Rows that are removed, or
+ * whose process is disabled, get N = 0.  Errors: QED_ERR_ARG. */
+qed_status qed_plan(qed_ctx* ctx, const qed_particles* p, int64_t n, float* chi, uint32_t* N);
+
+/* One global step of the event generator (Algorithms 1 and 2) for every row
+ * in use.  Each particle is planned, stepped through its sub-steps with
+ * Philox4x32-10 draws keyed by (id, step_index, sub-step), emits photons /
+ * decays (photons are marked removed, type 3), recoils, and is re-planned
+ * after every event over the remaining time.  Children are appended at rows
+ * count.. and, if cascade_in_step, processed in the same step.
+ * If out != NULL the call synchronises the stream and fills *out; if NULL it
+ * returns without waiting (statistics readable with qed_read_stats).
+ * Capacity: if the children do not fit, status QED_ERR_CAPACITY is returned
+ * (in *out and as the return value when out != NULL) with the rows needed;
+ * the step is then incomplete (parents that emitted a dropped child have
+ * recoiled) and the caller must restore its own copy of the store.
+ * Errors: QED_ERR_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY, QED_ERR_TIMEOUT. */
+qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                          qed_step_stats* out);
+
+/* Synchronise and read the statistics of the last step.  Errors: ARG, CUDA. */
+qed_status qed_read_stats(qed_ctx* ctx, qed_step_stats* out);
+
+/* Optional event log for validation: subsequent steps append one record per
+ * event to `records` (device array of `capacity` entries) while *count
+ * (device int64, caller-zeroed) counts the events seen; records beyond the
+ * capacity are dropped.  Pass records == NULL to disable.  Errors: ARG. */
+qed_status qed_set_event_log(qed_ctx* ctx, qed_event_record* records, int64_t capacity,
+                             int64_t* count);
+
+/* sizeof of a public struct by name ("qed_config", "qed_particles",
+ * "qed_step_stats", "qed_event_record"), or 0 for an unknown name.  Host
+ * only; lets bindings check their struct mirrors without a GPU. */
+size_t qed_abi_struct_size(const char* name);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QED_H */

@@ -341,7 +341,7 @@ static uint32_t plan_count(const orc_config* cf, int is_photon, double b, double
         double g = ceil(orc_small_F1_coeff() * c * pow(bb, 2.0 / 3.0) * scale_q);
         if (g > N) { N = g; if (guard) *guard = 1; }
     }
-    if (N > 4294967295.0) N = 4294967295.0;
+    if (N > 1073741824.0) N = 1073741824.0;   /* 2^30 */
     return (uint32_t)N;
 }
 

@@ -1,0 +1,247 @@
+"""ctypes binding of the CUDA library ``csrc/libqed.so`` (C ABI in include/qed.h).
+
+Argument marshalling only: every step of the event generator runs in the
+library's kernels.  PyTorch provides device memory and the CUDA stream.  The
+binding raises ``QEDError`` if the library is missing (build it with
+``python -c "import __graft_entry__ as g; g.build()"``); there is no CPU
+fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "csrc", "libqed.so")
+
+QED_OK, QED_ERR_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY, QED_ERR_TIMEOUT, QED_ERR_STATE = range(6)
+PROC_EMISSION, PROC_PAIR = 1, 2
+ELECTRON, POSITRON, PHOTON, REMOVED = 0, 1, 2, 3
+FLOAT_FIELDS = ("px", "py", "pz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "w")
+
+
+class QEDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("qed status %d: %s" % (status, msg))
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("dt_periods", C.c_double), ("lambda_m", C.c_double),
+                ("p_max", C.c_float), ("pair_bound_coeff", C.c_float),
+                ("process_mask", C.c_uint32), ("cascade_in_step", C.c_int32),
+                ("recoil", C.c_int32), ("max_passes", C.c_int32)]
+
+
+class Particles(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in FLOAT_FIELDS] + [
+        ("id", C.c_void_p), ("type", C.c_void_p), ("count", C.c_void_p), ("capacity", C.c_int64)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("substeps", C.c_uint64), ("emissions", C.c_uint64), ("pairs", C.c_uint64),
+                ("children", C.c_uint64), ("guard_hits", C.c_uint64), ("plans", C.c_uint64),
+                ("candidates", C.c_uint64), ("max_N", C.c_uint32), ("status", C.c_int32),
+                ("required_capacity", C.c_int64), ("count", C.c_int64), ("passes", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+EVENT_DTYPE = np.dtype([("parent_id", np.uint64), ("child0", np.uint64), ("child1", np.uint64),
+                        ("s", np.uint32), ("kind", np.uint32), ("delta", np.float32),
+                        ("chi", np.float32)])
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises QEDError if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise QEDError(QED_ERR_STATE, "CUDA library not built: %s is missing" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        vp, i64, u64, st = C.c_void_p, C.c_int64, C.c_uint64, C.c_int
+        L.qed_config_default.argtypes = [C.POINTER(Config)]
+        L.qed_config_default.restype = None
+        L.qed_init.argtypes = [C.POINTER(vp), C.POINTER(Config), vp]
+        L.qed_init.restype = st
+        L.qed_destroy.argtypes = [vp]
+        L.qed_destroy.restype = st
+        L.qed_last_error.argtypes = [vp]
+        L.qed_last_error.restype = C.c_char_p
+        L.qed_synchrotron_F1F2.argtypes = [vp, vp, vp, vp, i64]
+        L.qed_synchrotron_F1F2.restype = st
+        L.qed_synchrotron_generate.argtypes = [vp, u64, i64, C.c_float, C.c_float, vp, vp, vp, vp]
+        L.qed_synchrotron_generate.restype = st
+        L.qed_plan.argtypes = [vp, C.POINTER(Particles), i64, vp, vp]
+        L.qed_plan.restype = st
+        L.qed_event_step.argtypes = [vp, C.POINTER(Particles), u64, C.POINTER(StepStats)]
+        L.qed_event_step.restype = st
+        L.qed_read_stats.argtypes = [vp, C.POINTER(StepStats)]
+        L.qed_read_stats.restype = st
+        L.qed_set_event_log.argtypes = [vp, vp, i64, vp]
+        L.qed_set_event_log.restype = st
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise QEDError(QED_ERR_ARG, "tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise QEDError(QED_ERR_ARG, "tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def stats_dict(s):
+    return {k: int(getattr(s, k)) for k, _ in StepStats._fields_ if k != "reserved"}
+
+
+class ParticleStore:
+    """Caller-owned SoA particle arrays on the GPU (see qed_particles)."""
+
+    def __init__(self, capacity, device="cuda"):
+        self.capacity = int(capacity)
+        self.device = torch.device(device)
+        f = dict(dtype=torch.float32, device=self.device)
+        for k in FLOAT_FIELDS:
+            setattr(self, k, torch.zeros(self.capacity, **f))
+        self.id = torch.zeros(self.capacity, dtype=torch.int64, device=self.device)
+        self.type = torch.full((self.capacity,), REMOVED, dtype=torch.uint8, device=self.device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=self.device)
+
+    @classmethod
+    def from_numpy(cls, arrs, capacity=None, device="cuda"):
+        n = int(arrs["px"].shape[0])
+        s = cls(capacity if capacity is not None else max(n, 1), device)
+        s.load(arrs)
+        return s
+
+    def load(self, arrs):
+        n = int(arrs["px"].shape[0])
+        if n > self.capacity:
+            raise QEDError(QED_ERR_ARG, "more rows than capacity")
+        for k in FLOAT_FIELDS:
+            getattr(self, k)[:n].copy_(torch.from_numpy(np.ascontiguousarray(arrs[k], np.float32)))
+        self.id[:n].copy_(torch.from_numpy(np.ascontiguousarray(arrs["id"]).view(np.int64)))
+        self.type[:n].copy_(torch.from_numpy(np.ascontiguousarray(arrs["type"], np.uint8)))
+        self.type[n:].fill_(REMOVED)
+        self.count.fill_(n)
+
+    def n(self):
+        return int(self.count.item())
+
+    def to_numpy(self):
+        n = self.n()
+        out = {k: getattr(self, k)[:n].cpu().numpy() for k in FLOAT_FIELDS}
+        out["id"] = self.id[:n].cpu().numpy().view(np.uint64)
+        out["type"] = self.type[:n].cpu().numpy()
+        return out
+
+    def struct(self):
+        p = Particles()
+        for k in FLOAT_FIELDS:
+            setattr(p, k, _ptr(getattr(self, k)))
+        p.id = _ptr(self.id)
+        p.type = _ptr(self.type)
+        p.count = _ptr(self.count)
+        p.capacity = self.capacity
+        return p
+
+
+class Context:
+    """A library context bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, seed=20081046, dt=0.1, lambda_m=1e-6, p_max=0.01, pair_coeff=0.1,
+                 process_mask=PROC_EMISSION | PROC_PAIR, cascade=True, recoil=True,
+                 max_passes=64, stream=None):
+        L = lib()
+        cfg = Config()
+        L.qed_config_default(C.byref(cfg))
+        cfg.seed = int(seed)
+        cfg.dt_periods = float(dt)
+        cfg.lambda_m = float(lambda_m)
+        cfg.p_max = float(p_max)
+        cfg.pair_bound_coeff = float(pair_coeff)
+        cfg.process_mask = int(process_mask)
+        cfg.cascade_in_step = int(bool(cascade))
+        cfg.recoil = int(bool(recoil))
+        cfg.max_passes = int(max_passes)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self._h = C.c_void_p()
+        st = L.qed_init(C.byref(self._h), C.byref(cfg), C.c_void_p(stream.cuda_stream))
+        if st != QED_OK:
+            raise QEDError(st, "qed_init failed")
+        self._log = None
+
+    def _check(self, st):
+        if st != QED_OK:
+            raise QEDError(st, lib().qed_last_error(self._h).decode(errors="replace"))
+
+    def close(self):
+        if self._h:
+            lib().qed_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchrotron_F1F2(self, y, F1=None, F2=None):
+        n = int(y.numel())
+        self._check(lib().qed_synchrotron_F1F2(self._h, _ptr(y), _ptr(F1), _ptr(F2), n))
+        return F1, F2
+
+    def synchrotron_generate(self, seed, n, lo=1e-4, hi=50.0, checksum=None, y=None, F1=None,
+                             F2=None):
+        self._check(lib().qed_synchrotron_generate(self._h, int(seed), int(n), float(lo),
+                                                   float(hi), _ptr(checksum), _ptr(y), _ptr(F1),
+                                                   _ptr(F2)))
+
+    def plan(self, store, n, chi=None, N=None):
+        p = store.struct()
+        self._check(lib().qed_plan(self._h, C.byref(p), int(n), _ptr(chi), _ptr(N)))
+
+    def set_event_log(self, capacity):
+        """Record events of later steps into a device log of `capacity` records."""
+        if capacity <= 0:
+            self._check(lib().qed_set_event_log(self._h, None, 0, None))
+            self._log = None
+            return
+        buf = torch.zeros(int(capacity) * EVENT_DTYPE.itemsize, dtype=torch.uint8,
+                          device=torch.device("cuda"))
+        cnt = torch.zeros(1, dtype=torch.int64, device=buf.device)
+        self._check(lib().qed_set_event_log(self._h, _ptr(buf), int(capacity), _ptr(cnt)))
+        self._log = (buf, cnt, int(capacity))
+
+    def read_event_log(self):
+        buf, cnt, cap = self._log
+        n = min(int(cnt.item()), cap)
+        raw = buf[:n * EVENT_DTYPE.itemsize].cpu().numpy()
+        return raw.view(EVENT_DTYPE).copy(), int(cnt.item())
+
+    def event_step(self, store, step, sync=True):
+        """One global step; returns the statistics dict (sync=True) or None."""
+        p = store.struct()
+        if sync:
+            s = StepStats()
+            st = lib().qed_event_step(self._h, C.byref(p), int(step), C.byref(s))
+            if st not in (QED_OK, QED_ERR_CAPACITY):
+                self._check(st)
+            return stats_dict(s)
+        self._check(lib().qed_event_step(self._h, C.byref(p), int(step), None))
+        return None
+
+    def read_stats(self):
+        s = StepStats()
+        st = lib().qed_read_stats(self._h, C.byref(s))
+        if st not in (QED_OK, QED_ERR_CAPACITY):
+            self._check(st)
+        return stats_dict(s)
