@@ -1,0 +1,460 @@
+#!/usr/bin/env python3
+"""Benchmark of the QED event generator (arXiv:2008.10468) on GB300.
+
+Headline: sub-stepped particle-steps per second (executed sub-steps of
+Algorithms 1/2 per second) for one global step of the clumped mixed population:
+2^24 particles (25% e-, 25% e+, 50% photons), 1% of them in a contiguous hot
+clump with chi log-uniform in [10, 100], the rest chi in [1e-3, 1e-2];
+emission + pair production with the in-step cascade.  Every timed step starts
+from the same population (restored, then L2 flushed, outside the timed window)
+with a new step index, i.e. new random draws.
+
+Also reported: F1/F2 evaluations per second on 2^28 log-uniform arguments in
+[1e-4, 50] (array mode, 12 bytes per evaluation, and in-kernel generation
+mode), per-kernel times from CUDA events on the library stream, the roofline of
+the dominant kernel, the end-to-end rate through host buffers, SM clocks during
+the timed region, and the FP64 oracle on the host cores (a bounded sample).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_PARTICLES = 1 << 24
+SWEEP_N = 1 << 28
+SEED_CLUMPED = 20081046 + 3
+SEED_SWEEP = 20081046 + 2
+METRIC = "particle-steps/sec (sub-stepped)"
+UNIT = "substeps/s"
+WORKLOAD = ("clumped mixed population 2^24 (25% e-, 25% e+, 50% photons; 1% hot clump "
+            "chi 10-100), emission + pairs + in-step cascade, one global step dt = 0.1 T")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() in ("active", "yes", "0x1", "1"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# distributed helpers (one process per GPU; the path shards by particles)
+# --------------------------------------------------------------------------
+def dist_init(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def allreduce_max(pg, v):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(pg, v):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores, bounded sample
+# --------------------------------------------------------------------------
+def population_sample(arr, m, seed):
+    """m rows of the population with the same hot fraction (stratified)."""
+    n = len(arr["px"])
+    n_hot = int(round(n * 0.01))
+    h0 = (n - n_hot) // 2
+    rng = np.random.default_rng(seed)
+    k_hot = max(1, int(round(m * 0.01)))
+    hot = rng.choice(np.arange(h0, h0 + n_hot), k_hot, replace=False)
+    cold_pool = rng.choice(n - n_hot, m - k_hot, replace=False)
+    cold = np.where(cold_pool < h0, cold_pool, cold_pool + n_hot)
+    # random order: the oracle's threads take contiguous ranges, and a sorted
+    # sample would put the whole clump on one thread
+    rows = rng.permutation(np.concatenate([hot, cold]))
+    from paper_2008_10468_gb300 import inputs as I
+    return I.subset(arr, rows)
+
+
+def cpu_baseline(arr, seed, budget_s=15.0):
+    import oracle as O
+    cores = os.cpu_count() or 1
+    cf = O.make_config(seed, process_mask=3, cascade=1, threads=cores)
+    m = 2000
+    while True:
+        sub = population_sample(arr, m, 11)
+        t0 = time.perf_counter()
+        _, st = O.event_step_mt(cf, sub, 100, capacity=m * 64)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or m >= 1 << 20:
+            break
+        m = min(1 << 20, int(m * max(2.0, budget_s / 2 / max(dt, 1e-3))))
+    return {"value": st["substeps"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d rows of the same population (1%% hot, stratified), one step, "
+                      "%d sub-steps in %.1f s" % (m, st["substeps"], dt)}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_gb300(args):
+    import torch
+    from paper_2008_10468_gb300 import inputs as I
+    from paper_2008_10468_gb300 import qed
+
+    rank, world, local, pg = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbm_peak, peak_kind = peaks()
+
+    n = args.particles
+    arr = I.clumped_mixed(n, SEED_CLUMPED + 1000 * rank)
+    cap = n + 2 * n       # the hot clump cascades: ~35 children per hot particle
+    pristine = qed.ParticleStore.from_numpy(arr, capacity=cap, device=dev)
+    store = qed.ParticleStore(cap, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > L2
+    ctx = qed.Context(seed=SEED_CLUMPED + rank, process_mask=3, cascade=True)
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        for k in qed.FLOAT_FIELDS + ("id", "type"):
+            getattr(store, k)[:n].copy_(getattr(pristine, k)[:n])
+        store.type[n:].fill_(qed.REMOVED)
+        store.count.fill_(n)
+        flush.fill_(1)
+
+    for w in range(args.warmup):
+        restore()
+        ctx.event_step(store, 1000 + w)
+    torch.cuda.synchronize()
+    ctx.profile_read()
+    ctx.profile(True)
+
+    clocks = Clocks(local)
+    clocks.start()
+    total_ms = 0.0
+    sub_total = 0
+    agg = {"emissions": 0, "pairs": 0, "children": 0, "candidates": 0, "plans": 0,
+           "passes": 0, "max_N": 0, "substeps_warp": 0}
+    kern = {}
+    for k in range(args.steps):
+        restore()
+        torch.cuda.synchronize()
+        barrier(pg)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ctx.event_step(store, 2000 + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg)
+        total_ms += e0.elapsed_time(e1)
+        sub_total += st["substeps"]
+        for key in agg:
+            agg[key] = max(agg[key], st[key]) if key == "max_N" else agg[key] + st[key]
+        if st["status"] != 0:
+            raise SystemExit("step failed with status %d" % st["status"])
+        for name, (ms, nl) in ctx.profile_read().items():
+            a = kern.setdefault(name, [0.0, 0])
+            a[0] += ms
+            a[1] += nl
+    clk = clocks.stop()
+    ctx.profile(False)
+
+    t_max = allreduce_max(pg, total_ms)
+    subs = allreduce_sum(pg, sub_total)
+    value = subs / (t_max / 1e3)
+
+    # dominant kernel and its roofline (event-timed on the library stream)
+    dom = max(("cold", "hot"), key=lambda k: kern.get(k, [0])[0])
+    launches_timed = sum(v[1] for v in kern.values())
+    steps = args.steps
+    if dom == "cold":
+        # algorithmic bytes of the thread-per-particle pass per step: read type of
+        # every row (1 B) and p, E, B, id of every active row (44 B); write child
+        # rows with their remaining time (57 B) and changed momenta (12 B)
+        rows = n + agg["children"] / steps
+        bytes_step = 45.0 * rows + 57.0 * agg["children"] / steps + 12.0 * agg["emissions"] / steps
+        t_launch = kern["cold"][0] / kern["cold"][1]
+        per_launch = bytes_step / (kern["cold"][1] / steps)
+        achieved = per_launch / (t_launch / 1e3) / 1e9
+        roof = {"kernel": "k_cold", "bound": "hbm", "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_kind": peak_kind}
+    else:
+        # warp-per-particle pass: its work is Philox4x32-10, 4 32-bit multiply
+        # results per round, 40 per block, one block per two sub-steps -> 20
+        # multiplies per sub-step.  Peak: 152 SMs x 64 integer multiplies per
+        # clock per SM x the maximum SM clock.
+        sm_mhz = 2070.0
+        mul_peak = 152 * 64 * sm_mhz * 1e6 / 1e12
+        t_launch = kern["hot"][0] / kern["hot"][1] / 1e3
+        per_launch = 20.0 * agg["substeps_warp"] / kern["hot"][1]
+        achieved = per_launch / t_launch / 1e12
+        roof = {"kernel": "k_hot", "bound": "alu", "achieved": achieved, "peak": mul_peak,
+                "unit": "T int32-mul/s", "frac": achieved / mul_peak, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz"}
+
+    # synchrotron sweep, array mode and generation mode
+    sweep = run_sweep(ctx, dev, args, hbm_peak, peak_kind)
+
+    # end to end from pinned host buffers through the public API
+    e2e = None if args.no_e2e else run_e2e(ctx, arr, cap, dev, args)
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if n == N_PARTICLES else WORKLOAD + " (reduced: %d rows)" % n,
+                   "particles": n, "capacity": cap,
+                   "l2": "inputs (822 MB) larger than L2, and a 256 MB buffer written before "
+                         "each timed step", "parallelism": "independent particle shards"
+                                                       if world > 1 else "single GPU"},
+        "per_step": {k: v / steps for k, v in agg.items() if k != "max_N"},
+        "max_N": agg["max_N"],
+        "kernels_ms_per_step": {k: v[0] / steps for k, v in kern.items() if v[1]},
+        "roofline": roof,
+        "sweep": sweep,
+        "e2e": e2e,
+        "gpu_launches": launches_timed,
+        "clocks": clk,
+    }
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            res["cpu_baseline"] = cpu_baseline(arr, SEED_CLUMPED)
+        print(json.dumps(res))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def run_sweep(ctx, dev, args, hbm_peak, peak_kind):
+    import torch
+    from paper_2008_10468_gb300 import inputs as I
+    SWEEP_N = args.sweep_n
+    y = torch.from_numpy(I.sweep_points(SWEEP_N, SEED_SWEEP)).to(dev)
+    F1 = torch.empty_like(y)
+    F2 = torch.empty_like(y)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        ctx.synchrotron_F1F2(y, F1, F2)
+    torch.cuda.synchronize()
+    reps = max(3, args.steps)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.synchrotron_F1F2(y, F1, F2)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    evals = SWEEP_N / (ms / 1e3)
+    gbs = 12.0 * SWEEP_N / (ms / 1e3) / 1e9
+    # generation mode: no argument or result traffic
+    chk = torch.zeros(1, device=dev)
+    for _ in range(2):
+        ctx.synchrotron_generate(7, SWEEP_N, 1e-4, 50.0, chk)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.synchrotron_generate(7, SWEEP_N, 1e-4, 50.0, chk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_gen = e0.elapsed_time(e1) / reps
+    del y, F1, F2
+    return {"n": SWEEP_N, "evals_per_s": evals, "ms": ms,
+            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "peak_kind": peak_kind, "bytes_per_eval": 12},
+            "generate_evals_per_s": SWEEP_N / (ms_gen / 1e3), "generate_ms": ms_gen}
+
+
+def run_e2e(ctx, arr, cap, dev, args):
+    """Same metric through the API with host buffers: per step copy the
+    population from pinned host memory, step, copy every row back."""
+    import torch
+    from paper_2008_10468_gb300 import qed
+    n = len(arr["px"])
+    host = {}
+    for k in qed.FLOAT_FIELDS:
+        host[k] = torch.from_numpy(arr[k]).pin_memory()
+    host["id"] = torch.from_numpy(arr["id"].view(np.int64)).pin_memory()
+    host["type"] = torch.from_numpy(arr["type"]).pin_memory()
+    out = {k: torch.empty(cap, dtype=v.dtype).pin_memory() for k, v in host.items()}
+    store = qed.ParticleStore(cap, device=dev)
+    stream = torch.cuda.current_stream()
+    steps = max(2, min(args.steps, 5))
+    total = 0.0
+    subs = 0
+    h2d = d2h = 0
+    for k in range(steps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b_in = 0
+        for key, t in host.items():
+            getattr(store, key)[:n].copy_(t, non_blocking=True)
+            b_in += t.numel() * t.element_size()
+        store.type[n:].fill_(qed.REMOVED)
+        store.count.fill_(n)
+        st = ctx.event_step(store, 3000 + k)
+        m = st["count"]
+        b_out = 0
+        for key in host:
+            src = getattr(store, key)[:m]
+            out[key][:m].copy_(src, non_blocking=True)
+            b_out += src.numel() * src.element_size()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k == 0:
+            continue  # first one warms the pinned paths
+        total += e0.elapsed_time(e1)
+        subs += st["substeps"]
+        h2d += b_in
+        d2h += b_out
+    return {"value": subs / (total / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 oracle, as it stands, on the host cores
+# --------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2008_10468_gb300 import inputs as I
+    arr = I.clumped_mixed(N_PARTICLES, SEED_CLUMPED)
+    cores = os.cpu_count() or 1
+    cf = O.make_config(SEED_CLUMPED, process_mask=3, cascade=1, threads=cores)
+    m = int(os.environ.get("QED_REFERENCE_SAMPLE", "20000"))
+    sub = population_sample(arr, m, 11)
+    for w in range(args.warmup):
+        O.event_step_mt(cf, sub, 1000 + w, capacity=m * 64)
+    t = 0.0
+    subs = 0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        _, st = O.event_step_mt(cf, sub, 2000 + k, capacity=m * 64)
+        t += time.perf_counter() - t0
+        subs += st["substeps"]
+    value = subs / t
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": N_PARTICLES},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d rows of the population (1%% hot, stratified) per step" % m},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--particles", type=int, default=N_PARTICLES,
+                    help="population size (smaller values only for profiling runs)")
+    ap.add_argument("--sweep-n", type=int, default=SWEEP_N,
+                    help="synchrotron sweep length (smaller values only for profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

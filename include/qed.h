@@ -59,7 +59,15 @@ typedef struct {
     int32_t recoil;            /* 1: events change/remove the parent; 0 is a
                                   validation mode in which they do not          */
     int32_t max_passes;        /* cascade generations per step (0 -> 64)        */
+    float drain_chi;           /* compaction drains photons with chi below this
+                                  into the photon spectrum (0: never)           */
 } qed_config;
+
+/* Photon spectrum filled by the drain: weight per bin of log10(photon
+ * energy / m c^2), QED_SPECTRUM_BINS equal bins over [MIN, MAX). */
+#define QED_SPECTRUM_BINS 240
+#define QED_SPECTRUM_LOG10_MIN (-4)
+#define QED_SPECTRUM_LOG10_MAX 8
 
 /* Particle store (device pointers, caller-owned). */
 typedef struct {
@@ -88,6 +96,7 @@ typedef struct {
     int64_t count;             /* rows in use after the step                    */
     int32_t passes;            /* cascade generations processed                 */
     int32_t reserved;
+    uint64_t substeps_warp;    /* of `substeps`, those run on the warp-per-particle path */
 } qed_step_stats;
 
 /* One event, written to the optional device event log (validation). */
@@ -124,7 +133,8 @@ const char* qed_last_error(const qed_ctx* ctx);
  *   F2[i] = G(y[i]) = y K_{2/3}(y),
  * in binary32 (relative error <= 4e-6 for y in [1e-4, 50]; 0 for y <= 0 or
  * y >= 88).  y, F1, F2 are device arrays of n floats; F1 or F2 may be NULL to
- * skip that output.  Errors: QED_ERR_ARG (null ctx or y, n < 0). */
+ * skip that output; n == 0 is a no-op whatever the pointers.  Errors:
+ * QED_ERR_ARG (null ctx, null y with n > 0, n < 0). */
 qed_status qed_synchrotron_F1F2(qed_ctx* ctx, const float* y, float* F1, float* F2, int64_t n);
 
 /* The same functions on arguments generated in the kernel:
@@ -169,6 +179,65 @@ qed_status qed_read_stats(qed_ctx* ctx, qed_step_stats* out);
  * capacity are dropped.  Pass records == NULL to disable.  Errors: ARG. */
 qed_status qed_set_event_log(qed_ctx* ctx, qed_event_record* records, int64_t capacity,
                              int64_t* count);
+
+/* Remove the rows of removed particles (type 3) from the store, keeping the
+ * order of the others, and set *count to the rows kept.  If cfg.drain_chi > 0,
+ * photons with chi below it are first added (by weight) to the context's
+ * photon spectrum and removed: the paper's method never needs them again,
+ * since their pair probability is negligible.  Not part of the paper's
+ * algorithm; a store-management step of this library.  *removed (host,
+ * nullable) receives the rows removed (the call then synchronises).
+ * Device scratch of 49 bytes per row of capacity is allocated on first use.
+ * Errors: QED_ERR_ARG, QED_ERR_CUDA. */
+qed_status qed_compact(qed_ctx* ctx, const qed_particles* p, int64_t* removed);
+
+/* Copy the drained-photon spectrum (QED_SPECTRUM_BINS doubles) to `out`
+ * (host) and, if reset, zero it.  Synchronises.  Errors: QED_ERR_ARG. */
+qed_status qed_read_spectrum(qed_ctx* ctx, double* out, int nbins, int reset);
+
+/* Record `nsteps` consecutive global steps (step indices first_step ..
+ * first_step + nsteps - 1) on store `p` as one CUDA graph: per step, the
+ * cascade generations run in a device-side loop (a conditional WHILE node
+ * whose condition the last kernel of each generation sets), then the store is
+ * compacted (qed_compact), then the step's statistics are recorded on the
+ * device.  No host synchronisation inside.  A step that fails (capacity,
+ * cascade deeper than max_passes) makes the following steps no-ops; its
+ * record carries the status.  Replaces any earlier graph of the context.
+ * Errors: QED_ERR_ARG, QED_ERR_CUDA. */
+qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t first_step,
+                             int nsteps);
+
+/* Launch the captured graph on the context stream (asynchronous).
+ * Errors: QED_ERR_STATE (nothing captured), QED_ERR_CUDA. */
+qed_status qed_graph_launch(qed_ctx* ctx);
+
+/* Synchronise and copy the per-step statistics of the last graph launch
+ * (nsteps <= captured steps) to out[0..nsteps).  Returns the first non-zero
+ * step status, else QED_OK.  Errors: QED_ERR_ARG, QED_ERR_STATE, CUDA. */
+qed_status qed_graph_read_stats(qed_ctx* ctx, qed_step_stats* out, int nsteps);
+
+/* Kernel kinds for qed_profile_read. */
+enum {
+    QED_KERNEL_SWEEP = 0,      /* synchrotron functions over an array          */
+    QED_KERNEL_GENERATE = 1,   /* synchrotron functions, in-kernel arguments   */
+    QED_KERNEL_PLAN = 2,       /* planner                                      */
+    QED_KERNEL_COLD = 3,       /* event step: thread-per-particle pass         */
+    QED_KERNEL_HOT = 4,        /* event step: warp-per-particle queue pass     */
+    QED_KERNEL_CONTROL = 5,    /* event step: per-step and per-pass bookkeeping */
+    QED_KERNEL_KINDS = 8
+};
+
+/* Benchmark timing.  While enabled, every kernel this context launches is
+ * bracketed by CUDA events recorded on the context stream (this adds a few
+ * microseconds per launch).  Launch counts are kept whether or not timing is
+ * enabled.  Errors: QED_ERR_ARG, QED_ERR_CUDA. */
+qed_status qed_profile_enable(qed_ctx* ctx, int enable);
+
+/* Synchronise the stream, write the milliseconds measured and the kernels
+ * launched per kind since the last read into ms[0..n) and launches[0..n)
+ * (host arrays, either may be NULL; n <= QED_KERNEL_KINDS), then reset both
+ * accumulators.  Errors: QED_ERR_ARG, QED_ERR_CUDA. */
+qed_status qed_profile_read(qed_ctx* ctx, double* ms, int64_t* launches, int n);
 
 /* sizeof of a public struct by name ("qed_config", "qed_particles",
  * "qed_step_stats", "qed_event_record"), or 0 for an unknown name.  Host

@@ -22,6 +22,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "qed.h"
 #include "qed_device.cuh"
@@ -36,25 +37,38 @@ constexpr double kCLight = 299792458.0;             // m / s
 constexpr double kPiD = 3.14159265358979323846;
 
 constexpr uint32_t kHotMin = 64;       // plans with N >= kHotMin go to the warp path
+
+// Minimum resident blocks per SM requested from the register allocator.
+#ifndef QED_COLD_MIN_BLOCKS
+#define QED_COLD_MIN_BLOCKS 1
+#endif
+#ifndef QED_HOT_MIN_BLOCKS
+#define QED_HOT_MIN_BLOCKS 1
+#endif
 constexpr int kColdThreads = 256;
 constexpr int kHotThreads = 128;
 constexpr int kSweepThreads = 256;
 
 struct DevCtl {
     unsigned long long substeps, emissions, pairs, children, guard_hits, plans, candidates;
+    unsigned long long substeps_warp;
     unsigned int max_N;
     int status;
     long long required;
     long long pass_begin, pass_end;
     unsigned int hot_tail, hot_head;
     int more, passes;
-    long long log_count_unused;
+    int first_pass;      // 1 until the first generation of the step is done
+    int sticky;          // first error of a multi-step graph run: later steps do nothing
+    long long live;      // rows kept by the last compaction
+    int compact_needed;  // the last compaction found removed rows
+    int pad_;
 };
 
 struct HotItem {
     uint32_t idx;
     uint32_t s;
-    double t_rem;
+    ticks_t t_rem;   // remaining time in ticks (2^62 per global step)
 };
 
 struct DevParticles {
@@ -66,7 +80,7 @@ struct DevParticles {
 };
 
 struct Scratch {
-    double* t_rem;          // remaining time of appended children (capacity)
+    ticks_t* t_rem;         // remaining time (ticks) of appended children (capacity)
     HotItem* hot;           // queue of warp-path particles (capacity)
     qed_event_record* log;  // optional
     long long log_cap;
@@ -75,7 +89,7 @@ struct Scratch {
 
 struct Stats {
     unsigned long long substeps = 0, emissions = 0, pairs = 0, children = 0, guard = 0, plans = 0,
-                       cand = 0;
+                       cand = 0, warp_substeps = 0;
     unsigned int max_N = 0;
 };
 
@@ -93,7 +107,8 @@ __device__ __forceinline__ unsigned int warp_max(unsigned int v) {
 __device__ void flush_stats(const Stats& st, DevCtl* ctl) {
     const unsigned long long a = warp_sum(st.substeps), b = warp_sum(st.emissions),
                              c = warp_sum(st.pairs), d = warp_sum(st.children),
-                             e = warp_sum(st.guard), f = warp_sum(st.plans), g = warp_sum(st.cand);
+                             e = warp_sum(st.guard), f = warp_sum(st.plans), g = warp_sum(st.cand),
+                             h = warp_sum(st.warp_substeps);
     const unsigned int m = warp_max(st.max_N);
     if ((threadIdx.x & 31) == 0) {
         if (a) atomicAdd(&ctl->substeps, a);
@@ -103,12 +118,13 @@ __device__ void flush_stats(const Stats& st, DevCtl* ctl) {
         if (e) atomicAdd(&ctl->guard_hits, e);
         if (f) atomicAdd(&ctl->plans, f);
         if (g) atomicAdd(&ctl->candidates, g);
+        if (h) atomicAdd(&ctl->substeps_warp, h);
         if (m) atomicMax(&ctl->max_N, m);
     }
 }
 
 struct SharedTables {
-    float4 syn[kSynRows];
+    SynTable syn;
     float sqz_e[QED_SQZ_E_JMAX - QED_SQZ_E_JMIN];
     float sqz_p[QED_SQZ_P_JMAX - QED_SQZ_P_JMIN];
 };
@@ -129,7 +145,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep(const float* __restrict
                                                          float* __restrict__ F1,
                                                          float* __restrict__ F2, long long n,
                                                          int vec) {
-    __shared__ float4 tbl[kSynRows];
+    __shared__ SynTable tbl;
     stage_syn_table(tbl);
     __syncthreads();
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -162,7 +178,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_generate(uint32_t k0, uint32_
                                                             float lo, float log2_ratio,
                                                             float* checksum, float* y_out,
                                                             float* F1_out, float* F2_out) {
-    __shared__ float4 tbl[kSynRows];
+    __shared__ SynTable tbl;
     stage_syn_table(tbl);
     __syncthreads();
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -208,12 +224,10 @@ __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParam
                             (photon ? (SP.process_mask & QED_PROC_PAIR)
                                     : (SP.process_mask & QED_PROC_EMISSION));
         float eps;
-        chi = chi_ff(photon, P.px[i], P.py[i], P.pz[i], P.Ex[i], P.Ey[i], P.Ez[i], P.Bx[i],
-                     P.By[i], P.Bz[i], SP.inv_Es, &eps);
-        if (active && eps > 0.0f) {
-            const Plan pl = make_plan(SP, sm.sqz_e, sm.sqz_p, photon, chi, eps, SP.dt);
-            N = pl.N;
-        }
+        const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, P.px[i], P.py[i], P.pz[i],
+                                      P.Ex[i], P.Ey[i], P.Ez[i], P.Bx[i], P.By[i], P.Bz[i],
+                                      kTicksPerStep, &chi, &eps);
+        if (active && eps > 0.0f) N = pl.N;
         if (chi_out) chi_out[i] = chi;
         if (N_out) N_out[i] = N;
     }
@@ -226,11 +240,34 @@ struct PState {
     float px, py, pz;
 };
 
-// Reserve rows for children; on overflow mark the reserved rows removed and
-// record the capacity error.
-__device__ __forceinline__ long long reserve_rows(const DevParticles& P, DevCtl* ctl, int n) {
-    const long long slot =
-        (long long)atomicAdd(reinterpret_cast<unsigned long long*>(P.count), (unsigned long long)n);
+// Reserve n rows for children.  `aggregate`: the lanes of the warp that reach
+// this call together share one atomic (ballots of the active lanes give each
+// lane its offset, the first lane adds the total, the base is broadcast).  On overflow
+// the reserved rows are marked removed and the capacity error is recorded.
+__device__ __forceinline__ long long reserve_rows(const DevParticles& P, DevCtl* ctl, int n,
+                                                  bool aggregate) {
+    long long slot;
+    if (aggregate) {
+        // n is 1 (photon) or 2 (pair): the prefix over the active lanes is
+        // exact from two ballots, whatever lanes are active
+        const unsigned int act = __activemask();
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(act) - 1;
+        const unsigned int m1 = __ballot_sync(act, n == 1);
+        const unsigned int m2 = __ballot_sync(act, n == 2);
+        const unsigned int below = (1u << lane) - 1u;
+        const int offset = __popc(m1 & below) + 2 * __popc(m2 & below);
+        const int total = __popc(m1) + 2 * __popc(m2);
+        unsigned long long base = 0;
+        if (lane == leader)
+            base = atomicAdd(reinterpret_cast<unsigned long long*>(P.count),
+                             (unsigned long long)total);
+        base = __shfl_sync(act, base, leader);
+        slot = (long long)base + offset;
+    } else {
+        slot = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(P.count),
+                                    (unsigned long long)n);
+    }
     if (slot + n > P.capacity) {
         for (long long j = slot; j < slot + n && j < P.capacity; ++j) {
             P.type[j] = QED_REMOVED;
@@ -245,7 +282,7 @@ __device__ __forceinline__ long long reserve_rows(const DevParticles& P, DevCtl*
 
 __device__ __forceinline__ void write_child(const DevParticles& P, const Scratch& S, long long j,
                                             long long parent, float px, float py, float pz,
-                                            uint64_t id, uint8_t type, double t_rem) {
+                                            uint64_t id, uint8_t type, ticks_t t_rem) {
     P.px[j] = px;
     P.py[j] = py;
     P.pz[j] = pz;
@@ -265,19 +302,21 @@ __device__ __forceinline__ void write_child(const DevParticles& P, const Scratch
 // the particle was removed (photon decay).
 __device__ bool apply_event(const DevParticles& P, const Scratch& S, const StepParams& SP,
                             DevCtl* ctl, long long i, uint64_t id, bool photon, float x,
-                            float eps, float chi, uint32_t s, double t_after, PState& st,
-                            Stats& stats, bool write_rows) {
+                            float eps, float chi, uint32_t s, ticks_t t_after, PState& st,
+                            Stats& stats, bool write_rows, bool warp_caller) {
     const uint4 cid = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), SP.step, s),
                                     (uint32_t)SP.seed ^ kChildKeyLo,
                                     (uint32_t)(SP.seed >> 32) ^ kChildKeyHi);
     const uint64_t id0 = ((uint64_t)cid.x | ((uint64_t)cid.y << 32)) | (1ull << 63);
     const uint64_t id1 = ((uint64_t)cid.z | ((uint64_t)cid.w << 32)) | (1ull << 63);
+    // thread-per-particle callers aggregate their reservations per warp
+    const bool aggregate = write_rows && !warp_caller;
     float delta;
     bool removed = false;
     if (!photon) {
         delta = x * x * x;
         if (write_rows) {
-            const long long j = reserve_rows(P, ctl, 1);
+            const long long j = reserve_rows(P, ctl, 1, aggregate);
             if (j >= 0)
                 write_child(P, S, j, i, delta * st.px, delta * st.py, delta * st.pz, id0,
                             QED_PHOTON, t_after);
@@ -304,7 +343,7 @@ __device__ bool apply_event(const DevParticles& P, const Scratch& S, const StepP
     } else {
         delta = x;
         if (write_rows) {
-            const long long j = reserve_rows(P, ctl, 2);
+            const long long j = reserve_rows(P, ctl, 2, aggregate);
             if (j >= 0) {
                 const float omd = 1.0f - x;
                 write_child(P, S, j, i, x * st.px, x * st.py, x * st.pz, id0, QED_ELECTRON,
@@ -340,7 +379,7 @@ __device__ __forceinline__ bool process_enabled(const StepParams& SP, bool photo
 }
 
 __device__ __forceinline__ void push_hot(const Scratch& S, DevCtl* ctl, long long i, uint32_t s,
-                                         double t_rem) {
+                                         ticks_t t_rem) {
     const unsigned int k = atomicAdd(&ctl->hot_tail, 1u);
     HotItem it;
     it.idx = (uint32_t)i;
@@ -349,14 +388,16 @@ __device__ __forceinline__ void push_hot(const Scratch& S, DevCtl* ctl, long lon
     S.hot[k] = it;
 }
 
-// One thread per particle.  first_pass: rows [0, pass_end) with the full step;
-// otherwise rows [pass_begin, pass_end) (children) with their stored time.
-__global__ void __launch_bounds__(kColdThreads) k_cold(DevParticles P, StepParams SP, Scratch S,
-                                                       DevCtl* ctl, int first_pass) {
+// One thread per particle.  First generation of a step: rows [0, pass_end)
+// with the full step; later generations: rows [pass_begin, pass_end)
+// (children) with their stored remaining time.
+__global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevParticles P, StepParams SP, Scratch S,
+                                                       DevCtl* ctl) {
     __shared__ SharedTables sm;
     stage_tables(sm);
     __syncthreads();
     if (ctl->status == (int)QED_ERR_TIMEOUT) return;
+    const int first_pass = ctl->first_pass;
     const long long begin = first_pass ? 0 : ctl->pass_begin;
     const long long end = ctl->pass_end;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -368,8 +409,8 @@ __global__ void __launch_bounds__(kColdThreads) k_cold(DevParticles P, StepParam
         if (type > QED_PHOTON) continue;
         const bool photon = type == QED_PHOTON;
         if (!process_enabled(SP, photon)) continue;
-        double t_rem = first_pass ? SP.dt : S.t_rem[i];
-        if (!(t_rem > 0.0)) continue;
+        ticks_t t_rem = first_pass ? kTicksPerStep : S.t_rem[i];
+        if (t_rem == 0) continue;
         const uint64_t id = P.id[i];
         PState st{P.px[i], P.py[i], P.pz[i]};
         const float Ex = P.Ex[i], Ey = P.Ey[i], Ez = P.Ez[i];
@@ -378,12 +419,11 @@ __global__ void __launch_bounds__(kColdThreads) k_cold(DevParticles P, StepParam
         uint32_t s = 0;
         uint4 blk = make_uint4(0, 0, 0, 0);
         uint32_t blk_idx = 0xffffffffu;
-        while (t_rem > 0.0) {
-            float eps;
-            const float chi = chi_ff(photon, st.px, st.py, st.pz, Ex, Ey, Ez, Bx, By, Bz,
-                                     SP.inv_Es, &eps);
+        while (t_rem > 0) {
+            float eps, chi;
+            const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
+                                          Ey, Ez, Bx, By, Bz, t_rem, &chi, &eps);
             if (!(eps > 0.0f)) break;
-            const Plan pl = make_plan(SP, sm.sqz_e, sm.sqz_p, photon, chi, eps, t_rem);
             stats.plans++;
             stats.guard += pl.guard ? 1 : 0;
             stats.max_N = max(stats.max_N, pl.N);
@@ -396,7 +436,7 @@ __global__ void __launch_bounds__(kColdThreads) k_cold(DevParticles P, StepParam
                 }
                 stats.plans--;  // the warp path re-plans and counts it
                 push_hot(S, ctl, i, s, t_rem);
-                t_rem = 0.0;
+                t_rem = 0;
                 break;
             }
             bool event = false;
@@ -416,11 +456,10 @@ __global__ void __launch_bounds__(kColdThreads) k_cold(DevParticles P, StepParam
                     float delta;
                     const float Pa = acceptance(sm.syn, photon, pl.b, pl.c_h, x, &delta);
                     if (u01(ry) < Pa) {
-                        const double t_after =
-                            (k + 1 == pl.N) ? 0.0
-                                            : __dsub_rn(t_rem, __dmul_rn((double)(k + 1), pl.h));
+                        const ticks_t t_after =
+                            (k + 1 == pl.N) ? 0ull : t_rem - (ticks_t)(k + 1) * pl.h;
                         removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, s,
-                                              t_after, st, stats, true);
+                                              t_after, st, stats, true, false);
                         changed = true;
                         ++s;
                         t_rem = t_after;
@@ -431,7 +470,7 @@ __global__ void __launch_bounds__(kColdThreads) k_cold(DevParticles P, StepParam
                 ++s;
             }
             if (removed) break;
-            if (!event) t_rem = 0.0;
+            if (!event) t_rem = 0;
         }
         if (removed) {
             P.type[i] = QED_REMOVED;
@@ -445,7 +484,7 @@ __global__ void __launch_bounds__(kColdThreads) k_cold(DevParticles P, StepParam
 }
 
 // One warp per queued particle.
-__global__ void __launch_bounds__(kHotThreads) k_hot(DevParticles P, StepParams SP, Scratch S,
+__global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevParticles P, StepParams SP, Scratch S,
                                                      DevCtl* ctl) {
     __shared__ SharedTables sm;
     stage_tables(sm);
@@ -453,7 +492,8 @@ __global__ void __launch_bounds__(kHotThreads) k_hot(DevParticles P, StepParams 
     const int lane = threadIdx.x & 31;
     const unsigned int tail = ctl->hot_tail;
     const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
-    Stats stats;  // counted on lane 0 only
+    Stats stats;              // counted on lane 0 only
+    unsigned long long cand = 0;  // candidates, counted per lane
     while (true) {
         unsigned int q = 0;
         if (lane == 0) q = atomicAdd(&ctl->hot_head, 1u);
@@ -468,14 +508,13 @@ __global__ void __launch_bounds__(kHotThreads) k_hot(DevParticles P, StepParams 
         const float Ex = P.Ex[i], Ey = P.Ey[i], Ez = P.Ez[i];
         const float Bx = P.Bx[i], By = P.By[i], Bz = P.Bz[i];
         uint32_t s = it.s;
-        double t_rem = it.t_rem;
+        ticks_t t_rem = it.t_rem;
         bool removed = false, changed = false;
-        while (t_rem > 0.0) {
-            float eps;
-            const float chi = chi_ff(photon, st.px, st.py, st.pz, Ex, Ey, Ez, Bx, By, Bz,
-                                     SP.inv_Es, &eps);
+        while (t_rem > 0) {
+            float eps, chi;
+            const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
+                                          Ey, Ez, Bx, By, Bz, t_rem, &chi, &eps);
             if (!(eps > 0.0f)) break;
-            const Plan pl = make_plan(SP, sm.sqz_e, sm.sqz_p, photon, chi, eps, t_rem);
             if (lane == 0) {
                 stats.plans++;
                 stats.guard += pl.guard ? 1 : 0;
@@ -500,9 +539,7 @@ __global__ void __launch_bounds__(kHotThreads) k_hot(DevParticles P, StepParams 
                 if (c1) a1 = u01(r.w) < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(r.z), &dtmp);
                 const unsigned int m0 = __ballot_sync(0xffffffffu, a0);
                 const unsigned int m1 = __ballot_sync(0xffffffffu, a1);
-                const unsigned int nc =
-                    __popc(__ballot_sync(0xffffffffu, c0)) + __popc(__ballot_sync(0xffffffffu, c1));
-                if (lane == 0) stats.cand += nc;
+                cand += (unsigned)c0 + (unsigned)c1;
                 if ((m0 | m1) == 0u) {
                     const uint32_t chunk_end = min(sa + 64u, lim);
                     if (lane == 0) stats.substeps += chunk_end - sb;
@@ -518,10 +555,10 @@ __global__ void __launch_bounds__(kHotThreads) k_hot(DevParticles P, StepParams 
                 const float x = __shfl_sync(0xffffffffu, xo, pos >> 1);
                 const uint32_t k_ev = kdone + (s_ev - sb);
                 if (lane == 0) stats.substeps += s_ev - sb + 1;
-                const double t_after =
-                    (k_ev + 1 == pl.N) ? 0.0 : __dsub_rn(t_rem, __dmul_rn((double)(k_ev + 1), pl.h));
+                const ticks_t t_after =
+                    (k_ev + 1 == pl.N) ? 0ull : t_rem - (ticks_t)(k_ev + 1) * pl.h;
                 removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, s_ev, t_after,
-                                      st, stats, lane == 0);
+                                      st, stats, lane == 0, true);
                 changed = true;
                 s = s_ev + 1;
                 t_rem = t_after;
@@ -529,7 +566,7 @@ __global__ void __launch_bounds__(kHotThreads) k_hot(DevParticles P, StepParams 
                 break;
             }
             if (removed) break;
-            if (!event) t_rem = 0.0;
+            if (!event) t_rem = 0;
         }
         if (lane == 0) {
             if (removed) P.type[i] = QED_REMOVED;
@@ -541,10 +578,15 @@ __global__ void __launch_bounds__(kHotThreads) k_hot(DevParticles P, StepParams 
         }
     }
     if (lane != 0) stats = Stats();
+    stats.cand = cand;
+    stats.warp_substeps = stats.substeps;
     flush_stats(stats, ctl);
 }
 
-__global__ void k_step_init(DevCtl* ctl, long long* count, long long capacity) {
+// Start a step.  keep_sticky: inside a multi-step graph, a step that follows
+// a failed step does nothing (its range is empty and it keeps the status).
+__global__ void k_step_init(DevCtl* ctl, long long* count, long long capacity, int keep_sticky) {
+    const int sticky = keep_sticky ? ctl->sticky : 0;
     DevCtl c;
     memset(&c, 0, sizeof c);
     long long n = *count;
@@ -552,22 +594,223 @@ __global__ void k_step_init(DevCtl* ctl, long long* count, long long capacity) {
     if (n > capacity) n = capacity;
     *count = n;
     c.pass_begin = 0;
-    c.pass_end = n;
+    c.pass_end = sticky ? 0 : n;
+    c.first_pass = 1;
+    c.sticky = sticky;
+    c.status = sticky;
     *ctl = c;
 }
 
-__global__ void k_advance(DevCtl* ctl, long long* count, long long capacity, int more_allowed) {
+// Close a cascade generation: the next generation is the rows appended during
+// this one.  In a graph, the WHILE node's condition is set here.
+__global__ void k_advance(DevCtl* ctl, long long* count, long long capacity, int more_allowed,
+                          int max_passes, cudaGraphConditionalHandle handle, int use_handle) {
     long long n = *count;
     if (n > capacity) {
         n = capacity;
         *count = capacity;
     }
-    ctl->pass_begin = ctl->pass_end;
-    ctl->pass_end = n;
+    ctl->pass_begin = ctl->sticky ? 0 : ctl->pass_end;
+    ctl->pass_end = ctl->sticky ? 0 : n;
     ctl->hot_head = 0;
     ctl->hot_tail = 0;
     ctl->passes += 1;
-    ctl->more = (more_allowed && n > ctl->pass_begin && ctl->status == 0) ? 1 : 0;
+    ctl->first_pass = 0;
+    int more = (more_allowed && ctl->pass_end > ctl->pass_begin && ctl->status == 0) ? 1 : 0;
+    if (more && ctl->passes >= max_passes) {
+        more = 0;
+        ctl->status = (int)QED_ERR_STATE;  // cascade deeper than the configured passes
+    }
+    ctl->more = more;
+    if (use_handle) cudaGraphSetConditional(handle, (unsigned int)more);
+}
+
+// Write the statistics of the step into `rec` (if not null); an error becomes
+// sticky for the following steps of a graph run.
+__global__ void k_step_close(DevCtl* ctl, const long long* count, qed_step_stats* rec) {
+    const DevCtl c = *ctl;
+    if (rec) {
+        qed_step_stats r;
+        r.substeps = c.substeps;
+        r.emissions = c.emissions;
+        r.pairs = c.pairs;
+        r.children = c.children;
+        r.guard_hits = c.guard_hits;
+        r.plans = c.plans;
+        r.candidates = c.candidates;
+        r.max_N = c.max_N;
+        r.status = c.status;
+        r.required_capacity = c.required;
+        r.count = *count;
+        r.passes = c.passes;
+        r.reserved = 0;
+        r.substeps_warp = c.substeps_warp;
+        *rec = r;
+    }
+    if (c.status != 0 && c.sticky == 0) ctl->sticky = c.status;
+}
+
+// Reset the sticky status at the start of a multi-step graph run.
+__global__ void k_graph_begin(DevCtl* ctl) { ctl->sticky = 0; }
+
+// ---------------------------------------------------------------------------
+// Compaction: squeeze removed rows (decayed or drained photons) out of the
+// store, keeping the order of the remaining rows.  Optionally drains photons
+// whose chi is below `drain_chi` into a weighted log-energy spectrum first.
+// Out of place through a mirror store, then copied back.
+// ---------------------------------------------------------------------------
+constexpr int kCompactThreads = 1024;
+constexpr int kCompactRows = 4;                        // rows per thread per tile
+constexpr int kTile = kCompactThreads * kCompactRows;  // rows per block
+
+struct Mirror {
+    float *px, *py, *pz, *Ex, *Ey, *Ez, *Bx, *By, *Bz, *w;
+    uint64_t* id;
+    uint8_t* type;
+};
+
+__device__ __forceinline__ long long clamp_count(const DevParticles& P) {
+    long long n = *P.count;
+    return n < 0 ? 0 : (n > P.capacity ? P.capacity : n);
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+    k_compact_count(DevParticles P, StepParams SP, float drain_chi, double* hist,
+                    unsigned int* block_live) {
+    __shared__ unsigned int warp_tot[kCompactThreads / 32];
+    const long long n = clamp_count(P);
+    const long long base = (long long)blockIdx.x * kTile;
+    unsigned int live = 0;
+    if (base < n) {
+#pragma unroll
+        for (int k = 0; k < kCompactRows; ++k) {
+            const long long i = base + (long long)k * kCompactThreads + threadIdx.x;
+            if (i >= n) break;
+            uint8_t t = P.type[i];
+            if (t == QED_PHOTON && drain_chi > 0.0f) {
+                float eps;
+                const float chi = chi_ff(true, P.px[i], P.py[i], P.pz[i], P.Ex[i], P.Ey[i], P.Ez[i],
+                                         P.Bx[i], P.By[i], P.Bz[i], SP.inv_Es, &eps);
+                if (chi < drain_chi) {
+                    if (hist) {
+                        const float l = log10f(fmaxf(eps, 1e-30f));
+                        int bin = (int)floorf((l - (float)QED_SPECTRUM_LOG10_MIN) *
+                                              ((float)QED_SPECTRUM_BINS /
+                                               (float)(QED_SPECTRUM_LOG10_MAX - QED_SPECTRUM_LOG10_MIN)));
+                        bin = min(max(bin, 0), QED_SPECTRUM_BINS - 1);
+                        atomicAdd(&hist[bin], (double)P.w[i]);
+                    }
+                    P.type[i] = QED_REMOVED;
+                    t = QED_REMOVED;
+                }
+            }
+            live += t <= QED_PHOTON ? 1u : 0u;
+        }
+    }
+    // block sum
+    unsigned int v = live;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned int w = warp_tot[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) block_live[blockIdx.x] = w;
+    }
+}
+
+// Exclusive scan of the per-tile counts (one block); total -> ctl->live.
+__global__ void __launch_bounds__(kCompactThreads)
+    k_compact_scan(unsigned int* block_live, int nb, DevCtl* ctl, const long long* count) {
+    __shared__ unsigned long long part[kCompactThreads];
+    const int per = (nb + kCompactThreads - 1) / kCompactThreads;
+    const int lo = threadIdx.x * per;
+    const int hi = min(lo + per, nb);
+    unsigned long long sum = 0;
+    for (int i = lo; i < hi; ++i) sum += block_live[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over the 1024 partial sums
+    for (int o = 1; o < kCompactThreads; o <<= 1) {
+        const unsigned long long add = threadIdx.x >= o ? part[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += add;
+        __syncthreads();
+    }
+    unsigned long long run = part[threadIdx.x] - sum;  // exclusive
+    for (int i = lo; i < hi; ++i) {
+        const unsigned int c = block_live[i];
+        block_live[i] = (unsigned int)run;
+        run += c;
+    }
+    if (threadIdx.x == kCompactThreads - 1) {
+        const long long total = (long long)part[kCompactThreads - 1];
+        long long n = *count;
+        ctl->live = total;
+        ctl->compact_needed = total != n ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(kCompactThreads)
+    k_compact_scatter(DevParticles P, Mirror M, const unsigned int* block_off, const DevCtl* ctl) {
+    if (!ctl->compact_needed) return;
+    __shared__ unsigned int warp_tot[kCompactThreads / 32];
+    __shared__ unsigned int carry;
+    const long long n = clamp_count(P);
+    const long long base = (long long)blockIdx.x * kTile;
+    if (base >= n) return;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long off = block_off[blockIdx.x];
+    for (int k = 0; k < kCompactRows; ++k) {
+        const long long i = base + (long long)k * kCompactThreads + threadIdx.x;
+        const bool keep = i < n && P.type[i] <= QED_PHOTON;
+        const unsigned int b = __ballot_sync(0xffffffffu, keep);
+        const unsigned int in_warp = __popc(b & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[warp] = __popc(b);
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned int v = warp_tot[lane];
+            unsigned int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            warp_tot[lane] = incl - v;  // exclusive offsets of the warps
+        }
+        __syncthreads();
+        if (keep) {
+            const long long d = off + carry + warp_tot[warp] + in_warp;
+            M.px[d] = P.px[i]; M.py[d] = P.py[i]; M.pz[d] = P.pz[i];
+            M.Ex[d] = P.Ex[i]; M.Ey[d] = P.Ey[i]; M.Ez[d] = P.Ez[i];
+            M.Bx[d] = P.Bx[i]; M.By[d] = P.By[i]; M.Bz[d] = P.Bz[i];
+            M.w[d] = P.w[i]; M.id[d] = P.id[i]; M.type[d] = P.type[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == kCompactThreads - 1)
+            carry += warp_tot[warp] + in_warp + (keep ? 1u : 0u);
+        __syncthreads();
+    }
+}
+
+__global__ void k_compact_copyback(DevParticles P, Mirror M, DevCtl* ctl) {
+    if (!ctl->compact_needed) return;
+    const long long live = ctl->live;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < live; i += stride) {
+        P.px[i] = M.px[i]; P.py[i] = M.py[i]; P.pz[i] = M.pz[i];
+        P.Ex[i] = M.Ex[i]; P.Ey[i] = M.Ey[i]; P.Ez[i] = M.Ez[i];
+        P.Bx[i] = M.Bx[i]; P.By[i] = M.By[i]; P.Bz[i] = M.Bz[i];
+        P.w[i] = M.w[i]; P.id[i] = M.id[i]; P.type[i] = M.type[i];
+    }
+}
+
+__global__ void k_compact_finish(DevParticles P, const DevCtl* ctl) {
+    if (ctl->compact_needed) *P.count = ctl->live;
 }
 
 }  // namespace
@@ -582,13 +825,29 @@ struct qed_ctx {
     int sms;
     DevCtl* d_ctl;
     DevCtl* h_ctl;          // pinned
-    double* d_trem;
+    ticks_t* d_trem;
     HotItem* d_hot;
     long long scratch_cap;
     qed_event_record* log;
     long long log_cap;
     long long* log_count;
     int cold_blocks, hot_blocks;
+    // compaction
+    Mirror mirror;
+    long long mirror_cap;
+    unsigned int* d_block_live;
+    double* d_hist;
+    // multi-step graph
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
+    qed_step_stats* d_records;
+    int graph_steps;
+    // benchmark timing: event pairs recorded around launches
+    int prof_on;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_kind;
+    size_t prof_used;
+    long long launches[QED_KERNEL_KINDS];
     char err[512];
 };
 
@@ -618,6 +877,7 @@ StepParams make_params(const qed_config& c, uint64_t step) {
     const double period = c.lambda_m / kCLight;
     const double R = kAlpha / kTauC * period;                 // 1 / period
     P.K = (float)(1.7320508075688772 / kPiD * R);
+    P.K_tick = (float)(1.7320508075688772 / kPiD * R * c.dt_periods / (double)kTicksPerStep);
     const double omega = 2.0 * kPiD * kCLight / c.lambda_m;
     P.inv_Es = (float)(omega * kTauC);                        // 1 / E_s in code units
     P.p_max = c.p_max;
@@ -652,10 +912,92 @@ qed_status ensure_scratch(qed_ctx* ctx, long long cap) {
     ctx->d_trem = nullptr;
     ctx->d_hot = nullptr;
     ctx->scratch_cap = 0;
-    QED_CUDA(ctx, cudaMalloc(&ctx->d_trem, sizeof(double) * cap));
+    QED_CUDA(ctx, cudaMalloc(&ctx->d_trem, sizeof(ticks_t) * cap));
     QED_CUDA(ctx, cudaMalloc(&ctx->d_hot, sizeof(HotItem) * cap));
     ctx->scratch_cap = cap;
     return QED_OK;
+}
+
+// Bracket a launch with timing events when profiling is on; count it always.
+struct LaunchScope {
+    qed_ctx* ctx;
+    int kind;
+    size_t slot;
+    LaunchScope(qed_ctx* c, int k) : ctx(c), kind(k), slot((size_t)-1) {
+        ctx->launches[kind]++;
+        if (!ctx->prof_on) return;
+        if (ctx->prof_used + 2 > ctx->prof_ev.size()) {
+            size_t grow = ctx->prof_ev.size() ? ctx->prof_ev.size() : 512;
+            for (size_t i = 0; i < grow; ++i) {
+                cudaEvent_t e;
+                if (cudaEventCreate(&e) != cudaSuccess) return;
+                ctx->prof_ev.push_back(e);
+            }
+        }
+        slot = ctx->prof_used;
+        ctx->prof_used += 2;
+        ctx->prof_kind.push_back(kind);
+        cudaEventRecord(ctx->prof_ev[slot], ctx->stream);
+    }
+    ~LaunchScope() {
+        if (slot != (size_t)-1) cudaEventRecord(ctx->prof_ev[slot + 1], ctx->stream);
+    }
+};
+
+qed_status ensure_mirror(qed_ctx* ctx, long long cap) {
+    if (!ctx->d_hist) {
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_hist, sizeof(double) * QED_SPECTRUM_BINS));
+        QED_CUDA(ctx, cudaMemsetAsync(ctx->d_hist, 0, sizeof(double) * QED_SPECTRUM_BINS,
+                                      ctx->stream));
+    }
+    if (ctx->mirror_cap >= cap) return QED_OK;
+    float** f[] = {&ctx->mirror.px, &ctx->mirror.py, &ctx->mirror.pz, &ctx->mirror.Ex,
+                   &ctx->mirror.Ey, &ctx->mirror.Ez, &ctx->mirror.Bx, &ctx->mirror.By,
+                   &ctx->mirror.Bz, &ctx->mirror.w};
+    for (float** a : f) {
+        if (*a) cudaFree(*a);
+        *a = nullptr;
+    }
+    if (ctx->mirror.id) cudaFree(ctx->mirror.id);
+    if (ctx->mirror.type) cudaFree(ctx->mirror.type);
+    if (ctx->d_block_live) cudaFree(ctx->d_block_live);
+    ctx->mirror.id = nullptr;
+    ctx->mirror.type = nullptr;
+    ctx->d_block_live = nullptr;
+    ctx->mirror_cap = 0;
+    for (float** a : f) QED_CUDA(ctx, cudaMalloc(a, sizeof(float) * cap));
+    QED_CUDA(ctx, cudaMalloc(&ctx->mirror.id, sizeof(uint64_t) * cap));
+    QED_CUDA(ctx, cudaMalloc(&ctx->mirror.type, cap));
+    const long long nb = (cap + kTile - 1) / kTile;
+    QED_CUDA(ctx, cudaMalloc(&ctx->d_block_live, sizeof(unsigned int) * nb));
+    ctx->mirror_cap = cap;
+    return QED_OK;
+}
+
+void free_graph(qed_ctx* ctx) {
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->d_records) cudaFree(ctx->d_records);
+    ctx->graph_exec = nullptr;
+    ctx->graph = nullptr;
+    ctx->d_records = nullptr;
+    ctx->graph_steps = 0;
+}
+
+bool cascade_enabled(const qed_config& c) {
+    return c.cascade_in_step &&
+           (c.process_mask & (QED_PROC_EMISSION | QED_PROC_PAIR)) ==
+               (QED_PROC_EMISSION | QED_PROC_PAIR);
+}
+
+Scratch make_scratch(const qed_ctx* ctx) {
+    Scratch S;
+    S.t_rem = ctx->d_trem;
+    S.hot = ctx->d_hot;
+    S.log = ctx->log;
+    S.log_cap = ctx->log_cap;
+    S.log_count = ctx->log_count;
+    return S;
 }
 
 void fill_stats(const DevCtl& c, qed_step_stats* out, long long count) {
@@ -672,6 +1014,7 @@ void fill_stats(const DevCtl& c, qed_step_stats* out, long long count) {
     out->count = count;
     out->passes = c.passes;
     out->reserved = 0;
+    out->substeps_warp = c.substeps_warp;
 }
 
 }  // namespace
@@ -689,13 +1032,14 @@ void qed_config_default(qed_config* c) {
     c->cascade_in_step = 1;
     c->recoil = 1;
     c->max_passes = 64;
+    c->drain_chi = 0.0f;
 }
 
 qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
     if (!out || !cfg) return QED_ERR_ARG;
     *out = nullptr;
     if (!(cfg->p_max > 0.0f && cfg->p_max <= 1.0f) || !(cfg->dt_periods > 0.0) ||
-        !(cfg->lambda_m > 0.0) || !(cfg->pair_bound_coeff > 0.0f))
+        !(cfg->lambda_m > 0.0) || !(cfg->pair_bound_coeff > 0.0f) || !(cfg->drain_chi >= 0.0f))
         return QED_ERR_ARG;
     qed_ctx* ctx = new (std::nothrow) qed_ctx();
     if (!ctx) return QED_ERR_ARG;
@@ -730,11 +1074,21 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
 
 qed_status qed_destroy(qed_ctx* ctx) {
     if (!ctx) return QED_ERR_ARG;
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     if (ctx->stream || ctx->d_ctl) cudaStreamSynchronize(ctx->stream);
     if (ctx->d_ctl) cudaFree(ctx->d_ctl);
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     if (ctx->d_trem) cudaFree(ctx->d_trem);
     if (ctx->d_hot) cudaFree(ctx->d_hot);
+    free_graph(ctx);
+    float* f[] = {ctx->mirror.px, ctx->mirror.py, ctx->mirror.pz, ctx->mirror.Ex, ctx->mirror.Ey,
+                  ctx->mirror.Ez, ctx->mirror.Bx, ctx->mirror.By, ctx->mirror.Bz, ctx->mirror.w};
+    for (float* a : f)
+        if (a) cudaFree(a);
+    if (ctx->mirror.id) cudaFree(ctx->mirror.id);
+    if (ctx->mirror.type) cudaFree(ctx->mirror.type);
+    if (ctx->d_block_live) cudaFree(ctx->d_block_live);
+    if (ctx->d_hist) cudaFree(ctx->d_hist);
     delete ctx;
     return QED_OK;
 }
@@ -743,14 +1097,15 @@ const char* qed_last_error(const qed_ctx* ctx) { return ctx ? ctx->err : "null c
 
 qed_status qed_synchrotron_F1F2(qed_ctx* ctx, const float* y, float* F1, float* F2, int64_t n) {
     if (!ctx) return QED_ERR_ARG;
+    if (n == 0 || (n > 0 && !F1 && !F2)) return QED_OK;
     if (!y || n < 0) return set_err(ctx, QED_ERR_ARG, "qed_synchrotron_F1F2: bad argument");
-    if (n == 0 || (!F1 && !F2)) return QED_OK;
     const int vec = ((((uintptr_t)y) | ((uintptr_t)F1) | ((uintptr_t)F2)) & 15u) == 0 ? 1 : 0;
     long long work = vec ? (n + 3) / 4 : n;
     long long blocks = (work + kSweepThreads - 1) / kSweepThreads;
     const long long max_blocks = (long long)ctx->sms * 8;
     if (blocks > max_blocks) blocks = max_blocks;
     if (blocks < 1) blocks = 1;
+    LaunchScope ls(ctx, QED_KERNEL_SWEEP);
     if (F1 && F2)
         k_sweep<true, true><<<(int)blocks, kSweepThreads, 0, ctx->stream>>>(y, F1, F2, n, vec);
     else if (F1)
@@ -769,6 +1124,7 @@ qed_status qed_synchrotron_generate(qed_ctx* ctx, uint64_t seed, int64_t n, floa
     long long blocks = ((n + 3) / 4 + kSweepThreads - 1) / kSweepThreads;
     const long long max_blocks = (long long)ctx->sms * 8;
     if (blocks > max_blocks) blocks = max_blocks;
+    LaunchScope ls(ctx, QED_KERNEL_GENERATE);
     k_generate<<<(int)blocks, kSweepThreads, 0, ctx->stream>>>(
         (uint32_t)seed, (uint32_t)(seed >> 32), n, lo, log2f(hi / lo), checksum, y_out, F1_out,
         F2_out);
@@ -783,6 +1139,7 @@ qed_status qed_plan(qed_ctx* ctx, const qed_particles* p, int64_t n, float* chi,
     const StepParams SP = make_params(ctx->cfg, 0);
     long long blocks = (n + kColdThreads - 1) / kColdThreads;
     if (blocks > ctx->cold_blocks) blocks = ctx->cold_blocks;
+    LaunchScope ls(ctx, QED_KERNEL_PLAN);
     k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(to_dev(p), SP, n, chi, N);
     return cuda_check(ctx, cudaGetLastError(), "k_plan");
 }
@@ -807,21 +1164,26 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
     if (st != QED_OK) return st;
     const StepParams SP = make_params(ctx->cfg, step_index);
     const DevParticles D = to_dev(p);
-    Scratch S;
-    S.t_rem = ctx->d_trem;
-    S.hot = ctx->d_hot;
-    S.log = ctx->log;
-    S.log_cap = ctx->log_cap;
-    S.log_count = ctx->log_count;
-    const bool cascade = ctx->cfg.cascade_in_step &&
-                         (ctx->cfg.process_mask & (QED_PROC_EMISSION | QED_PROC_PAIR)) ==
-                             (QED_PROC_EMISSION | QED_PROC_PAIR);
-    k_step_init<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity);
+    const Scratch S = make_scratch(ctx);
+    const bool cascade = cascade_enabled(ctx->cfg);
+    {
+        LaunchScope ls(ctx, QED_KERNEL_CONTROL);
+        k_step_init<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, 0);
+    }
     for (int pass = 0; pass < ctx->cfg.max_passes; ++pass) {
-        k_cold<<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl,
-                                                                    pass == 0 ? 1 : 0);
-        k_hot<<<ctx->hot_blocks, kHotThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
-        k_advance<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, cascade ? 1 : 0);
+        {
+            LaunchScope ls(ctx, QED_KERNEL_COLD);
+            k_cold<<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+        }
+        {
+            LaunchScope ls(ctx, QED_KERNEL_HOT);
+            k_hot<<<ctx->hot_blocks, kHotThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+        }
+        {
+            LaunchScope ls(ctx, QED_KERNEL_CONTROL);
+            k_advance<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, cascade ? 1 : 0,
+                                                ctx->cfg.max_passes, 0ull, 0);
+        }
         QED_CUDA(ctx, cudaGetLastError());
         if (!cascade) break;
         QED_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, sizeof(DevCtl),
@@ -840,6 +1202,238 @@ qed_status qed_read_stats(qed_ctx* ctx, qed_step_stats* out) {
     QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     fill_stats(*ctx->h_ctl, out, ctx->h_ctl->pass_end);
     return (qed_status)ctx->h_ctl->status;
+}
+
+// Launch the compaction kernels (and the photon drain) on the context stream.
+static qed_status launch_compaction(qed_ctx* ctx, const DevParticles& D, const StepParams& SP) {
+    const long long nb = (D.capacity + kTile - 1) / kTile;
+    if (nb > (1ll << 31) - 1) return set_err(ctx, QED_ERR_ARG, "capacity too large");
+    {
+        LaunchScope ls(ctx, QED_KERNEL_CONTROL);
+        k_compact_count<<<(int)nb, kCompactThreads, 0, ctx->stream>>>(
+            D, SP, ctx->cfg.drain_chi, ctx->d_hist, ctx->d_block_live);
+        k_compact_scan<<<1, kCompactThreads, 0, ctx->stream>>>(ctx->d_block_live, (int)nb,
+                                                               ctx->d_ctl, D.count);
+        k_compact_scatter<<<(int)nb, kCompactThreads, 0, ctx->stream>>>(D, ctx->mirror,
+                                                                        ctx->d_block_live, ctx->d_ctl);
+        k_compact_copyback<<<ctx->sms * 8, 256, 0, ctx->stream>>>(D, ctx->mirror, ctx->d_ctl);
+        k_compact_finish<<<1, 1, 0, ctx->stream>>>(D, ctx->d_ctl);
+    }
+    return cuda_check(ctx, cudaGetLastError(), "compaction");
+}
+
+qed_status qed_compact(qed_ctx* ctx, const qed_particles* p, int64_t* removed) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!particles_ok(p)) return set_err(ctx, QED_ERR_ARG, "qed_compact: bad argument");
+    qed_status st = ensure_mirror(ctx, p->capacity);
+    if (st != QED_OK) return st;
+    const DevParticles D = to_dev(p);
+    const StepParams SP = make_params(ctx->cfg, 0);
+    long long before = 0;
+    if (removed) {
+        QED_CUDA(ctx, cudaMemcpyAsync(&before, p->count, sizeof before, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    }
+    st = launch_compaction(ctx, D, SP);
+    if (st != QED_OK) return st;
+    if (removed) {
+        long long after = 0;
+        QED_CUDA(ctx, cudaMemcpyAsync(&after, p->count, sizeof after, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        *removed = before - after;
+    }
+    return QED_OK;
+}
+
+qed_status qed_read_spectrum(qed_ctx* ctx, double* out, int nbins, int reset) {
+    if (!ctx || !out || nbins != QED_SPECTRUM_BINS) return QED_ERR_ARG;
+    if (!ctx->d_hist) {
+        for (int i = 0; i < nbins; ++i) out[i] = 0.0;
+        return QED_OK;
+    }
+    QED_CUDA(ctx, cudaMemcpyAsync(out, ctx->d_hist, sizeof(double) * nbins,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    if (reset)
+        QED_CUDA(ctx, cudaMemsetAsync(ctx->d_hist, 0, sizeof(double) * nbins, ctx->stream));
+    QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return QED_OK;
+}
+
+namespace {
+
+// Append a kernel node with `args` to graph g after `deps`.
+qed_status add_kernel(qed_ctx* ctx, cudaGraph_t g, cudaGraphNode_t* node, const void* func,
+                      dim3 grid, dim3 block, void** args, const cudaGraphNode_t* deps, int ndeps) {
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof kp);
+    kp.func = const_cast<void*>(func);
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    return cuda_check(ctx, cudaGraphAddKernelNode(node, g, deps, (size_t)ndeps, &kp),
+                      "cudaGraphAddKernelNode");
+}
+
+}  // namespace
+
+qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t first_step,
+                             int nsteps) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!particles_ok(p) || nsteps <= 0 || first_step + (uint64_t)nsteps > 0x100000000ull)
+        return set_err(ctx, QED_ERR_ARG, "qed_graph_capture: bad argument");
+    free_graph(ctx);
+    qed_status st = ensure_scratch(ctx, p->capacity);
+    if (st == QED_OK) st = ensure_mirror(ctx, p->capacity);
+    if (st != QED_OK) return st;
+    QED_CUDA(ctx, cudaMalloc(&ctx->d_records, sizeof(qed_step_stats) * nsteps));
+    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_records, 0, sizeof(qed_step_stats) * nsteps, ctx->stream));
+    QED_CUDA(ctx, cudaGraphCreate(&ctx->graph, 0));
+    cudaGraph_t g = ctx->graph;
+    DevParticles D = to_dev(p);
+    Scratch S = make_scratch(ctx);
+    DevCtl* ctl = ctx->d_ctl;
+    long long* count = D.count;
+    long long capacity = D.capacity;
+    int more_allowed = cascade_enabled(ctx->cfg) ? 1 : 0;
+    int max_passes = ctx->cfg.max_passes;
+    int keep_sticky = 1;
+    float drain = ctx->cfg.drain_chi;
+    double* hist = ctx->d_hist;
+    Mirror M = ctx->mirror;
+    unsigned int* block_live = ctx->d_block_live;
+    const long long nbl = (capacity + kTile - 1) / kTile;
+    int nb = (int)nbl;
+
+    cudaGraphNode_t prev;
+    {
+        void* a[] = {&ctl};
+        st = add_kernel(ctx, g, &prev, (const void*)k_graph_begin, dim3(1), dim3(1), a, nullptr, 0);
+        if (st != QED_OK) return st;
+    }
+    for (int k = 0; k < nsteps && st == QED_OK; ++k) {
+        StepParams SP = make_params(ctx->cfg, first_step + (uint64_t)k);
+        qed_step_stats* rec = ctx->d_records + k;
+        cudaGraphNode_t init, wnode, n1, n2, n3, n4, n5, close;
+        {
+            void* a[] = {&ctl, &count, &capacity, &keep_sticky};
+            st = add_kernel(ctx, g, &init, (const void*)k_step_init, dim3(1), dim3(1), a, &prev, 1);
+        }
+        // WHILE node: one cascade generation per iteration
+        cudaGraphConditionalHandle h;
+        if (st == QED_OK)
+            st = cuda_check(ctx, cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault),
+                            "cudaGraphConditionalHandleCreate");
+        if (st != QED_OK) break;
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        memset(&cp.conditional, 0, sizeof cp.conditional);
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        st = cuda_check(ctx, cudaGraphAddNode(&wnode, g, &init, nullptr, 1, &cp), "cudaGraphAddNode");
+        if (st != QED_OK) break;
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t bc, bh, ba;
+        int use_handle = 1;
+        {
+            void* a[] = {&D, &SP, &S, &ctl};
+            st = add_kernel(ctx, body, &bc, (const void*)k_cold, dim3(ctx->cold_blocks),
+                            dim3(kColdThreads), a, nullptr, 0);
+        }
+        if (st == QED_OK) {
+            void* a[] = {&D, &SP, &S, &ctl};
+            st = add_kernel(ctx, body, &bh, (const void*)k_hot, dim3(ctx->hot_blocks),
+                            dim3(kHotThreads), a, &bc, 1);
+        }
+        if (st == QED_OK) {
+            void* a[] = {&ctl, &count, &capacity, &more_allowed, &max_passes, &h, &use_handle};
+            st = add_kernel(ctx, body, &ba, (const void*)k_advance, dim3(1), dim3(1), a, &bh, 1);
+        }
+        // compaction (and optional photon drain) after the cascade
+        if (st == QED_OK) {
+            void* a[] = {&D, &SP, &drain, &hist, &block_live};
+            st = add_kernel(ctx, g, &n1, (const void*)k_compact_count, dim3(nb),
+                            dim3(kCompactThreads), a, &wnode, 1);
+        }
+        if (st == QED_OK) {
+            void* a[] = {&block_live, &nb, &ctl, &count};
+            st = add_kernel(ctx, g, &n2, (const void*)k_compact_scan, dim3(1), dim3(kCompactThreads),
+                            a, &n1, 1);
+        }
+        if (st == QED_OK) {
+            void* a[] = {&D, &M, &block_live, &ctl};
+            st = add_kernel(ctx, g, &n3, (const void*)k_compact_scatter, dim3(nb),
+                            dim3(kCompactThreads), a, &n2, 1);
+        }
+        if (st == QED_OK) {
+            void* a[] = {&D, &M, &ctl};
+            st = add_kernel(ctx, g, &n4, (const void*)k_compact_copyback, dim3(ctx->sms * 8),
+                            dim3(256), a, &n3, 1);
+        }
+        if (st == QED_OK) {
+            void* a[] = {&D, &ctl};
+            st = add_kernel(ctx, g, &n5, (const void*)k_compact_finish, dim3(1), dim3(1), a, &n4, 1);
+        }
+        if (st == QED_OK) {
+            void* a[] = {&ctl, &count, &rec};
+            st = add_kernel(ctx, g, &close, (const void*)k_step_close, dim3(1), dim3(1), a, &n5, 1);
+        }
+        prev = close;
+    }
+    if (st == QED_OK)
+        st = cuda_check(ctx, cudaGraphInstantiate(&ctx->graph_exec, g, 0), "cudaGraphInstantiate");
+    if (st != QED_OK) {
+        free_graph(ctx);
+        return st;
+    }
+    ctx->graph_steps = nsteps;
+    return QED_OK;
+}
+
+qed_status qed_graph_launch(qed_ctx* ctx) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!ctx->graph_exec) return set_err(ctx, QED_ERR_STATE, "qed_graph_launch: no graph captured");
+    ctx->launches[QED_KERNEL_CONTROL] += 1;
+    return cuda_check(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->stream), "cudaGraphLaunch");
+}
+
+qed_status qed_graph_read_stats(qed_ctx* ctx, qed_step_stats* out, int nsteps) {
+    if (!ctx || !out || nsteps <= 0) return QED_ERR_ARG;
+    if (!ctx->d_records || nsteps > ctx->graph_steps)
+        return set_err(ctx, QED_ERR_STATE, "qed_graph_read_stats: no such steps");
+    QED_CUDA(ctx, cudaMemcpyAsync(out, ctx->d_records, sizeof(qed_step_stats) * nsteps,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < nsteps; ++k)
+        if (out[k].status != 0) return (qed_status)out[k].status;
+    return QED_OK;
+}
+
+qed_status qed_profile_enable(qed_ctx* ctx, int enable) {
+    if (!ctx) return QED_ERR_ARG;
+    ctx->prof_on = enable ? 1 : 0;
+    return QED_OK;
+}
+
+qed_status qed_profile_read(qed_ctx* ctx, double* ms, int64_t* launches, int n) {
+    if (!ctx || n < 0 || n > QED_KERNEL_KINDS) return QED_ERR_ARG;
+    QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    double acc[QED_KERNEL_KINDS] = {0};
+    for (size_t k = 0; k < ctx->prof_kind.size(); ++k) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, ctx->prof_ev[2 * k], ctx->prof_ev[2 * k + 1]) == cudaSuccess)
+            acc[ctx->prof_kind[k]] += t;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (ms) ms[i] = acc[i];
+        if (launches) launches[i] = ctx->launches[i];
+    }
+    ctx->prof_kind.clear();
+    ctx->prof_used = 0;
+    for (int i = 0; i < QED_KERNEL_KINDS; ++i) ctx->launches[i] = 0;
+    return cuda_check(ctx, cudaGetLastError(), "qed_profile_read");
 }
 
 size_t qed_abi_struct_size(const char* name) {

@@ -111,16 +111,47 @@ __device__ __forceinline__ float chi_ff(bool photon, float px, float py, float p
     return qv > 0.0f ? __fsqrt_rn(qv) * inv_Es : 0.0f;
 }
 
+// chi in binary32 (Sec. 2.2).  Sets *well_conditioned when the rounding
+// error of chi is certainly below 3.2e-6 relative: the error of the computed
+// chi^2 is at most ~13 eps M^2 with M = eps|E| + |p||B| (a bound on |eps E +
+// p x B| and |p.E|), so kappa = 2 (eps^2 E^2 + p^2 B^2) / chi^2 >= M^2 / chi^2
+// <= 8 keeps it below 6.5 eps kappa ~ 3.2e-6.  Otherwise use chi_ff.
+__device__ __forceinline__ float chi_f32(bool photon, float px, float py, float pz, float Ex,
+                                         float Ey, float Ez, float Bx, float By, float Bz,
+                                         float inv_Es, float* eps_out, bool* well_conditioned) {
+    const float p2 = fmaf(px, px, fmaf(py, py, pz * pz));
+    const float eps = photon ? sqrtf(p2) : sqrtf(1.0f + p2);
+    const float cx = fmaf(py, Bz, -pz * By);
+    const float cy = fmaf(pz, Bx, -px * Bz);
+    const float cz = fmaf(px, By, -py * Bx);
+    const float ax = fmaf(eps, Ex, cx), ay = fmaf(eps, Ey, cy), az = fmaf(eps, Ez, cz);
+    const float s = fmaf(px, Ex, fmaf(py, Ey, pz * Ez));
+    const float q = fmaf(-s, s, fmaf(ax, ax, fmaf(ay, ay, az * az)));
+    const float E2 = fmaf(Ex, Ex, fmaf(Ey, Ey, Ez * Ez));
+    const float B2 = fmaf(Bx, Bx, fmaf(By, By, Bz * Bz));
+    const float M2 = 2.0f * fmaf(eps * eps, E2, p2 * B2);
+    *eps_out = eps;
+    *well_conditioned = q > 0.125f * M2;
+    return q > 0.0f ? sqrtf(q) * inv_Es : 0.0f;
+}
+
 // ---------------------------------------------------------------------------
 // Synchrotron functions F (first) and G (second), Sec. 3.2.1:
 //   F(x) = x^{1/3} exp(-lam_k x) P_k(t),  t = log2 x - k on [2^k, 2^(k+1)),
 //   t = x^{2/3} on the piece below 2^KMIN.  `tbl` is the table of
 //   synchro_coeffs.h as float4 rows of 16 floats (F c0..c5, G c0..c5, lam).
 // ---------------------------------------------------------------------------
-constexpr int kSynRows = QED_SYN_NPIECE * 4;  // float4 per table
+constexpr int kSynCoef = 2 * (QED_SYN_DEG + 1);   // F and G coefficients per piece
+constexpr int kSynStride = 32;                     // pieces padded to one bank row
 
-__device__ __forceinline__ void synchrotron_FG(const float4* __restrict__ tbl, float x, float& F,
-                                               float& G) {
+// Shared-memory form of the table: coefficient-major, so that the lanes of a
+// warp reading coefficient j of different pieces hit different banks.
+struct SynTable {
+    float c[kSynCoef][kSynStride];
+    unsigned int lam_mask;   // bit p set: piece p carries the exp(-x) envelope
+};
+
+__device__ __forceinline__ void synchrotron_FG(const SynTable& tb, float x, float& F, float& G) {
     const float l2 = __log2f(x);
     const float u = exp2f(l2 * (1.0f / 3.0f));                 // x^{1/3}
     const int e = ((__float_as_int(x) >> 23) & 0xff) - 127;   // floor(log2 x), normal x
@@ -129,19 +160,15 @@ __device__ __forceinline__ void synchrotron_FG(const float4* __restrict__ tbl, f
     const int piece = small ? 0 : k - QED_SYN_KMIN + 1;
     float t = small ? u * u : l2 - (float)k;
     t = fminf(t, 1.02f);
-    const float4* row = tbl + 4 * piece;
-    const float4 a = row[0], b = row[1], c = row[2], d = row[3];
-    float pf = fmaf(b.y, t, b.x);
-    pf = fmaf(pf, t, a.w);
-    pf = fmaf(pf, t, a.z);
-    pf = fmaf(pf, t, a.y);
-    pf = fmaf(pf, t, a.x);
-    float pg = fmaf(c.w, t, c.z);
-    pg = fmaf(pg, t, c.y);
-    pg = fmaf(pg, t, c.x);
-    pg = fmaf(pg, t, b.w);
-    pg = fmaf(pg, t, b.z);
-    const float env = u * expf(-d.x * x);
+    float pf = tb.c[QED_SYN_DEG][piece];
+    float pg = tb.c[2 * QED_SYN_DEG + 1][piece];
+#pragma unroll
+    for (int j = QED_SYN_DEG - 1; j >= 0; --j) {
+        pf = fmaf(pf, t, tb.c[j][piece]);
+        pg = fmaf(pg, t, tb.c[QED_SYN_DEG + 1 + j][piece]);
+    }
+    const float lam = ((tb.lam_mask >> piece) & 1u) ? 1.0f : 0.0f;
+    const float env = u * expf(-lam * x);
     const bool ok = (x > 0.0f) && (x < 88.0f);
     F = ok ? env * pf : 0.0f;
     G = ok ? env * pg : 0.0f;
@@ -149,11 +176,17 @@ __device__ __forceinline__ void synchrotron_FG(const float4* __restrict__ tbl, f
 
 // Copy the synchrotron table into shared memory (call with all threads of
 // the block, then __syncthreads()).
-__device__ __forceinline__ void stage_syn_table(float4* dst) {
-    // the __device__ source array is only 4-byte aligned: copy float by float
-    const float* src = &qed_syn_table[0][0];
-    float* d = reinterpret_cast<float*>(dst);
-    for (int i = threadIdx.x; i < 4 * kSynRows; i += blockDim.x) d[i] = src[i];
+__device__ __forceinline__ void stage_syn_table(SynTable& tb) {
+    for (int i = threadIdx.x; i < kSynCoef * kSynStride; i += blockDim.x) {
+        const int j = i / kSynStride, p = i % kSynStride;
+        tb.c[j][p] = p < QED_SYN_NPIECE ? qed_syn_table[p][j] : 0.0f;
+    }
+    if (threadIdx.x == 0) {
+        unsigned int m = 0;
+        for (int p = 0; p < QED_SYN_NPIECE; ++p)
+            if (qed_syn_table[p][kSynCoef] > 0.0f) m |= 1u << p;
+        tb.lam_mask = m;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -175,19 +208,29 @@ __device__ __forceinline__ float bound_emission(float b, float c) {
 // x -> 0 limit of 3 x^2 P(x^3) over c b^{2/3}:  4 pi / (sqrt3 Gamma(1/3) 2^{1/3}).
 constexpr float kSmallF = 2.14952824153447863f;
 
+// Remaining time of a particle within the global step, as an exact fixed-point
+// count: one global step is 2^62 ticks.  Sub-step lengths are floor(T / N)
+// ticks and the time after sub-step k of a plan is T - (k + 1) h, with the
+// last sub-step ending the plan exactly; integer arithmetic keeps the
+// partition exact without FP64 (whose rate on this GPU is 1/64 of FP32).
+using ticks_t = unsigned long long;
+constexpr ticks_t kTicksPerStep = 1ull << 62;
+
 struct Plan {
     uint32_t N;      // sub-steps for the remaining time
     float b;         // 3 chi / 2
     float c_h;       // sqrt3 R h / (pi gamma) for one sub-step
     uint32_t T;      // squeeze threshold on (r >> 9): candidates have (r >> 9) < T
-    double h;        // sub-step length (periods)
+    ticks_t h;       // sub-step length in ticks
     bool guard;      // N raised by the validity guard
+    bool safe;       // N cannot change within +-1e-5 (relative) of chi and f
 };
 
 struct StepParams {
     uint64_t seed;
     double dt;           // global step (periods)
     float K;             // sqrt3 R / pi  (1 / period)
+    float K_tick;        // K dt / 2^62: the same per tick
     float inv_Es;        // 1 / Schwinger field (code units)
     float p_max;
     float pair_coeff;
@@ -224,43 +267,90 @@ __device__ __forceinline__ uint32_t squeeze_threshold(float B) {
     return t <= 0.0f ? 0u : (t >= 0x1p23f ? (1u << 23) : (uint32_t)t);
 }
 
-// Plan the sub-steps of the remaining time t_rem (Algorithms 1/2, line 1).
+__device__ __forceinline__ int emission_piece(float b) {
+    return b < 0.1f ? 0 : (b < 0.5f ? 1 : (b < 10.0f ? 2 : 3));
+}
+
+// Plan the sub-steps of the remaining time T (Algorithms 1/2, line 1).
+// `safe` reports whether N is certain when chi carries a relative error of up
+// to 1e-5: every f(b) piece grows at most linearly in b, so f moves by less
+// than 2e-5 relative unless b crosses a piece boundary.
 __device__ __forceinline__ Plan make_plan(const StepParams& P, const float* __restrict__ sqz_e,
                                           const float* __restrict__ sqz_p, bool photon, float chi,
-                                          float eps, double t_rem) {
+                                          float eps, ticks_t T) {
+    constexpr float d = 2e-5f;
     Plan pl;
     pl.b = 1.5f * chi;
     const float inv_eps = 1.0f / eps;
-    const float c_rem = P.K * (float)t_rem * inv_eps;
+    const float c_rem = P.K_tick * (float)T * inv_eps;
     const float b = pl.b;
-    float f = photon ? P.pair_coeff * c_rem * b : bound_emission(b, c_rem);
-    float q = f / P.p_max;
+    const float f = photon ? P.pair_coeff * c_rem * b : bound_emission(b, c_rem);
+    const float q = f / P.p_max;
     float N = fmaxf(1.0f, ceilf(q));
     float b23 = 0.0f;
     if (b > 0.0f) b23 = exp2f(__log2f(b) * (2.0f / 3.0f));
     pl.guard = false;
+    float graw = 0.0f;
     if (!photon) {
-        const float g = ceilf(kSmallF * c_rem * b23);
+        graw = kSmallF * c_rem * b23;
+        const float g = ceilf(graw);
         if (g > N) { N = g; pl.guard = true; }
     }
+    // N = max(1, ceil(q), ceil(g)) is monotone in q and g: it is certain when
+    // it is the same at both ends of the band (and b stays in its f piece)
+    const float n_lo = fmaxf(1.0f, fmaxf(ceilf(q * (1.0f - d)), ceilf(graw * (1.0f - d))));
+    const float n_hi = fmaxf(1.0f, fmaxf(ceilf(q * (1.0f + d)), ceilf(graw * (1.0f + d))));
+    bool safe = n_lo == n_hi;
+    if (!photon)
+        safe = safe && emission_piece(b * (1.0f - 1e-5f)) == emission_piece(b * (1.0f + 1e-5f));
     N = fminf(N, 1073741824.0f);  // 2^30: keeps the 32-bit sub-step counter from wrapping
     pl.N = (uint32_t)N;
-    pl.h = t_rem / (double)pl.N;
-    pl.c_h = P.K * (float)pl.h * inv_eps;
+    pl.safe = safe;
+    pl.h = T / (ticks_t)pl.N;
+    pl.c_h = P.K_tick * (float)pl.h * inv_eps;
     pl.T = squeeze_threshold(squeeze_bound(sqz_e, sqz_p, photon, b, pl.c_h, b23));
     return pl;
+}
+
+// chi and the plan of a particle: binary32 chi when it is well conditioned and
+// the plan is safe, otherwise chi in float-float (and the plan again).
+__device__ __forceinline__ Plan plan_particle(const StepParams& P, const float* __restrict__ sqz_e,
+                                              const float* __restrict__ sqz_p, bool photon,
+                                              float px, float py, float pz, float Ex, float Ey,
+                                              float Ez, float Bx, float By, float Bz, ticks_t T,
+                                              float* chi_out, float* eps_out) {
+    bool wc;
+    float eps;
+    float chi = chi_f32(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps, &wc);
+    Plan pl;
+    if (wc && eps > 0.0f) {
+        pl = make_plan(P, sqz_e, sqz_p, photon, chi, eps, T);
+        if (pl.safe) {
+            *chi_out = chi;
+            *eps_out = eps;
+            return pl;
+        }
+    }
+    chi = chi_ff(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps);
+    *chi_out = chi;
+    *eps_out = eps;
+    if (!(eps > 0.0f)) {
+        pl.N = 0;
+        return pl;
+    }
+    return make_plan(P, sqz_e, sqz_p, photon, chi, eps, T);
 }
 
 // Acceptance function of Algorithm 1 (emission, delta = x^3, Eq. 1):
 //   3 x^2 P(x^3) = (c b / x) [(1 - delta) F(z) + delta^2 G(z)],  z = delta / (b (1-delta)).
 // Algorithm 2 (pair, delta = x, Eq. 2 with the positive bracket):
 //   P_p = (c b / 3) [G(z) - delta (1 - delta) F(z)],  z = 1 / (b delta (1 - delta)).
-__device__ __forceinline__ float acceptance(const float4* __restrict__ tbl, bool photon, float b,
+__device__ __forceinline__ float acceptance(const SynTable& tbl, bool photon, float b,
                                             float c_h, float x, float* delta_out) {
     float F, G;
     if (!photon) {
         const float d = x * x * x;
-        const float omd = 1.0f - d;
+        const float omd = (1.0f - x) * fmaf(x, x + 1.0f, 1.0f);  // 1 - x^3 without cancellation
         const float z = d / (b * omd);
         synchrotron_FG(tbl, z, F, G);
         *delta_out = d;

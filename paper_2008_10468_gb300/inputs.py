@@ -6,13 +6,16 @@ none of the event generator's arithmetic.  The recipes stand in for the
 laser-plasma cascade workloads of the paper (Sec. 3.1.2), whose datasets are
 not public; every draw is from numpy's seeded PCG64 generator.
 
-Field geometry: every particle sees a crossed field E = E0 y^, B = E0 z^ with
-a per-particle (or per-cell) amplitude E0.  For that geometry a particle of
-momentum p (energy eps) has eps*E + p x B = E0 (p_y, eps - p_x, 0) and
-p.E = E0 p_y, so its quantum parameter is E0 (eps - p_x) / E_s.  The amplitude
-is set from a target value with that closed form; eps - p_x is evaluated as
-(eps^2 - p_x^2) / (eps + p_x) to avoid cancellation for particles moving
-along +x.
+Field geometry.  In the particle populations every particle meets a local
+crossed field head-on, as an electron beam meets a laser pulse: with n = p/|p|
+and a random unit vector e1 perpendicular to n, E = E0 e1 and
+B = -E0 (n x e1), so eps*E + p x B = (eps + |p|) E0 e1 and p.E = 0.  The
+quantum parameter is then (eps + |p|) E0 / E_s, and the amplitude E0 is set
+from the target value with this closed form.  Recoil lowers |p| and with it
+chi, so no particle runs away; amplitudes stay within a few times 10^4
+m c omega / e.  In the cascade batch every cell has one crossed field
+E = E0 y^, B = E0 z^ and isotropic particles, where the same closed form reads
+chi = E0 (eps - p_x) / E_s.
 """
 import numpy as np
 
@@ -44,24 +47,29 @@ def _isotropic(rng, n):
     return mu, s * np.cos(phi), s * np.sin(phi)
 
 
-def _crossed_amplitude(p, eps, chi_target):
-    """E0 giving chi_target for momentum p (n,3) and energy eps in E = E0 y^, B = E0 z^."""
-    px = p[:, 0]
-    perp2 = p[:, 1] ** 2 + p[:, 2] ** 2
-    # eps - p_x = (eps^2 - p_x^2) / (eps + p_x), eps^2 - p_x^2 = (eps^2 - p^2) + perp^2
-    rest = eps * eps - (px * px + perp2)          # 1 for e+-, 0 for photons
-    rest = np.where(np.abs(rest) < 0.5, 0.0, 1.0)
-    lead = np.where(px > 0, (rest + perp2) / (eps + px), eps - px)
-    return chi_target * E_S / lead
+def _head_on_fields(rng, p, eps, chi_target):
+    """E, B (n,3) of a crossed field met head-on by momentum p with target chi."""
+    n = p / np.linalg.norm(p, axis=1, keepdims=True)
+    # a unit vector perpendicular to n, at a random angle around n
+    a = np.where(np.abs(n[:, :1]) < 0.9, [[1.0, 0.0, 0.0]], [[0.0, 1.0, 0.0]])
+    u = np.cross(a, n)
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    v = np.cross(n, u)
+    phi = rng.uniform(0.0, 2.0 * np.pi, len(p))[:, None]
+    e1 = np.cos(phi) * u + np.sin(phi) * v
+    E0 = chi_target * E_S / (eps + np.linalg.norm(p, axis=1))
+    E = E0[:, None] * e1
+    B = -E0[:, None] * np.cross(n, e1)
+    return E, B
 
 
-def _assemble(p, E0, types, ids, weight=None):
+def _assemble(p, E, B, types, ids, weight=None):
     n = p.shape[0]
     f32 = np.float32
     out = {
         "px": p[:, 0].astype(f32), "py": p[:, 1].astype(f32), "pz": p[:, 2].astype(f32),
-        "Ex": np.zeros(n, f32), "Ey": E0.astype(f32), "Ez": np.zeros(n, f32),
-        "Bx": np.zeros(n, f32), "By": np.zeros(n, f32), "Bz": E0.astype(f32),
+        "Ex": E[:, 0].astype(f32), "Ey": E[:, 1].astype(f32), "Ez": E[:, 2].astype(f32),
+        "Bx": B[:, 0].astype(f32), "By": B[:, 1].astype(f32), "Bz": B[:, 2].astype(f32),
         "w": np.ones(n, f32) if weight is None else weight.astype(f32),
         "id": ids.astype(np.uint64), "type": types.astype(np.uint8),
     }
@@ -69,21 +77,22 @@ def _assemble(p, E0, types, ids, weight=None):
 
 
 def uniform_field_electrons(n, seed, gamma=(1e2, 1e4), chi=(0.1, 10.0), ptype=TYPE_ELECTRON):
-    """Static uniform crossed field, gamma and chi log-uniform, isotropic directions.
+    """Static crossed field (|E| = |B|, B perpendicular to E) met head-on;
+    gamma and chi log-uniform, isotropic directions.
 
-    Default ranges: 1e5 electrons, gamma in [1e2, 1e4], chi in [0.1, 10]."""
+    Default ranges: gamma in [1e2, 1e4], chi in [0.1, 10]."""
     rng = np.random.Generator(np.random.PCG64(seed))
     g = _loguniform(rng, gamma[0], gamma[1], n)
     c = _loguniform(rng, chi[0], chi[1], n)
     mu, sy, sz = _isotropic(rng, n)
     pm = np.sqrt(g * g - 1.0)
     p = np.stack([pm * mu, pm * sy, pm * sz], axis=1)
-    # amplitude from the binary32 momenta so that chi is close to its target
+    # fields from the binary32 momenta so that chi is close to its target
     p32 = p.astype(np.float32).astype(np.float64)
     eps = np.sqrt(1.0 + np.sum(p32 * p32, axis=1))
-    E0 = _crossed_amplitude(p32, eps, c)
+    E, B = _head_on_fields(rng, p32, eps, c)
     types = np.full(n, ptype, dtype=np.uint8)
-    return _assemble(p32, E0, types, np.arange(n, dtype=np.uint64))
+    return _assemble(p32, E, B, types, np.arange(n, dtype=np.uint64))
 
 
 def clumped_mixed(n, seed, hot_fraction=0.01, hot_chi=(10.0, 100.0), hot_gamma=(3e3, 3e4),
@@ -112,8 +121,8 @@ def clumped_mixed(n, seed, hot_fraction=0.01, hot_chi=(10.0, 100.0), hot_gamma=(
     p32 = p.astype(np.float32).astype(np.float64)
     p2 = np.sum(p32 * p32, axis=1)
     eps = np.where(photon, np.sqrt(p2), np.sqrt(1.0 + p2))
-    E0 = _crossed_amplitude(p32, eps, c)
-    return _assemble(p32, E0, types, np.arange(n, dtype=np.uint64))
+    E, B = _head_on_fields(rng, p32, eps, c)
+    return _assemble(p32, E, B, types, np.arange(n, dtype=np.uint64))
 
 
 def cascade_cells(n_cells, seed, n_min=1, n_max=65536, exponent=-1.5,
@@ -139,8 +148,11 @@ def cascade_cells(n_cells, seed, n_min=1, n_max=65536, exponent=-1.5,
     pm = np.sqrt(g * g - 1.0)
     p = np.stack([pm * mu, pm * sy, pm * sz], axis=1).astype(np.float32).astype(np.float64)
     E0 = A[cell]
+    zero = np.zeros(n)
+    E = np.stack([zero, E0, zero], axis=1)
+    B = np.stack([zero, zero, E0], axis=1)
     types = np.full(n, TYPE_ELECTRON, dtype=np.uint8)
-    return _assemble(p, E0, types, np.arange(n, dtype=np.uint64)), cell
+    return _assemble(p, E, B, types, np.arange(n, dtype=np.uint64)), cell
 
 
 def sweep_points(n, seed, lo=1e-4, hi=50.0):

@@ -19,6 +19,8 @@ QED_OK, QED_ERR_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY, QED_ERR_TIMEOUT, QED_ERR_ST
 PROC_EMISSION, PROC_PAIR = 1, 2
 ELECTRON, POSITRON, PHOTON, REMOVED = 0, 1, 2, 3
 FLOAT_FIELDS = ("px", "py", "pz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "w")
+KERNEL_KINDS = ("sweep", "generate", "plan", "cold", "hot", "control")
+SPECTRUM_BINS, SPECTRUM_LOG10_MIN, SPECTRUM_LOG10_MAX = 240, -4, 8
 
 
 class QEDError(RuntimeError):
@@ -31,7 +33,7 @@ class Config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("dt_periods", C.c_double), ("lambda_m", C.c_double),
                 ("p_max", C.c_float), ("pair_bound_coeff", C.c_float),
                 ("process_mask", C.c_uint32), ("cascade_in_step", C.c_int32),
-                ("recoil", C.c_int32), ("max_passes", C.c_int32)]
+                ("recoil", C.c_int32), ("max_passes", C.c_int32), ("drain_chi", C.c_float)]
 
 
 class Particles(C.Structure):
@@ -44,7 +46,7 @@ class StepStats(C.Structure):
                 ("children", C.c_uint64), ("guard_hits", C.c_uint64), ("plans", C.c_uint64),
                 ("candidates", C.c_uint64), ("max_N", C.c_uint32), ("status", C.c_int32),
                 ("required_capacity", C.c_int64), ("count", C.c_int64), ("passes", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("substeps_warp", C.c_uint64)]
 
 
 EVENT_DTYPE = np.dtype([("parent_id", np.uint64), ("child0", np.uint64), ("child1", np.uint64),
@@ -82,6 +84,20 @@ def lib():
         L.qed_read_stats.restype = st
         L.qed_set_event_log.argtypes = [vp, vp, i64, vp]
         L.qed_set_event_log.restype = st
+        L.qed_compact.argtypes = [vp, C.POINTER(Particles), C.POINTER(i64)]
+        L.qed_compact.restype = st
+        L.qed_read_spectrum.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.c_int]
+        L.qed_read_spectrum.restype = st
+        L.qed_graph_capture.argtypes = [vp, C.POINTER(Particles), u64, C.c_int]
+        L.qed_graph_capture.restype = st
+        L.qed_graph_launch.argtypes = [vp]
+        L.qed_graph_launch.restype = st
+        L.qed_graph_read_stats.argtypes = [vp, C.POINTER(StepStats), C.c_int]
+        L.qed_graph_read_stats.restype = st
+        L.qed_profile_enable.argtypes = [vp, C.c_int]
+        L.qed_profile_enable.restype = st
+        L.qed_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
+        L.qed_profile_read.restype = st
         _lib = L
     return _lib
 
@@ -157,7 +173,7 @@ class Context:
 
     def __init__(self, seed=20081046, dt=0.1, lambda_m=1e-6, p_max=0.01, pair_coeff=0.1,
                  process_mask=PROC_EMISSION | PROC_PAIR, cascade=True, recoil=True,
-                 max_passes=64, stream=None):
+                 max_passes=64, drain_chi=0.0, stream=None):
         L = lib()
         cfg = Config()
         L.qed_config_default(C.byref(cfg))
@@ -170,6 +186,7 @@ class Context:
         cfg.cascade_in_step = int(bool(cascade))
         cfg.recoil = int(bool(recoil))
         cfg.max_passes = int(max_passes)
+        cfg.drain_chi = float(drain_chi)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -238,6 +255,47 @@ class Context:
             return stats_dict(s)
         self._check(lib().qed_event_step(self._h, C.byref(p), int(step), None))
         return None
+
+    def compact(self, store):
+        """Squeeze removed rows out of the store; returns the rows removed."""
+        p = store.struct()
+        r = C.c_int64()
+        self._check(lib().qed_compact(self._h, C.byref(p), C.byref(r)))
+        return int(r.value)
+
+    def read_spectrum(self, reset=False):
+        out = (C.c_double * SPECTRUM_BINS)()
+        self._check(lib().qed_read_spectrum(self._h, out, SPECTRUM_BINS, int(bool(reset))))
+        return np.array(out[:])
+
+    def graph_capture(self, store, first_step, nsteps):
+        """Record nsteps global steps on `store` as one CUDA graph."""
+        self._graph_store = store
+        p = store.struct()
+        self._check(lib().qed_graph_capture(self._h, C.byref(p), int(first_step), int(nsteps)))
+        self._graph_steps = int(nsteps)
+
+    def graph_launch(self):
+        self._check(lib().qed_graph_launch(self._h))
+
+    def graph_read_stats(self):
+        """Per-step statistics of the last graph launch (list of dicts)."""
+        n = self._graph_steps
+        out = (StepStats * n)()
+        st = lib().qed_graph_read_stats(self._h, out, n)
+        if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_STATE):
+            self._check(st)
+        return [stats_dict(out[k]) for k in range(n)]
+
+    def profile(self, enable=True):
+        self._check(lib().qed_profile_enable(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{kind: (ms, launches)} since the last read, for kinds in KERNEL_KINDS."""
+        ms = (C.c_double * 8)()
+        ln = (C.c_int64 * 8)()
+        self._check(lib().qed_profile_read(self._h, ms, ln, 8))
+        return {name: (float(ms[i]), int(ln[i])) for i, name in enumerate(KERNEL_KINDS)}
 
     def read_stats(self):
         s = StepStats()

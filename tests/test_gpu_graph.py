@@ -1,0 +1,125 @@
+"""Store compaction, photon drain and the multi-step CUDA graph.  GPU only."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2008_10468_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2008_10468_gb300 import qed  # noqa: E402
+
+
+def _sorted(store_np):
+    o = np.argsort(store_np["id"])
+    return {k: v[o] for k, v in store_np.items()}
+
+
+@pytest.mark.parametrize("n,frac", [(0, 0.0), (1, 1.0), (4095, 0.3), (4097, 0.0), (50001, 0.5),
+                                    (12288, 1.0)])
+def test_compaction_is_stable_and_exact(n, frac):
+    ctx = qed.Context()
+    arr = I.clumped_mixed(max(n, 1), 6)
+    arr = {k: v[:n] for k, v in arr.items()}
+    rng = np.random.default_rng(n)
+    dead = rng.random(n) < frac
+    arr["type"] = np.where(dead, 3, arr["type"]).astype(np.uint8)
+    store = qed.ParticleStore.from_numpy(arr, capacity=n + 9000)
+    removed = ctx.compact(store)
+    assert removed == int(dead.sum())
+    got = store.to_numpy()
+    keep = ~dead
+    for k in arr:
+        np.testing.assert_array_equal(got[k], arr[k][keep])
+
+
+def test_photon_drain_fills_spectrum():
+    arr = I.clumped_mixed(20000, 9)
+    cf = O.make_config(1)
+    chi = np.array([O.chi((arr["px"][i], arr["py"][i], arr["pz"][i]),
+                          (arr["Ex"][i], arr["Ey"][i], arr["Ez"][i]),
+                          (arr["Bx"][i], arr["By"][i], arr["Bz"][i]), photon=True)[0]
+                    for i in range(20000)])
+    photon = arr["type"] == 2
+    thr = 5e-3
+    drained = photon & (chi < thr)
+    margin = photon & (np.abs(chi / thr - 1) < 1e-5)   # binary32 chi may fall either side
+    ctx = qed.Context(drain_chi=thr)
+    store = qed.ParticleStore.from_numpy(arr, capacity=20000)
+    ctx.read_spectrum(reset=True)
+    removed = ctx.compact(store)
+    assert abs(removed - drained.sum()) <= margin.sum()
+    spec = ctx.read_spectrum()
+    assert spec.sum() == pytest.approx(float(arr["w"][drained].sum()), abs=margin.sum() + 1e-6)
+    energy = np.sqrt(arr["px"] ** 2 + arr["py"] ** 2 + arr["pz"] ** 2)[drained]
+    h, _ = np.histogram(np.log10(energy), bins=qed.SPECTRUM_BINS,
+                        range=(qed.SPECTRUM_LOG10_MIN, qed.SPECTRUM_LOG10_MAX))
+    assert np.abs(spec - h).sum() <= 2 * margin.sum() + 2  # bin-edge rounding only
+
+
+def _eager_steps(arr, cap, first, k, **cfg):
+    ctx = qed.Context(**cfg)
+    store = qed.ParticleStore.from_numpy(arr, capacity=cap)
+    stats = []
+    for j in range(k):
+        st = ctx.event_step(store, first + j)
+        ctx.compact(store)
+        st["count"] = store.n()
+        stats.append(st)
+    return store.to_numpy(), stats
+
+
+def _graph_steps(arr, cap, first, k, **cfg):
+    ctx = qed.Context(**cfg)
+    store = qed.ParticleStore.from_numpy(arr, capacity=cap)
+    ctx.graph_capture(store, first, k)
+    ctx.graph_launch()
+    stats = ctx.graph_read_stats()
+    return store.to_numpy(), stats, ctx, store
+
+
+def test_graph_equals_eager_steps():
+    arr = I.clumped_mixed(3000, 21, hot_fraction=0.03)
+    cap = 400000
+    e_store, e_stats = _eager_steps(arr, cap, 50, 5, seed=99)
+    g_store, g_stats, ctx, store = _graph_steps(arr, cap, 50, 5, seed=99)
+    for a, b in zip(e_stats, g_stats):
+        for k in ("substeps", "emissions", "pairs", "children", "plans", "candidates", "max_N",
+                  "passes", "status", "count"):
+            assert a[k] == b[k], (k, a[k], b[k])
+    e, g = _sorted(e_store), _sorted(g_store)
+    for k in e:
+        np.testing.assert_array_equal(e[k], g[k])
+    # a second launch continues from the evolved store with the same step indices
+    ctx.graph_launch()
+    again = ctx.graph_read_stats()
+    assert all(s["status"] == 0 for s in again)
+    assert again[0]["count"] != g_stats[0]["count"] or again[0]["substeps"] != g_stats[0]["substeps"]
+
+
+def test_graph_capacity_overflow_is_sticky():
+    arr = I.uniform_field_electrons(2000, 20081047)
+    g_store, stats, ctx, store = _graph_steps(arr, 2300, 0, 4, process_mask=1, cascade=False)
+    assert stats[0]["status"] == qed.QED_ERR_CAPACITY
+    assert stats[0]["required_capacity"] > 2300
+    for s in stats[1:]:
+        assert s["status"] == qed.QED_ERR_CAPACITY and s["substeps"] == 0
+    # the context is still usable: a new capture on a roomy store works
+    store2 = qed.ParticleStore.from_numpy(I.uniform_field_electrons(100, 1), capacity=100000)
+    ctx.graph_capture(store2, 0, 2)
+    ctx.graph_launch()
+    assert all(s["status"] == 0 for s in ctx.graph_read_stats())
+
+
+def test_cascade_batch_graph_small():
+    arr, cell = I.cascade_cells(128, 20081050, n_max=4096)
+    n = len(arr["px"])
+    _, stats, ctx, store = _graph_steps(arr, n * 40, 0, 10, seed=20081050, drain_chi=0.05)
+    assert all(s["status"] == 0 for s in stats), stats
+    assert stats[-1]["count"] > 0
+    assert sum(s["substeps"] for s in stats) > n
+    assert ctx.read_spectrum().sum() > 0

@@ -222,6 +222,7 @@ def test_event_step_pairs_only():
 def _sampled_full_size(arr, capacity, seed, mask, roots, log_cap):
     g_store, g_st, g_ev = _run_gpu(arr, 0, capacity, log_cap=log_cap, seed=seed,
                                    process_mask=mask, cascade=True)
+    print("full-size step:", g_st)
     assert g_st["status"] == 0
     sub = I.subset(arr, roots)
     cf = O.make_config(seed, process_mask=mask, cascade=1)
@@ -249,7 +250,8 @@ def test_event_step_clumped_full_size_sampled():
     cold = rng.choice(np.concatenate([np.arange(0, h0), np.arange(h0 + n_hot, n)]), 40,
                       replace=False)
     roots = np.sort(np.concatenate([hot, cold]))
-    _sampled_full_size(arr, n + (n >> 2), 20081049, 3, roots, 1 << 23)
+    # the hot clump cascades within the step (~85 children per hot particle)
+    _sampled_full_size(arr, n + (1 << 25), 20081049, 3, roots, 1 << 25)
 
 
 # --------------------------------------------------------------------------
