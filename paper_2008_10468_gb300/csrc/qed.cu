@@ -38,12 +38,14 @@ constexpr double kPiD = 3.14159265358979323846;
 
 constexpr uint32_t kHotMin = 64;       // plans with N >= kHotMin go to the warp path
 
-// Minimum resident blocks per SM requested from the register allocator.
+// Minimum resident blocks per SM requested from the register allocator:
+// 3 x 256 and 6 x 128 threads keep both event kernels at 80 registers
+// (24 warps per SM) without spills.
 #ifndef QED_COLD_MIN_BLOCKS
-#define QED_COLD_MIN_BLOCKS 1
+#define QED_COLD_MIN_BLOCKS 3
 #endif
 #ifndef QED_HOT_MIN_BLOCKS
-#define QED_HOT_MIN_BLOCKS 1
+#define QED_HOT_MIN_BLOCKS 6
 #endif
 constexpr int kColdThreads = 256;
 constexpr int kHotThreads = 128;
@@ -68,7 +70,7 @@ struct DevCtl {
 struct HotItem {
     uint32_t idx;
     uint32_t s;
-    ticks_t t_rem;   // remaining time in ticks (2^62 per global step)
+    ftime t_rem;     // remaining time (periods)
 };
 
 struct DevParticles {
@@ -80,16 +82,18 @@ struct DevParticles {
 };
 
 struct Scratch {
-    ticks_t* t_rem;         // remaining time (ticks) of appended children (capacity)
+    ftime* t_rem;           // remaining time of appended children (capacity)
     HotItem* hot;           // queue of warp-path particles (capacity)
     qed_event_record* log;  // optional
     long long log_cap;
     long long* log_count;
 };
 
+// Per-thread counters of one launch (32-bit: a thread's share of one launch
+// stays far below 2^32); summed per warp and added to the control block.
 struct Stats {
-    unsigned long long substeps = 0, emissions = 0, pairs = 0, children = 0, guard = 0, plans = 0,
-                       cand = 0, warp_substeps = 0;
+    unsigned int substeps = 0, emissions = 0, pairs = 0, children = 0, guard = 0, plans = 0,
+                 cand = 0, warp_substeps = 0;
     unsigned int max_N = 0;
 };
 
@@ -108,7 +112,7 @@ __device__ void flush_stats(const Stats& st, DevCtl* ctl) {
     const unsigned long long a = warp_sum(st.substeps), b = warp_sum(st.emissions),
                              c = warp_sum(st.pairs), d = warp_sum(st.children),
                              e = warp_sum(st.guard), f = warp_sum(st.plans), g = warp_sum(st.cand),
-                             h = warp_sum(st.warp_substeps);
+                             h = warp_sum(st.warp_substeps);  // 64-bit sums of 32-bit counters
     const unsigned int m = warp_max(st.max_N);
     if ((threadIdx.x & 31) == 0) {
         if (a) atomicAdd(&ctl->substeps, a);
@@ -224,9 +228,10 @@ __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParam
                             (photon ? (SP.process_mask & QED_PROC_PAIR)
                                     : (SP.process_mask & QED_PROC_EMISSION));
         float eps;
+        const ftime T0{(float)SP.dt, (float)(SP.dt - (double)(float)SP.dt)};
         const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, P.px[i], P.py[i], P.pz[i],
-                                      P.Ex[i], P.Ey[i], P.Ez[i], P.Bx[i], P.By[i], P.Bz[i],
-                                      kTicksPerStep, &chi, &eps);
+                                      P.Ex[i], P.Ey[i], P.Ez[i], P.Bx[i], P.By[i], P.Bz[i], T0,
+                                      &chi, &eps);
         if (active && eps > 0.0f) N = pl.N;
         if (chi_out) chi_out[i] = chi;
         if (N_out) N_out[i] = N;
@@ -282,7 +287,7 @@ __device__ __forceinline__ long long reserve_rows(const DevParticles& P, DevCtl*
 
 __device__ __forceinline__ void write_child(const DevParticles& P, const Scratch& S, long long j,
                                             long long parent, float px, float py, float pz,
-                                            uint64_t id, uint8_t type, ticks_t t_rem) {
+                                            uint64_t id, uint8_t type, ftime t_rem) {
     P.px[j] = px;
     P.py[j] = py;
     P.pz[j] = pz;
@@ -300,9 +305,9 @@ __device__ __forceinline__ void write_child(const DevParticles& P, const Scratch
 
 // Apply an accepted event (recoil or decay, children, log).  Returns true if
 // the particle was removed (photon decay).
-__device__ bool apply_event(const DevParticles& P, const Scratch& S, const StepParams& SP,
+__device__ __noinline__ bool apply_event(const DevParticles& P, const Scratch& S, const StepParams& SP,
                             DevCtl* ctl, long long i, uint64_t id, bool photon, float x,
-                            float eps, float chi, uint32_t s, ticks_t t_after, PState& st,
+                            float eps, float chi, uint32_t s, ftime t_after, PState& st,
                             Stats& stats, bool write_rows, bool warp_caller) {
     const uint4 cid = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), SP.step, s),
                                     (uint32_t)SP.seed ^ kChildKeyLo,
@@ -379,7 +384,7 @@ __device__ __forceinline__ bool process_enabled(const StepParams& SP, bool photo
 }
 
 __device__ __forceinline__ void push_hot(const Scratch& S, DevCtl* ctl, long long i, uint32_t s,
-                                         ticks_t t_rem) {
+                                         ftime t_rem) {
     const unsigned int k = atomicAdd(&ctl->hot_tail, 1u);
     HotItem it;
     it.idx = (uint32_t)i;
@@ -409,8 +414,8 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
         if (type > QED_PHOTON) continue;
         const bool photon = type == QED_PHOTON;
         if (!process_enabled(SP, photon)) continue;
-        ticks_t t_rem = first_pass ? kTicksPerStep : S.t_rem[i];
-        if (t_rem == 0) continue;
+        ftime t_rem = first_pass ? SP.t_step : S.t_rem[i];
+        if (!time_positive(t_rem)) continue;
         const uint64_t id = P.id[i];
         PState st{P.px[i], P.py[i], P.pz[i]};
         const float Ex = P.Ex[i], Ey = P.Ey[i], Ez = P.Ez[i];
@@ -419,7 +424,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
         uint32_t s = 0;
         uint4 blk = make_uint4(0, 0, 0, 0);
         uint32_t blk_idx = 0xffffffffu;
-        while (t_rem > 0) {
+        while (time_positive(t_rem)) {
             float eps, chi;
             const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
                                           Ey, Ez, Bx, By, Bz, t_rem, &chi, &eps);
@@ -436,7 +441,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                 }
                 stats.plans--;  // the warp path re-plans and counts it
                 push_hot(S, ctl, i, s, t_rem);
-                t_rem = 0;
+                t_rem = ftime{0.0f, 0.0f};
                 break;
             }
             bool event = false;
@@ -456,8 +461,8 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                     float delta;
                     const float Pa = acceptance(sm.syn, photon, pl.b, pl.c_h, x, &delta);
                     if (u01(ry) < Pa) {
-                        const ticks_t t_after =
-                            (k + 1 == pl.N) ? 0ull : t_rem - (ticks_t)(k + 1) * pl.h;
+                        const ftime t_after = (k + 1 == pl.N) ? ftime{0.0f, 0.0f}
+                                                              : time_sub_mul(t_rem, k + 1, pl.h);
                         removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, s,
                                               t_after, st, stats, true, false);
                         changed = true;
@@ -470,7 +475,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                 ++s;
             }
             if (removed) break;
-            if (!event) t_rem = 0;
+            if (!event) t_rem = ftime{0.0f, 0.0f};
         }
         if (removed) {
             P.type[i] = QED_REMOVED;
@@ -493,7 +498,7 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
     const unsigned int tail = ctl->hot_tail;
     const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
     Stats stats;              // counted on lane 0 only
-    unsigned long long cand = 0;  // candidates, counted per lane
+    unsigned int cand = 0;    // candidates, counted per lane
     while (true) {
         unsigned int q = 0;
         if (lane == 0) q = atomicAdd(&ctl->hot_head, 1u);
@@ -508,9 +513,9 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
         const float Ex = P.Ex[i], Ey = P.Ey[i], Ez = P.Ez[i];
         const float Bx = P.Bx[i], By = P.By[i], Bz = P.Bz[i];
         uint32_t s = it.s;
-        ticks_t t_rem = it.t_rem;
+        ftime t_rem = it.t_rem;
         bool removed = false, changed = false;
-        while (t_rem > 0) {
+        while (time_positive(t_rem)) {
             float eps, chi;
             const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
                                           Ey, Ez, Bx, By, Bz, t_rem, &chi, &eps);
@@ -555,8 +560,8 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
                 const float x = __shfl_sync(0xffffffffu, xo, pos >> 1);
                 const uint32_t k_ev = kdone + (s_ev - sb);
                 if (lane == 0) stats.substeps += s_ev - sb + 1;
-                const ticks_t t_after =
-                    (k_ev + 1 == pl.N) ? 0ull : t_rem - (ticks_t)(k_ev + 1) * pl.h;
+                const ftime t_after = (k_ev + 1 == pl.N) ? ftime{0.0f, 0.0f}
+                                                         : time_sub_mul(t_rem, k_ev + 1, pl.h);
                 removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, s_ev, t_after,
                                       st, stats, lane == 0, true);
                 changed = true;
@@ -566,7 +571,7 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
                 break;
             }
             if (removed) break;
-            if (!event) t_rem = 0;
+            if (!event) t_rem = ftime{0.0f, 0.0f};
         }
         if (lane == 0) {
             if (removed) P.type[i] = QED_REMOVED;
@@ -825,7 +830,7 @@ struct qed_ctx {
     int sms;
     DevCtl* d_ctl;
     DevCtl* h_ctl;          // pinned
-    ticks_t* d_trem;
+    ftime* d_trem;
     HotItem* d_hot;
     long long scratch_cap;
     qed_event_record* log;
@@ -877,7 +882,8 @@ StepParams make_params(const qed_config& c, uint64_t step) {
     const double period = c.lambda_m / kCLight;
     const double R = kAlpha / kTauC * period;                 // 1 / period
     P.K = (float)(1.7320508075688772 / kPiD * R);
-    P.K_tick = (float)(1.7320508075688772 / kPiD * R * c.dt_periods / (double)kTicksPerStep);
+    P.t_step.hi = (float)c.dt_periods;
+    P.t_step.lo = (float)(c.dt_periods - (double)P.t_step.hi);
     const double omega = 2.0 * kPiD * kCLight / c.lambda_m;
     P.inv_Es = (float)(omega * kTauC);                        // 1 / E_s in code units
     P.p_max = c.p_max;
@@ -912,7 +918,7 @@ qed_status ensure_scratch(qed_ctx* ctx, long long cap) {
     ctx->d_trem = nullptr;
     ctx->d_hot = nullptr;
     ctx->scratch_cap = 0;
-    QED_CUDA(ctx, cudaMalloc(&ctx->d_trem, sizeof(ticks_t) * cap));
+    QED_CUDA(ctx, cudaMalloc(&ctx->d_trem, sizeof(ftime) * cap));
     QED_CUDA(ctx, cudaMalloc(&ctx->d_hot, sizeof(HotItem) * cap));
     ctx->scratch_cap = cap;
     return QED_OK;
@@ -1446,3 +1452,4 @@ size_t qed_abi_struct_size(const char* name) {
 }
 
 }  // extern "C"
+

@@ -144,10 +144,11 @@ __device__ __forceinline__ float chi_f32(bool photon, float px, float py, float 
 constexpr int kSynCoef = 2 * (QED_SYN_DEG + 1);   // F and G coefficients per piece
 constexpr int kSynStride = 32;                     // pieces padded to one bank row
 
-// Shared-memory form of the table: coefficient-major, so that the lanes of a
-// warp reading coefficient j of different pieces hit different banks.
+// Shared-memory form of the table: c[j][p] = (F_j, G_j) of piece p.  Lanes of a
+// warp reading power j of different pieces hit different banks (pieces p and
+// p + 16 share a bank pair), and one 64-bit load serves both functions.
 struct SynTable {
-    float c[kSynCoef][kSynStride];
+    float2 c[QED_SYN_DEG + 1][kSynStride];
     unsigned int lam_mask;   // bit p set: piece p carries the exp(-x) envelope
 };
 
@@ -160,12 +161,13 @@ __device__ __forceinline__ void synchrotron_FG(const SynTable& tb, float x, floa
     const int piece = small ? 0 : k - QED_SYN_KMIN + 1;
     float t = small ? u * u : l2 - (float)k;
     t = fminf(t, 1.02f);
-    float pf = tb.c[QED_SYN_DEG][piece];
-    float pg = tb.c[2 * QED_SYN_DEG + 1][piece];
+    float2 c = tb.c[QED_SYN_DEG][piece];
+    float pf = c.x, pg = c.y;
 #pragma unroll
     for (int j = QED_SYN_DEG - 1; j >= 0; --j) {
-        pf = fmaf(pf, t, tb.c[j][piece]);
-        pg = fmaf(pg, t, tb.c[QED_SYN_DEG + 1 + j][piece]);
+        c = tb.c[j][piece];
+        pf = fmaf(pf, t, c.x);
+        pg = fmaf(pg, t, c.y);
     }
     const float lam = ((tb.lam_mask >> piece) & 1u) ? 1.0f : 0.0f;
     const float env = u * expf(-lam * x);
@@ -177,9 +179,11 @@ __device__ __forceinline__ void synchrotron_FG(const SynTable& tb, float x, floa
 // Copy the synchrotron table into shared memory (call with all threads of
 // the block, then __syncthreads()).
 __device__ __forceinline__ void stage_syn_table(SynTable& tb) {
-    for (int i = threadIdx.x; i < kSynCoef * kSynStride; i += blockDim.x) {
+    for (int i = threadIdx.x; i < (QED_SYN_DEG + 1) * kSynStride; i += blockDim.x) {
         const int j = i / kSynStride, p = i % kSynStride;
-        tb.c[j][p] = p < QED_SYN_NPIECE ? qed_syn_table[p][j] : 0.0f;
+        tb.c[j][p] = p < QED_SYN_NPIECE
+                         ? make_float2(qed_syn_table[p][j], qed_syn_table[p][QED_SYN_DEG + 1 + j])
+                         : make_float2(0.0f, 0.0f);
     }
     if (threadIdx.x == 0) {
         unsigned int m = 0;
@@ -208,20 +212,44 @@ __device__ __forceinline__ float bound_emission(float b, float c) {
 // x -> 0 limit of 3 x^2 P(x^3) over c b^{2/3}:  4 pi / (sqrt3 Gamma(1/3) 2^{1/3}).
 constexpr float kSmallF = 2.14952824153447863f;
 
-// Remaining time of a particle within the global step, as an exact fixed-point
-// count: one global step is 2^62 ticks.  Sub-step lengths are floor(T / N)
-// ticks and the time after sub-step k of a plan is T - (k + 1) h, with the
-// last sub-step ending the plan exactly; integer arithmetic keeps the
-// partition exact without FP64 (whose rate on this GPU is 1/64 of FP32).
-using ticks_t = unsigned long long;
-constexpr ticks_t kTicksPerStep = 1ull << 62;
+// Remaining time of a particle within the global step, in laser periods, as a
+// float-float pair (about 48 significant bits).  Sub-steps have length
+// h = t / N and the time after sub-step k of a plan is t - (k + 1) h, the
+// last sub-step ending the plan exactly.  The pair keeps this accumulator on
+// the FP32 pipe: FP64, and 64-bit integer conversions and divisions (which
+// this GPU runs on its FP64 pipe, at 1/64 of the FP32 rate), stay off the
+// sub-step path.
+struct ftime {
+    float hi, lo;
+};
+
+__device__ __forceinline__ bool time_positive(ftime t) { return t.hi > 0.0f; }
+
+// t / N for an integer N >= 1, to float-float precision.
+__device__ __forceinline__ ftime time_div(ftime t, uint32_t N) {
+    const float n = (float)N;                 // exact for N <= 2^24; N <= 2^30 rounds
+    const float q = __fdiv_rn(t.hi, n);
+    // residual t - q n, exact products through FMA
+    const float p = __fmul_rn(q, n);
+    const float pe = __fmaf_rn(q, n, -p);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(t.hi, p), pe), t.lo);
+    const ff out = fast_two_sum(q, __fdiv_rn(r, n));
+    return {out.hi, out.lo};
+}
+
+// t - m h for an integer m.
+__device__ __forceinline__ ftime time_sub_mul(ftime t, uint32_t m, ftime h) {
+    const ff mh = ff_add(two_prod(h.hi, (float)m), ff{__fmul_rn(h.lo, (float)m), 0.0f});
+    const ff d = ff_add(ff{t.hi, t.lo}, ff_neg(mh));
+    return {d.hi, d.lo};
+}
 
 struct Plan {
     uint32_t N;      // sub-steps for the remaining time
     float b;         // 3 chi / 2
     float c_h;       // sqrt3 R h / (pi gamma) for one sub-step
     uint32_t T;      // squeeze threshold on (r >> 9): candidates have (r >> 9) < T
-    ticks_t h;       // sub-step length in ticks
+    ftime h;         // sub-step length (periods)
     bool guard;      // N raised by the validity guard
     bool safe;       // N cannot change within +-1e-5 (relative) of chi and f
 };
@@ -230,10 +258,10 @@ struct StepParams {
     uint64_t seed;
     double dt;           // global step (periods)
     float K;             // sqrt3 R / pi  (1 / period)
-    float K_tick;        // K dt / 2^62: the same per tick
     float inv_Es;        // 1 / Schwinger field (code units)
     float p_max;
     float pair_coeff;
+    ftime t_step;        // dt as float-float
     uint32_t step;       // global step index (Philox counter word 2)
     uint32_t process_mask;
     int recoil;
@@ -277,12 +305,12 @@ __device__ __forceinline__ int emission_piece(float b) {
 // than 2e-5 relative unless b crosses a piece boundary.
 __device__ __forceinline__ Plan make_plan(const StepParams& P, const float* __restrict__ sqz_e,
                                           const float* __restrict__ sqz_p, bool photon, float chi,
-                                          float eps, ticks_t T) {
+                                          float eps, ftime T) {
     constexpr float d = 2e-5f;
     Plan pl;
     pl.b = 1.5f * chi;
     const float inv_eps = 1.0f / eps;
-    const float c_rem = P.K_tick * (float)T * inv_eps;
+    const float c_rem = P.K * T.hi * inv_eps;
     const float b = pl.b;
     const float f = photon ? P.pair_coeff * c_rem * b : bound_emission(b, c_rem);
     const float q = f / P.p_max;
@@ -306,10 +334,29 @@ __device__ __forceinline__ Plan make_plan(const StepParams& P, const float* __re
     N = fminf(N, 1073741824.0f);  // 2^30: keeps the 32-bit sub-step counter from wrapping
     pl.N = (uint32_t)N;
     pl.safe = safe;
-    pl.h = T / (ticks_t)pl.N;
-    pl.c_h = P.K_tick * (float)pl.h * inv_eps;
+    pl.h = time_div(T, pl.N);
+    pl.c_h = P.K * pl.h.hi * inv_eps;
     pl.T = squeeze_threshold(squeeze_bound(sqz_e, sqz_p, photon, b, pl.c_h, b23));
     return pl;
+}
+
+// Slow path of plan_particle: chi in float-float, then the plan.  Kept out of
+// line so that the common path does not carry its registers.
+__device__ __noinline__ Plan plan_slow(const StepParams& P, const float* __restrict__ sqz_e,
+                                       const float* __restrict__ sqz_p, bool photon, float px,
+                                       float py, float pz, float Ex, float Ey, float Ez, float Bx,
+                                       float By, float Bz, ftime T, float* chi_out,
+                                       float* eps_out) {
+    float eps;
+    const float chi = chi_ff(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps);
+    *chi_out = chi;
+    *eps_out = eps;
+    Plan pl;
+    if (!(eps > 0.0f)) {
+        pl.N = 0;
+        return pl;
+    }
+    return make_plan(P, sqz_e, sqz_p, photon, chi, eps, T);
 }
 
 // chi and the plan of a particle: binary32 chi when it is well conditioned and
@@ -317,28 +364,21 @@ __device__ __forceinline__ Plan make_plan(const StepParams& P, const float* __re
 __device__ __forceinline__ Plan plan_particle(const StepParams& P, const float* __restrict__ sqz_e,
                                               const float* __restrict__ sqz_p, bool photon,
                                               float px, float py, float pz, float Ex, float Ey,
-                                              float Ez, float Bx, float By, float Bz, ticks_t T,
+                                              float Ez, float Bx, float By, float Bz, ftime T,
                                               float* chi_out, float* eps_out) {
     bool wc;
     float eps;
-    float chi = chi_f32(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps, &wc);
-    Plan pl;
+    const float chi = chi_f32(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps, &wc);
     if (wc && eps > 0.0f) {
-        pl = make_plan(P, sqz_e, sqz_p, photon, chi, eps, T);
+        const Plan pl = make_plan(P, sqz_e, sqz_p, photon, chi, eps, T);
         if (pl.safe) {
             *chi_out = chi;
             *eps_out = eps;
             return pl;
         }
     }
-    chi = chi_ff(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps);
-    *chi_out = chi;
-    *eps_out = eps;
-    if (!(eps > 0.0f)) {
-        pl.N = 0;
-        return pl;
-    }
-    return make_plan(P, sqz_e, sqz_p, photon, chi, eps, T);
+    return plan_slow(P, sqz_e, sqz_p, photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, T, chi_out,
+                     eps_out);
 }
 
 // Acceptance function of Algorithm 1 (emission, delta = x^3, Eq. 1):

@@ -82,11 +82,7 @@ def _graph_steps(arr, cap, first, k, **cfg):
     return store.to_numpy(), stats, ctx, store
 
 
-def test_graph_equals_eager_steps():
-    arr = I.clumped_mixed(3000, 21, hot_fraction=0.03)
-    cap = 400000
-    e_store, e_stats = _eager_steps(arr, cap, 50, 5, seed=99)
-    g_store, g_stats, ctx, store = _graph_steps(arr, cap, 50, 5, seed=99)
+def _same(e_stats, g_stats, e_store, g_store):
     for a, b in zip(e_stats, g_stats):
         for k in ("substeps", "emissions", "pairs", "children", "plans", "candidates", "max_N",
                   "passes", "status", "count"):
@@ -94,11 +90,32 @@ def test_graph_equals_eager_steps():
     e, g = _sorted(e_store), _sorted(g_store)
     for k in e:
         np.testing.assert_array_equal(e[k], g[k])
-    # a second launch continues from the evolved store with the same step indices
+
+
+def test_graph_equals_eager_steps():
+    arr = I.clumped_mixed(3000, 21, hot_fraction=0.03)
+    cap = 2_000_000
+    ectx = qed.Context(seed=99)
+    estore = qed.ParticleStore.from_numpy(arr, capacity=cap)
+
+    def eager(first, k):
+        stats = []
+        for j in range(k):
+            st = ectx.event_step(estore, first + j)
+            ectx.compact(estore)
+            st["count"] = estore.n()
+            stats.append(st)
+        return stats
+
+    e_stats = eager(50, 5)
+    g_store, g_stats, ctx, store = _graph_steps(arr, cap, 50, 5, seed=99)
+    _same(e_stats, g_stats, estore.to_numpy(), g_store)
+    # a second launch continues from the evolved store (same step indices)
+    e_stats2 = eager(50, 5)
     ctx.graph_launch()
-    again = ctx.graph_read_stats()
-    assert all(s["status"] == 0 for s in again)
-    assert again[0]["count"] != g_stats[0]["count"] or again[0]["substeps"] != g_stats[0]["substeps"]
+    g_stats2 = ctx.graph_read_stats()
+    assert all(s["status"] == 0 for s in g_stats2), [s["status"] for s in g_stats2]
+    _same(e_stats2, g_stats2, estore.to_numpy(), store.to_numpy())
 
 
 def test_graph_capacity_overflow_is_sticky():
@@ -116,9 +133,10 @@ def test_graph_capacity_overflow_is_sticky():
 
 
 def test_cascade_batch_graph_small():
+    # the cascade batch grows roughly tenfold per step even with the drain
     arr, cell = I.cascade_cells(128, 20081050, n_max=4096)
     n = len(arr["px"])
-    _, stats, ctx, store = _graph_steps(arr, n * 40, 0, 10, seed=20081050, drain_chi=0.05)
+    _, stats, ctx, store = _graph_steps(arr, n * 2000, 0, 3, seed=20081050, drain_chi=0.05)
     assert all(s["status"] == 0 for s in stats), stats
     assert stats[-1]["count"] > 0
     assert sum(s["substeps"] for s in stats) > n
