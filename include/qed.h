@@ -239,6 +239,32 @@ qed_status qed_profile_enable(qed_ctx* ctx, int enable);
  * accumulators.  Errors: QED_ERR_ARG, QED_ERR_CUDA. */
 qed_status qed_profile_read(qed_ctx* ctx, double* ms, int64_t* launches, int n);
 
+/* Largest store (rows of capacity) that qed_event_step_noalloc accepts. */
+#define QED_NOALLOC_MAX_ROWS 65536
+
+/* qed_event_step for callers that cannot allocate device memory: code that
+ * runs while a CUDA stream is being captured, hosts that hand out a fixed
+ * memory budget in advance, and plug-ins living inside another program's
+ * memory pool.  No context: the run configuration is passed directly, and the
+ * step's scratch (about 1.5 MB) lives in a device array built into this
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  The paper has no counterpart; this is a packaging of the same step.
+ *
+ * Same arguments and results as qed_event_step (no event log), on `stream`
+ * (a cudaStream_t, NULL: the legacy default stream); synchronises that
+ * stream between cascade generations and, if out != NULL, at the end.
+ * The first call on a device looks up the array and the launch geometry with
+ * that device current (make that first call before any stream capture);
+ * later calls on the device reuse them.  The array is shared by every call
+ * and keeps the contents of the last one: each step starts by resetting what
+ * it reads, but calls whose work overlaps on the GPU (other streams, other
+ * host threads) race with each other; serialise them.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.
+ * Errors: QED_ERR_ARG (bad argument, or p->capacity > QED_NOALLOC_MAX_ROWS),
+ * QED_ERR_CUDA, and the statuses of qed_event_step. */
+qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_particles* p,
+                                  uint64_t step_index, void* stream, qed_step_stats* out);
+
 /* sizeof of a public struct by name ("qed_config", "qed_particles",
  * "qed_step_stats", "qed_event_record"), or 0 for an unknown name.  Host
  * only; lets bindings check their struct mirrors without a GPU. */

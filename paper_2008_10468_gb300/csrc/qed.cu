@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1453,3 +1454,112 @@ size_t qed_abi_struct_size(const char* name) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Event step without allocation.
+//
+// For callers that may not allocate device memory: code running while a CUDA
+// stream is being captured (an allocation there breaks or invalidates the
+// capture), hosts that hand out a fixed memory budget up front, and plug-ins
+// inside another application's memory pool.  The scratch of the event step
+// (control block, remaining times of children, queue of long sub-step
+// chains) lives in one file-scope device array sized for
+// QED_NOALLOC_MAX_ROWS rows; every GPU that loads this library keeps it
+// until the process exits.  The first call on a device looks up the array's
+// device address (cudaGetSymbolAddress) and the launch geometry with that
+// device current; later calls reuse them.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocCtlBytes = 256;
+constexpr size_t kNoAllocTremOffset = kNoAllocCtlBytes;
+constexpr size_t kNoAllocHotOffset =
+    kNoAllocTremOffset + sizeof(ftime) * (size_t)QED_NOALLOC_MAX_ROWS;
+constexpr size_t kNoAllocBytes = kNoAllocHotOffset + sizeof(HotItem) * (size_t)QED_NOALLOC_MAX_ROWS;
+static_assert(sizeof(DevCtl) <= kNoAllocCtlBytes, "control block does not fit");
+static_assert(kNoAllocHotOffset % 16 == 0, "queue alignment");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+struct NoAllocDevice {
+    int ready;
+    unsigned char* base;   // device address of g_noalloc_scratch on this device
+    int cold_blocks, hot_blocks;
+};
+constexpr int kNoAllocMaxDevices = 64;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+qed_status noalloc_setup(int dev, NoAllocDevice* out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
+            return QED_ERR_CUDA;
+        int sms = 0, per_cold = 0, per_hot = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return QED_ERR_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_cold, k_cold, kColdThreads, 0) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot, kHotThreads, 0) !=
+                cudaSuccess)
+            return QED_ERR_CUDA;
+        d.base = static_cast<unsigned char*>(ptr);
+        d.cold_blocks = sms * (per_cold > 0 ? per_cold : 1);
+        d.hot_blocks = sms * (per_hot > 0 ? per_hot : 1);
+        d.ready = 1;
+    }
+    *out = d;
+    return QED_OK;
+}
+
+}  // namespace
+
+extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_particles* p,
+                                             uint64_t step_index, void* stream,
+                                             qed_step_stats* out) {
+    if (!cfg || !particles_ok(p) || step_index > 0xffffffffull) return QED_ERR_ARG;
+    if (p->capacity > (int64_t)QED_NOALLOC_MAX_ROWS) return QED_ERR_ARG;
+    if (!(cfg->p_max > 0.0f && cfg->p_max <= 1.0f) || !(cfg->dt_periods > 0.0) ||
+        !(cfg->lambda_m > 0.0) || !(cfg->pair_bound_coeff > 0.0f))
+        return QED_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QED_ERR_CUDA;
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return QED_ERR_ARG;
+    NoAllocDevice nd;
+    qed_status st = noalloc_setup(dev, &nd);
+    if (st != QED_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int max_passes = cfg->max_passes > 0 ? cfg->max_passes : 64;
+    const StepParams SP = make_params(*cfg, step_index);
+    const DevParticles D = to_dev(p);
+    DevCtl* ctl = reinterpret_cast<DevCtl*>(nd.base);
+    Scratch S;
+    S.t_rem = reinterpret_cast<ftime*>(nd.base + kNoAllocTremOffset);
+    S.hot = reinterpret_cast<HotItem*>(nd.base + kNoAllocHotOffset);
+    S.log = nullptr;
+    S.log_cap = 0;
+    S.log_count = nullptr;
+    const bool cascade = cascade_enabled(*cfg);
+    // the step-init kernel resets the whole control block, so nothing left
+    // from an earlier call is read
+    k_step_init<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, 0);
+    DevCtl h;
+    for (int pass = 0; pass < max_passes; ++pass) {
+        k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
+        k_hot<<<nd.hot_blocks, kHotThreads, 0, s>>>(D, SP, S, ctl);
+        k_advance<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, cascade ? 1 : 0, max_passes, 0ull, 0);
+        if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
+        if (!cascade) break;
+        if (cudaMemcpyAsync(&h, ctl, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return QED_ERR_CUDA;
+        if (!h.more) break;
+    }
+    if (!out) return QED_OK;
+    if (cudaMemcpyAsync(&h, ctl, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return QED_ERR_CUDA;
+    fill_stats(h, out, h.pass_end);
+    return (qed_status)h.status;
+}
