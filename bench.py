@@ -34,6 +34,10 @@ N_PARTICLES = 1 << 24
 SWEEP_N = 1 << 28
 SEED_CLUMPED = 20081046 + 3
 SEED_SWEEP = 20081046 + 2
+SEED_CASCADE = 20081046 + 4
+CASCADE_CELLS = 4096
+CASCADE_CAPACITY = 1 << 26
+CASCADE_DRAIN_CHI = 0.05
 METRIC = "particle-steps/sec (sub-stepped)"
 UNIT = "substeps/s"
 WORKLOAD = ("clumped mixed population 2^24 (25% e-, 25% e+, 50% photons; 1% hot clump "
@@ -68,7 +72,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -122,22 +126,31 @@ def barrier(pg):
         pg.barrier()
 
 
-def allreduce_max(pg, v):
+def allreduce_max(pg, v, device="cuda"):
+    """Largest value over the ranks (the job's time is its slowest rank's)."""
     if pg is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
 
 
-def allreduce_sum(pg, v):
+def allreduce_sum(pg, v, device="cuda"):
+    """Sum over the ranks (work done by the whole job)."""
     if pg is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     pg.all_reduce(t, op=pg.ReduceOp.SUM)
     return float(t.item())
+
+
+def job_rate(pg, units, ms, device="cuda"):
+    """Whole-job throughput of independent shards: all ranks' units over the
+    slowest rank's time (weak scaling, no data-path collective)."""
+    t_max = allreduce_max(pg, ms, device)
+    return allreduce_sum(pg, units, device) / (t_max / 1e3), t_max
 
 
 # --------------------------------------------------------------------------
@@ -216,6 +229,7 @@ def run_gb300(args):
 
     clocks = Clocks(local)
     clocks.start()
+    time.sleep(0.5)   # the sampler's first record comes before the timed steps
     total_ms = 0.0
     sub_total = 0
     agg = {"emissions": 0, "pairs": 0, "children": 0, "candidates": 0, "plans": 0,
@@ -245,9 +259,7 @@ def run_gb300(args):
     clk = clocks.stop()
     ctx.profile(False)
 
-    t_max = allreduce_max(pg, total_ms)
-    subs = allreduce_sum(pg, sub_total)
-    value = subs / (t_max / 1e3)
+    value, t_max = job_rate(pg, sub_total, total_ms)
 
     # dominant kernel and its roofline (event-timed on the library stream)
     dom = max(("cold", "hot"), key=lambda k: kern.get(k, [0])[0])
@@ -285,6 +297,13 @@ def run_gb300(args):
     # end to end from pinned host buffers through the public API
     e2e = None if args.no_e2e else run_e2e(ctx, arr, cap, dev, args)
 
+    # cascade batch: many steps of growing pools in one captured graph
+    cascade = None if args.no_cascade else run_cascade(dev, args)
+
+    # learned sampler against rejection on the same population
+    sampler = None if args.no_sampler else run_sampler(arr, pristine, store, cap, n, dev, args,
+                                                        restore, value)
+
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -299,6 +318,8 @@ def run_gb300(args):
         "kernels_ms_per_step": {k: v[0] / steps for k, v in kern.items() if v[1]},
         "roofline": roof,
         "sweep": sweep,
+        "sampler": sampler,
+        "cascade": cascade,
         "e2e": e2e,
         "gpu_launches": launches_timed,
         "clocks": clk,
@@ -349,6 +370,103 @@ def run_sweep(ctx, dev, args, hbm_peak, peak_kind):
             "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                     "peak_kind": peak_kind, "bytes_per_eval": 12},
             "generate_evals_per_s": SWEEP_N / (ms_gen / 1e3), "generate_ms": ms_gen}
+
+
+def run_cascade(dev, args):
+    """Independent cells with power-law counts; all global steps in one CUDA
+    graph, photons below the drain chi moved to the spectrum at each step's
+    compaction.  The pools grow by cascades; a step that would exceed the
+    capacity stops the run with QED_ERR_CAPACITY and the later steps do
+    nothing, so the record gives the steps completed.  Timed on the second
+    launch of the graph (the first warms up), from the same initial pools."""
+    import torch
+    from paper_2008_10468_gb300 import inputs as I
+    from paper_2008_10468_gb300 import qed
+    arr, _cell = I.cascade_cells(CASCADE_CELLS, SEED_CASCADE)
+    n0 = len(arr["px"])
+    cap = CASCADE_CAPACITY
+    pristine = qed.ParticleStore.from_numpy(arr, capacity=n0, device=dev)
+    store = qed.ParticleStore(cap, device=dev)
+    ctx = qed.Context(seed=SEED_CASCADE, process_mask=3, cascade=True, drain_chi=CASCADE_DRAIN_CHI)
+
+    def restore():
+        for k in qed.FLOAT_FIELDS + ("id", "type"):
+            getattr(store, k)[:n0].copy_(getattr(pristine, k)[:n0])
+        store.type[n0:].fill_(qed.REMOVED)
+        store.count.fill_(n0)
+
+    restore()
+    ctx.graph_capture(store, 0, args.cascade_steps)
+    ctx.graph_launch()
+    torch.cuda.synchronize()
+    restore()
+    ctx.read_spectrum(reset=True)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.graph_launch()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    stats = ctx.graph_read_stats()
+    done = [s for s in stats if s["status"] == 0]
+    failed = next((s for s in stats if s["status"] != 0), None)
+    sub = sum(s["substeps"] for s in done)
+    spec = ctx.read_spectrum()
+    return {
+        "cells": CASCADE_CELLS, "particles0": n0, "capacity": cap, "steps": args.cascade_steps,
+        "steps_completed": len(done),
+        "status": failed["status"] if failed else 0,
+        "required_capacity": failed["required_capacity"] if failed else 0,
+        "ms": ms, "substeps": sub, "substeps_per_s": sub / (ms / 1e3) if ms > 0 else None,
+        "count_after": [s["count"] for s in done],
+        "substeps_per_step": [s["substeps"] for s in done],
+        "drained_photon_weight": float(spec.sum()), "drain_chi": CASCADE_DRAIN_CHI,
+    }
+
+
+def run_sampler(arr, pristine, store, cap, n, dev, args, restore, plain_value):
+    """Train the inverse-CDF sampler on 2^26 exact-CDF samples, measure its
+    per-bin CDF error, and time the same steps with it (rejection is kept
+    outside chi in [1e-2, 1e2) and in bins above 1e-3 error)."""
+    import torch
+    from paper_2008_10468_gb300 import qed
+    ctx = qed.Context(seed=SEED_CLUMPED, process_mask=3, cascade=True, sampler=True,
+                      sampler_max_err=1e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = ctx.sampler_train(20081051, 1 << 26, batch=4096, lr=3e-3)
+    train_s = time.perf_counter() - t0
+    err = ctx.sampler_evaluate()
+    usable = err <= 1e-3
+    stream = torch.cuda.current_stream()
+    for w in range(2):
+        restore()
+        ctx.event_step(store, 4000 + w)
+    total_ms, subs, sampled, emis = 0.0, 0, 0, 0
+    for k in range(args.steps):
+        restore()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ctx.event_step(store, 2000 + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        subs += st["substeps"]
+        sampled += st["sampler_events"]
+        emis += st["emissions"]
+    value = subs / (total_ms / 1e3)
+    return {"train_samples": 1 << 26, "train_s": train_s, "final_mse": loss,
+            "bins_usable": int(usable.sum()), "bins": int(len(err)),
+            "max_cdf_err_usable": float(err[usable].max()) if usable.any() else None,
+            "max_cdf_err_all": float(err.max()), "median_cdf_err": float(np.median(err)),
+            "substeps_per_s": value, "ms_per_step": total_ms / args.steps,
+            "emissions_from_sampler": sampled / max(emis, 1),
+            "speedup_vs_rejection": value / plain_value}
 
 
 def run_e2e(ctx, arr, cap, dev, args):
@@ -438,11 +556,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sampler", action="store_true")
+    ap.add_argument("--no-cascade", action="store_true")
+    ap.add_argument("--cascade-steps", type=int, default=100)
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="population size (smaller values only for profiling runs)")
     ap.add_argument("--sweep-n", type=int, default=SWEEP_N,

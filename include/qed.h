@@ -61,6 +61,10 @@ typedef struct {
     int32_t max_passes;        /* cascade generations per step (0 -> 64)        */
     float drain_chi;           /* compaction drains photons with chi below this
                                   into the photon spectrum (0: never)           */
+    int32_t sampler_mode;      /* 1: learned inverse-CDF sampler for e+- emission
+                                  where usable (see qed_sampler_train)          */
+    float sampler_max_err;     /* a chi bin is usable if its max CDF error <= this
+                                  (1e-3)                                        */
 } qed_config;
 
 /* Photon spectrum filled by the drain: weight per bin of log10(photon
@@ -97,6 +101,7 @@ typedef struct {
     int32_t passes;            /* cascade generations processed                 */
     int32_t reserved;
     uint64_t substeps_warp;    /* of `substeps`, those run on the warp-per-particle path */
+    uint64_t sampler_events;   /* emissions whose energy came from the learned sampler */
 } qed_step_stats;
 
 /* One event, written to the optional device event log (validation). */
@@ -147,7 +152,7 @@ qed_status qed_synchrotron_F1F2(qed_ctx* ctx, const float* y, float* F1, float* 
 qed_status qed_synchrotron_generate(qed_ctx* ctx, uint64_t seed, int64_t n, float lo, float hi,
                                     float* checksum, float* y_out, float* F1_out, float* F2_out);
 
-/* Algorithms 1/2, line 1 only: for rows [0, n) compute chi (Sec. 2.2) and
+/* The planning step of Algorithms 1/2 only: for rows [0, n) compute chi (Sec. 2.2) and
  * the sub-step count N of a full global step (bound f(b) of Sec. 3.1.1,
  * N = max(1, ceil(f / P_max)), validity guard for e+-).  chi and N are
  * device arrays of n entries (either may be NULL).  Rows that are removed, or
@@ -200,7 +205,10 @@ qed_status qed_read_spectrum(qed_ctx* ctx, double* out, int nbins, int reset);
  * cascade generations run in a device-side loop (a conditional WHILE node
  * whose condition the last kernel of each generation sets), then the store is
  * compacted (qed_compact), then the step's statistics are recorded on the
- * device.  No host synchronisation inside.  A step that fails (capacity,
+ * device.  No host synchronisation inside.  Each launch continues the step
+ * numbering: the first launch runs steps first_step .. first_step + nsteps - 1,
+ * the next one the following nsteps indices (fresh draws and child ids).
+ * A step that fails (capacity,
  * cascade deeper than max_passes) makes the following steps no-ops; its
  * record carries the status.  Replaces any earlier graph of the context.
  * Errors: QED_ERR_ARG, QED_ERR_CUDA. */
@@ -215,6 +223,77 @@ qed_status qed_graph_launch(qed_ctx* ctx);
  * (nsteps <= captured steps) to out[0..nsteps).  Returns the first non-zero
  * step status, else QED_OK.  Errors: QED_ERR_ARG, QED_ERR_STATE, CUDA. */
 qed_status qed_graph_read_stats(qed_ctx* ctx, qed_step_stats* out, int nsteps);
+
+/* Learned inverse-CDF sampler (the inverse-sampling event generator the
+ * paper names as the classical alternative, Sec. 2.2, for the emission of
+ * Eq. 1).  A 2-64-64-64-1 perceptron (SiLU; logistic output anchored at
+ * logit u, so that x(0) = 0 and x(1) = 1; BF16 weights and FP32
+ * accumulation in the event kernels) maps (log10 chi, u) to x, the cube
+ * root of the photon energy fraction, for chi in [1e-2, 1e2).  With
+ * cfg.sampler_mode, e+- in a usable chi bin decide events from the tabulated
+ * total probability per sub-step c_h W(b) and take x from the network at the
+ * event's uniform; all others keep rejection.  The 64 bins are uniform in
+ * log10 chi; a bin is usable when its measured max |CDF(x_net(u)) - u| is at
+ * most cfg.sampler_max_err. */
+#define QED_SAMPLER_PARAMS 8577
+#define QED_SAMPLER_BINS 64
+
+/* Train with Adam (cosine-decayed step `lr`) on `samples` pairs drawn in
+ * batches of `batch` (64 <= batch <= 2^20): log10 chi and u uniform, target x
+ * from the exact CDF of the emission spectrum, tabulated on the GPU from the
+ * acceptance function of Algorithm 1 (1024 chi rows x 4096 x intervals).
+ * Loss: mean of (CDF(chi, x_net) - u)^2, the squared CDF error of the
+ * sampler, with CDF and density from the same tables; the forward pass uses
+ * the BF16-rounded weights the event kernels use, its gradient updating the
+ * FP32 weights.
+ * Starts from deterministic initial weights (seed) unless parameters were
+ * trained or loaded before.  *final_loss (host, nullable): mean squared
+ * error of the last batch.  Synchronises.  Errors: ARG, CUDA. */
+qed_status qed_sampler_train(qed_ctx* ctx, uint64_t seed, int64_t samples, int batch, float lr,
+                             float* final_loss);
+
+/* Measure the max CDF error per bin (bin_err: host array of
+ * QED_SAMPLER_BINS) on 4 chi rows x 1024 u per bin against exact CDF rows,
+ * and mark the usable bins.  Required before an event step in sampler mode.
+ * Errors: ARG, STATE (no sampler), CUDA. */
+qed_status qed_sampler_evaluate(qed_ctx* ctx, float* bin_err, int nbins);
+
+/* Loss mean(w^2 (x - t)^2) of the network `params` (device,
+ * QED_SAMPLER_PARAMS floats, used unrounded) on inputs v (device, B x 2:
+ * log10 chi / 2, logit(u) / 8), targets t and weights w (device, B; weight NULL:
+ * all 1), and its gradient into grad (device, QED_SAMPLER_PARAMS); *loss
+ * (device, nullable).  For gradient checks.  Errors: ARG, CUDA. */
+qed_status qed_sampler_gradient(qed_ctx* ctx, const float* params, const float* v,
+                                const float* target, const float* weight, int64_t B, float* grad,
+                                float* loss);
+
+/* x = delta^{1/3} at (log10chi[i], u[i]) for i < n (device arrays; log10 chi
+ * clamped to [-2, 2]; u in the open interval (0, 1)): use_net = 0 the exact
+ * inverse CDF from the tables
+ * (bilinear in log10 chi and x), 1 the network.  Errors: ARG, STATE, CUDA. */
+qed_status qed_sampler_quantile(qed_ctx* ctx, const float* log10chi, const float* u, float* x,
+                                int64_t n, int use_net);
+
+/* Copy parameters in (host -> device, also refreshes the BF16 copy) or out. */
+qed_status qed_sampler_load(qed_ctx* ctx, const float* params, int64_t n);
+qed_status qed_sampler_save(qed_ctx* ctx, float* params, int64_t n);
+
+/* Launch settings: the sub-step count from which a particle is stepped by a
+ * whole warp (default 64), and the resident blocks per SM of the thread and
+ * warp passes (default: the occupancy maximum; larger values are clamped to
+ * it).  0 keeps a setting.  Errors: QED_ERR_ARG. */
+qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, int cold_blocks_per_sm,
+                          int hot_blocks_per_sm);
+
+/* Time qed_event_step on `p` (step index step_index) for a coordinate search
+ * over the launch settings (warp-path threshold 16/32/64/128, blocks per SM
+ * of each pass), keep the fastest, and restore the store from a snapshot
+ * after every trial (the store is unchanged on return).  Writes the chosen
+ * settings and all trial timings as JSON to out_json (host file path,
+ * nullable).  Uses the compaction mirror as snapshot.  Synchronises.
+ * Errors: ARG, CUDA and those of qed_event_step. */
+qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                        const char* out_json);
 
 /* Kernel kinds for qed_profile_read. */
 enum {

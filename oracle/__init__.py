@@ -108,8 +108,8 @@ class Log(C.Structure):
 
 FIELDS = ("px", "py", "pz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "w")
 
-# Tie bands (the benchmark spec: a draw within 1e-5 of the acceptance probability is
-# exempt from the event-count comparison; the plan band is derived from the
+# Tie bands (a draw within 1e-5 of the acceptance probability is exempt from
+# the event-count comparison; the plan band is derived from the
 # binary32 error of the bound f computed by the kernel).
 TIE_DRAW = 1e-5
 TIE_PLAN = 4e-6
@@ -229,7 +229,7 @@ def make_config(seed, dt=0.1, lambda_m=1e-6, p_max=0.01, pair_coeff=0.1,
 
 
 def plan(cf, p, E, B, t_rem, photon=False):
-    """Sub-step count N of Algorithms 1/2, line 1, with chi, gamma and f."""
+    """Sub-step count N of the planning step of Algorithms 1/2, with chi, gamma and f."""
     ch, g, f = C.c_double(), C.c_double(), C.c_double()
     N = lib().orc_plan(C.byref(cf), int(photon), *[float(a) for a in (*p, *E, *B)],
                        float(t_rem), C.byref(ch), C.byref(g), C.byref(f))

@@ -417,7 +417,7 @@ static void process_particle(const orc_config* cf, orc_particles* P, int64_t i, 
     const double k_sqrt3_pi = ORC_SQRT3 / ORC_PI;
 
     while (t_rem > 0.0) {
-        /* Algorithm 1/2, line 1: sub-step for the remaining time. */
+        /* Algorithms 1/2, planning: sub-step for the remaining time. */
         double gamma;
         double chi = orc_chi(is_photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, cf->E_s, &gamma);
         if (!(gamma > 0.0)) break;   /* a photon without momentum does nothing */
@@ -440,11 +440,11 @@ static void process_particle(const orc_config* cf, orc_particles* P, int64_t i, 
         double c_h = k_sqrt3_pi * cf->R * h / gamma;
         int event = 0;
         for (uint32_t k = 0; k < N; ++k) {
-            /* line 5: sample x, y */
+            /* draw x, y for this sub-step */
             double x, y;
             orc_draw(cf->seed, id, step, s, &x, &y);
             st->substeps++;
-            /* line 6: acceptance test */
+            /* acceptance test */
             double P_acc = is_photon ? orc_Pp(b, c_h, x) : orc_Pm(b, c_h, x);
             if (!tied && fabs(y - P_acc) <= cf->tie_draw) { tied = 1; log_tie(L, id, s, 1); }
             if (y < P_acc) {
@@ -485,7 +485,7 @@ static void process_particle(const orc_config* cf, orc_particles* P, int64_t i, 
                     st->children += 2;
                     log_event(L, &e);
                     if (cf->recoil) {
-                        /* Algorithm 2, line 8: delete the photon and stop */
+                        /* Algorithm 2: the decayed photon is deleted and stops */
                         P->type[i] = 3;
                         P->px[i] = (float)px; P->py[i] = (float)py; P->pz[i] = (float)pz;
                         return;

@@ -3,10 +3,10 @@
 // Kernels
 //   k_sweep / k_generate   synchrotron functions over an array or over
 //                          in-kernel arguments (Sec. 3.2.1)
-//   k_plan                 chi and the sub-step count (Algorithms 1/2 line 1)
+//   k_plan                 chi and the sub-step count (planning, Algorithms 1/2)
 //   k_cold                 one thread per particle: plan, sub-step loop,
 //                          events, children; particles whose plan exceeds
-//                          kHotMin sub-steps are pushed to the hot queue
+//                          hot_min sub-steps are pushed to the hot queue
 //   k_hot                  persistent kernel: one warp per queued particle,
 //                          64 sub-steps per iteration (lane l draws the
 //                          Philox block of sub-steps 2l, 2l+1), first accepted
@@ -21,12 +21,15 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <vector>
 
 #include "qed.h"
 #include "qed_device.cuh"
+#include "qed_sampler.cuh"
 
 using namespace qed;
 
@@ -37,7 +40,7 @@ constexpr double kTauC = 1.2880886664441626e-21;    // hbar / (m c^2), s
 constexpr double kCLight = 299792458.0;             // m / s
 constexpr double kPiD = 3.14159265358979323846;
 
-constexpr uint32_t kHotMin = 64;       // plans with N >= kHotMin go to the warp path
+constexpr uint32_t kHotMinDefault = 64;  // plans with N >= hot_min go to the warp path
 
 // Minimum resident blocks per SM requested from the register allocator:
 // 3 x 256 and 6 x 128 threads keep both event kernels at 80 registers
@@ -55,6 +58,7 @@ constexpr int kSweepThreads = 256;
 struct DevCtl {
     unsigned long long substeps, emissions, pairs, children, guard_hits, plans, candidates;
     unsigned long long substeps_warp;
+    unsigned long long sampler_events;
     unsigned int max_N;
     int status;
     long long required;
@@ -94,7 +98,7 @@ struct Scratch {
 // stays far below 2^32); summed per warp and added to the control block.
 struct Stats {
     unsigned int substeps = 0, emissions = 0, pairs = 0, children = 0, guard = 0, plans = 0,
-                 cand = 0, warp_substeps = 0;
+                 cand = 0, warp_substeps = 0, sampled = 0;
     unsigned int max_N = 0;
 };
 
@@ -113,7 +117,8 @@ __device__ void flush_stats(const Stats& st, DevCtl* ctl) {
     const unsigned long long a = warp_sum(st.substeps), b = warp_sum(st.emissions),
                              c = warp_sum(st.pairs), d = warp_sum(st.children),
                              e = warp_sum(st.guard), f = warp_sum(st.plans), g = warp_sum(st.cand),
-                             h = warp_sum(st.warp_substeps);  // 64-bit sums of 32-bit counters
+                             h = warp_sum(st.warp_substeps),  // 64-bit sums of 32-bit counters
+                             q = warp_sum(st.sampled);
     const unsigned int m = warp_max(st.max_N);
     if ((threadIdx.x & 31) == 0) {
         if (a) atomicAdd(&ctl->substeps, a);
@@ -124,6 +129,7 @@ __device__ void flush_stats(const Stats& st, DevCtl* ctl) {
         if (f) atomicAdd(&ctl->plans, f);
         if (g) atomicAdd(&ctl->candidates, g);
         if (h) atomicAdd(&ctl->substeps_warp, h);
+        if (q) atomicAdd(&ctl->sampler_events, q);
         if (m) atomicMax(&ctl->max_N, m);
     }
 }
@@ -306,27 +312,95 @@ __device__ __forceinline__ void write_child(const DevParticles& P, const Scratch
 
 // Apply an accepted event (recoil or decay, children, log).  Returns true if
 // the particle was removed (photon decay).
-__device__ __noinline__ bool apply_event(const DevParticles& P, const Scratch& S, const StepParams& SP,
+// The parent's fields, copied to its children.
+struct Fields {
+    float Ex, Ey, Ez, Bx, By, Bz;
+};
+
+// Warp form of write_child: lanes 13 r + f (f < 13) store field f of child
+// row r (r < nrows), so the rows are written by one round of parallel stores.
+__device__ __forceinline__ void write_children_warp(const DevParticles& P, const Scratch& S,
+                                                   long long j, int nrows, long long parent,
+                                                   const Fields& F, const float (&p)[2][3],
+                                                   const uint64_t (&cid)[2],
+                                                   const uint8_t (&ctype)[2], ftime t_rem) {
+    const int lane = threadIdx.x & 31;
+    const int r = lane / 13, f = lane - 13 * r;
+    if (r >= nrows) return;
+    const long long d = j + r;
+    switch (f) {
+        case 0: P.px[d] = p[r][0]; break;
+        case 1: P.py[d] = p[r][1]; break;
+        case 2: P.pz[d] = p[r][2]; break;
+        case 3: P.Ex[d] = F.Ex; break;
+        case 4: P.Ey[d] = F.Ey; break;
+        case 5: P.Ez[d] = F.Ez; break;
+        case 6: P.Bx[d] = F.Bx; break;
+        case 7: P.By[d] = F.By; break;
+        case 8: P.Bz[d] = F.Bz; break;
+        case 9: P.w[d] = P.w[parent]; break;
+        case 10: P.id[d] = cid[r]; break;
+        case 11: P.type[d] = ctype[r]; break;
+        default: S.t_rem[d] = t_rem; break;
+    }
+}
+
+// Apply an accepted event (recoil or decay, children, log).  Returns true if
+// the particle was removed (photon decay).  Thread callers (write_rows) do
+// everything themselves, sharing one reservation atomic per warp; warp
+// callers (all 32 lanes, identical arguments) reserve on lane 0 and store the
+// child rows across lanes.  The reservation is issued first so that its
+// latency overlaps the child-id computation.
+__device__ __forceinline__ bool apply_event(const DevParticles& P, const Scratch& S, const StepParams& SP,
                             DevCtl* ctl, long long i, uint64_t id, bool photon, float x,
-                            float eps, float chi, uint32_t s, ftime t_after, PState& st,
-                            Stats& stats, bool write_rows, bool warp_caller) {
-    const uint4 cid = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), SP.step, s),
+                            float eps, float chi, uint32_t step, uint32_t s, ftime t_after, PState& st,
+                            Stats& stats, bool write_rows, bool warp_caller, const Fields& F) {
+    const int nch = photon ? 2 : 1;
+    const int lane = threadIdx.x & 31;
+    long long j = -1;
+    if (warp_caller) {
+        if (lane == 0) j = reserve_rows(P, ctl, nch, false);
+        j = __shfl_sync(0xffffffffu, j, 0);
+    } else if (write_rows) {
+        j = reserve_rows(P, ctl, nch, true);
+    }
+    const uint4 cid = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, s),
                                     (uint32_t)SP.seed ^ kChildKeyLo,
                                     (uint32_t)(SP.seed >> 32) ^ kChildKeyHi);
     const uint64_t id0 = ((uint64_t)cid.x | ((uint64_t)cid.y << 32)) | (1ull << 63);
     const uint64_t id1 = ((uint64_t)cid.z | ((uint64_t)cid.w << 32)) | (1ull << 63);
-    // thread-per-particle callers aggregate their reservations per warp
-    const bool aggregate = write_rows && !warp_caller;
     float delta;
     bool removed = false;
+    float cp[2][3];
     if (!photon) {
         delta = x * x * x;
-        if (write_rows) {
-            const long long j = reserve_rows(P, ctl, 1, aggregate);
-            if (j >= 0)
-                write_child(P, S, j, i, delta * st.px, delta * st.py, delta * st.pz, id0,
-                            QED_PHOTON, t_after);
+        cp[0][0] = delta * st.px;
+        cp[0][1] = delta * st.py;
+        cp[0][2] = delta * st.pz;
+        cp[1][0] = cp[1][1] = cp[1][2] = 0.0f;
+    } else {
+        delta = x;
+        const float omd = 1.0f - x;
+        cp[0][0] = x * st.px;
+        cp[0][1] = x * st.py;
+        cp[0][2] = x * st.pz;
+        cp[1][0] = omd * st.px;
+        cp[1][1] = omd * st.py;
+        cp[1][2] = omd * st.pz;
+    }
+    if (j >= 0) {
+        const uint64_t cids[2] = {id0, id1};
+        const uint8_t ctypes[2] = {photon ? (uint8_t)QED_ELECTRON : (uint8_t)QED_PHOTON,
+                                   (uint8_t)QED_POSITRON};
+        if (warp_caller) {
+            write_children_warp(P, S, j, nch, i, F, cp, cids, ctypes, t_after);
+        } else {
+            for (int r = 0; r < nch; ++r)
+                write_child(P, S, j + r, i, cp[r][0], cp[r][1], cp[r][2], cids[r], ctypes[r],
+                            t_after);
         }
+    }
+    if (!photon) {
         if (SP.recoil) {
             if (delta < 1e-6f && eps > 1e4f) {
                 const double f = 1.0 - (double)delta;
@@ -347,22 +421,12 @@ __device__ __noinline__ bool apply_event(const DevParticles& P, const Scratch& S
         stats.emissions++;
         stats.children++;
     } else {
-        delta = x;
-        if (write_rows) {
-            const long long j = reserve_rows(P, ctl, 2, aggregate);
-            if (j >= 0) {
-                const float omd = 1.0f - x;
-                write_child(P, S, j, i, x * st.px, x * st.py, x * st.pz, id0, QED_ELECTRON,
-                            t_after);
-                write_child(P, S, j + 1, i, omd * st.px, omd * st.py, omd * st.pz, id1,
-                            QED_POSITRON, t_after);
-            }
-        }
         removed = SP.recoil != 0;
         stats.pairs++;
         stats.children += 2;
     }
-    if (write_rows && S.log) {
+    const bool logger = warp_caller ? lane == 0 : write_rows;
+    if (logger && S.log) {
         const long long k = (long long)atomicAdd(reinterpret_cast<unsigned long long*>(S.log_count), 1ull);
         if (k < S.log_cap) {
             qed_event_record r;
@@ -394,11 +458,28 @@ __device__ __forceinline__ void push_hot(const Scratch& S, DevCtl* ctl, long lon
     S.hot[k] = it;
 }
 
+// With the learned sampler on, e+- whose chi lies in a usable bin of its
+// range are stepped on the warp path, where the network is evaluated.
+__device__ __forceinline__ bool sampler_bin_ok(const StepParams& SP, float chi) {
+    if (!SP.sampler || !(chi >= 1e-2f && chi < 1e2f)) return false;
+    const int bin = min(max((int)((log10f(chi) - kMlpLog10Lo) * 16.0f), 0), 63);
+    return (SP.net_bins >> bin) & 1ull;
+}
+
+// Graph runs keep the global step index as a device base plus the node's
+// offset, so that relaunching a graph continues with new step indices.
+__device__ __forceinline__ uint32_t step_index(const StepParams& SP) {
+    return SP.step_base ? SP.step + *SP.step_base : SP.step;
+}
+
 // One thread per particle.  First generation of a step: rows [0, pass_end)
 // with the full step; later generations: rows [pass_begin, pass_end)
-// (children) with their stored remaining time.
+// (children) with their stored remaining time.  Particles whose plan reaches
+// hot_min sub-steps (or, with the sampler, e+- in a usable chi bin) go to the
+// warp queue at that point.
 __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevParticles P, StepParams SP, Scratch S,
                                                        DevCtl* ctl) {
+    const uint32_t step = step_index(SP);
     __shared__ SharedTables sm;
     stage_tables(sm);
     __syncthreads();
@@ -430,26 +511,25 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
             const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
                                           Ey, Ez, Bx, By, Bz, t_rem, &chi, &eps);
             if (!(eps > 0.0f)) break;
-            stats.plans++;
-            stats.guard += pl.guard ? 1 : 0;
             stats.max_N = max(stats.max_N, pl.N);
-            if (pl.N >= kHotMin) {
+            if (pl.N >= SP.hot_min || (!photon && sampler_bin_ok(SP, chi))) {
                 if (changed) {
                     P.px[i] = st.px;
                     P.py[i] = st.py;
                     P.pz[i] = st.pz;
                     changed = false;
                 }
-                stats.plans--;  // the warp path re-plans and counts it
                 push_hot(S, ctl, i, s, t_rem);
                 t_rem = ftime{0.0f, 0.0f};
                 break;
             }
+            stats.plans++;
+            stats.guard += pl.guard ? 1 : 0;
             bool event = false;
             for (uint32_t k = 0; k < pl.N; ++k) {
                 const uint32_t b = s >> 1;
                 if (b != blk_idx) {
-                    blk = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), SP.step, b),
+                    blk = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, b),
                                         k0, k1);
                     blk_idx = b;
                 }
@@ -464,8 +544,9 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                     if (u01(ry) < Pa) {
                         const ftime t_after = (k + 1 == pl.N) ? ftime{0.0f, 0.0f}
                                                               : time_sub_mul(t_rem, k + 1, pl.h);
-                        removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, s,
-                                              t_after, st, stats, true, false);
+                        removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s,
+                                              t_after, st, stats, true, false,
+                                              Fields{Ex, Ey, Ez, Bx, By, Bz});
                         changed = true;
                         ++s;
                         t_rem = t_after;
@@ -490,10 +571,21 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
 }
 
 // One warp per queued particle.
+// kSampler: e+- in a usable bin of the sampler's chi range decide events from
+// the tabulated total probability c_h W(b) and take the energy fraction from
+// the network (x = delta^{1/3} at the event's uniform); the others use
+// rejection as usual.
+template <bool kSampler>
 __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevParticles P, StepParams SP, Scratch S,
                                                      DevCtl* ctl) {
+    const uint32_t step = step_index(SP);
     __shared__ SharedTables sm;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    SamplerSmem& net = *reinterpret_cast<SamplerSmem*>(dyn_smem);
     stage_tables(sm);
+    if (kSampler)
+        stage_sampler(net, reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
+                      SP.net_rows, SP.net_bins);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const unsigned int tail = ctl->hot_tail;
@@ -507,8 +599,7 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
         if (q >= tail) break;
         const HotItem it = S.hot[q];
         const long long i = it.idx;
-        const uint8_t type = P.type[i];
-        const bool photon = type == QED_PHOTON;
+        const bool photon = P.type[i] == QED_PHOTON;
         const uint64_t id = P.id[i];
         PState st{P.px[i], P.py[i], P.pz[i]};
         const float Ex = P.Ex[i], Ey = P.Ey[i], Ez = P.Ez[i];
@@ -526,6 +617,8 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
                 stats.guard += pl.guard ? 1 : 0;
                 stats.max_N = max(stats.max_N, pl.N);
             }
+            const bool use_net = kSampler && !photon && sampler_bin_ok(SP, chi);
+            const float thr = use_net ? pl.c_h * sampler_wtot(net, chi) : 0.0f;
             uint32_t kdone = 0;
             bool event = false;
             while (kdone < pl.N) {
@@ -534,15 +627,21 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
                 const uint32_t lim = sb + (pl.N - kdone);
                 const uint32_t s0 = sa + 2u * (uint32_t)lane;
                 const uint4 r = philox4x32_10(
-                    make_uint4((uint32_t)id, (uint32_t)(id >> 32), SP.step, (sa >> 1) + lane), k0, k1);
+                    make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, (sa >> 1) + lane), k0, k1);
                 const bool v0 = s0 >= sb && s0 < lim;
                 const bool v1 = s0 + 1 >= sb && s0 + 1 < lim;
-                const bool c0 = v0 && (r.y >> 9) < pl.T;
-                const bool c1 = v1 && (r.w >> 9) < pl.T;
-                bool a0 = false, a1 = false;
-                float dtmp;
-                if (c0) a0 = u01(r.y) < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(r.x), &dtmp);
-                if (c1) a1 = u01(r.w) < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(r.z), &dtmp);
+                bool c0, c1, a0 = false, a1 = false;
+                if (use_net) {
+                    c0 = c1 = false;
+                    a0 = v0 && u01(r.y) < thr;
+                    a1 = v1 && u01(r.w) < thr;
+                } else {
+                    c0 = v0 && (r.y >> 9) < pl.T;
+                    c1 = v1 && (r.w >> 9) < pl.T;
+                    float dtmp;
+                    if (c0) a0 = u01(r.y) < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(r.x), &dtmp);
+                    if (c1) a1 = u01(r.w) < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(r.z), &dtmp);
+                }
                 const unsigned int m0 = __ballot_sync(0xffffffffu, a0);
                 const unsigned int m1 = __ballot_sync(0xffffffffu, a1);
                 cand += (unsigned)c0 + (unsigned)c1;
@@ -558,13 +657,18 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
                 const int pos = min(p0, p1);
                 const uint32_t s_ev = sa + (uint32_t)pos;
                 const float xo = (pos & 1) ? u01(r.z) : u01(r.x);
-                const float x = __shfl_sync(0xffffffffu, xo, pos >> 1);
+                float x = __shfl_sync(0xffffffffu, xo, pos >> 1);
+                if (use_net) {
+                    // inverse sampling: the event's uniform goes through the network
+                    x = mlp_infer_warp(net, log10f(chi) * 0.5f, mlp_input_u(x));
+                    if (lane == 0) stats.sampled++;
+                }
                 const uint32_t k_ev = kdone + (s_ev - sb);
                 if (lane == 0) stats.substeps += s_ev - sb + 1;
                 const ftime t_after = (k_ev + 1 == pl.N) ? ftime{0.0f, 0.0f}
                                                          : time_sub_mul(t_rem, k_ev + 1, pl.h);
-                removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, s_ev, t_after,
-                                      st, stats, lane == 0, true);
+                removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev, t_after,
+                                      st, stats, lane == 0, true, Fields{Ex, Ey, Ez, Bx, By, Bz});
                 changed = true;
                 s = s_ev + 1;
                 t_rem = t_after;
@@ -633,8 +737,10 @@ __global__ void k_advance(DevCtl* ctl, long long* count, long long capacity, int
 
 // Write the statistics of the step into `rec` (if not null); an error becomes
 // sticky for the following steps of a graph run.
-__global__ void k_step_close(DevCtl* ctl, const long long* count, qed_step_stats* rec) {
+__global__ void k_step_close(DevCtl* ctl, const long long* count, qed_step_stats* rec,
+                             uint32_t* step_base, uint32_t advance) {
     const DevCtl c = *ctl;
+    if (step_base && advance) *step_base += advance;
     if (rec) {
         qed_step_stats r;
         r.substeps = c.substeps;
@@ -651,6 +757,7 @@ __global__ void k_step_close(DevCtl* ctl, const long long* count, qed_step_stats
         r.passes = c.passes;
         r.reserved = 0;
         r.substeps_warp = c.substeps_warp;
+        r.sampler_events = c.sampler_events;
         *rec = r;
     }
     if (c.status != 0 && c.sticky == 0) ctl->sticky = c.status;
@@ -838,15 +945,32 @@ struct qed_ctx {
     long long log_cap;
     long long* log_count;
     int cold_blocks, hot_blocks;
+    int cold_blocks_max, hot_blocks_max;
+    uint32_t hot_min;
     // compaction
     Mirror mirror;
     long long mirror_cap;
     unsigned int* d_block_live;
     double* d_hist;
+    // learned sampler
+    float* d_theta;            // FP32 master parameters
+    float* d_m1;               // Adam moments
+    float* d_m2;
+    __nv_bfloat16* d_wbf;      // BF16 copy used by the event kernels
+    float* d_cdf;              // exact CDF rows (training targets)
+    float* d_wtot;             // total probability per c along log10 chi
+    float* d_partial;          // per-block partial gradients
+    float* d_batch;            // training inputs (2 per sample), targets and weights
+    int batch_cap;
+    float* d_loss;
+    int net_ready;             // parameters loaded or trained
+    unsigned long long net_bins;
+    long long adam_t;
     // multi-step graph
     cudaGraph_t graph;
     cudaGraphExec_t graph_exec;
     qed_step_stats* d_records;
+    uint32_t* d_step_base;
     int graph_steps;
     // benchmark timing: event pairs recorded around launches
     int prof_on;
@@ -856,6 +980,10 @@ struct qed_ctx {
     long long launches[QED_KERNEL_KINDS];
     char err[512];
 };
+
+namespace {
+qed_status sampler_params(qed_ctx* ctx, StepParams* SP);
+}  // namespace
 
 namespace {
 
@@ -888,7 +1016,15 @@ StepParams make_params(const qed_config& c, uint64_t step) {
     const double omega = 2.0 * kPiD * kCLight / c.lambda_m;
     P.inv_Es = (float)(omega * kTauC);                        // 1 / E_s in code units
     P.p_max = c.p_max;
+    P.inv_p_max = 1.0f / c.p_max;
     P.pair_coeff = c.pair_bound_coeff;
+    P.step_base = nullptr;
+    P.hot_min = kHotMinDefault;
+    P.sampler = 0;
+    P.net_rows = 0;
+    P.net_bins = 0;
+    P.net_w = nullptr;
+    P.net_wtot = nullptr;
     P.step = (uint32_t)step;
     P.process_mask = c.process_mask;
     P.recoil = c.recoil;
@@ -985,9 +1121,11 @@ void free_graph(qed_ctx* ctx) {
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
     if (ctx->d_records) cudaFree(ctx->d_records);
+    if (ctx->d_step_base) cudaFree(ctx->d_step_base);
     ctx->graph_exec = nullptr;
     ctx->graph = nullptr;
     ctx->d_records = nullptr;
+    ctx->d_step_base = nullptr;
     ctx->graph_steps = 0;
 }
 
@@ -1022,6 +1160,7 @@ void fill_stats(const DevCtl& c, qed_step_stats* out, long long count) {
     out->passes = c.passes;
     out->reserved = 0;
     out->substeps_warp = c.substeps_warp;
+    out->sampler_events = c.sampler_events;
 }
 
 }  // namespace
@@ -1040,6 +1179,8 @@ void qed_config_default(qed_config* c) {
     c->recoil = 1;
     c->max_passes = 64;
     c->drain_chi = 0.0f;
+    c->sampler_mode = 0;
+    c->sampler_max_err = 1e-3f;
 }
 
 qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
@@ -1065,10 +1206,11 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
     if (st == QED_OK) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cold, kColdThreads, 0);
-        ctx->cold_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
+        ctx->cold_blocks = ctx->cold_blocks_max = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot, kHotThreads, 0);
-        ctx->hot_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot<false>, kHotThreads, 0);
+        ctx->hot_blocks = ctx->hot_blocks_max = ctx->sms * (per_sm > 0 ? per_sm : 1);
+        ctx->hot_min = kHotMinDefault;
         st = cuda_check(ctx, cudaGetLastError(), "occupancy");
     }
     if (st != QED_OK) {
@@ -1096,6 +1238,10 @@ qed_status qed_destroy(qed_ctx* ctx) {
     if (ctx->mirror.type) cudaFree(ctx->mirror.type);
     if (ctx->d_block_live) cudaFree(ctx->d_block_live);
     if (ctx->d_hist) cudaFree(ctx->d_hist);
+    void* sp[] = {ctx->d_theta, ctx->d_m1, ctx->d_m2, ctx->d_wbf, ctx->d_cdf, ctx->d_wtot,
+                  ctx->d_partial, ctx->d_batch, ctx->d_loss};
+    for (void* a : sp)
+        if (a) cudaFree(a);
     delete ctx;
     return QED_OK;
 }
@@ -1169,7 +1315,10 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
         return set_err(ctx, QED_ERR_ARG, "qed_event_step: bad argument");
     qed_status st = ensure_scratch(ctx, p->capacity);
     if (st != QED_OK) return st;
-    const StepParams SP = make_params(ctx->cfg, step_index);
+    StepParams SP = make_params(ctx->cfg, step_index);
+    SP.hot_min = ctx->hot_min;
+    st = sampler_params(ctx, &SP);
+    if (st != QED_OK) return st;
     const DevParticles D = to_dev(p);
     const Scratch S = make_scratch(ctx);
     const bool cascade = cascade_enabled(ctx->cfg);
@@ -1184,7 +1333,11 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
         }
         {
             LaunchScope ls(ctx, QED_KERNEL_HOT);
-            k_hot<<<ctx->hot_blocks, kHotThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+            if (SP.sampler)
+                k_hot<true><<<ctx->hot_blocks, kHotThreads, sizeof(SamplerSmem), ctx->stream>>>(
+                    D, SP, S, ctx->d_ctl);
+            else
+                k_hot<false><<<ctx->hot_blocks, kHotThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
         }
         {
             LaunchScope ls(ctx, QED_KERNEL_CONTROL);
@@ -1271,13 +1424,14 @@ namespace {
 
 // Append a kernel node with `args` to graph g after `deps`.
 qed_status add_kernel(qed_ctx* ctx, cudaGraph_t g, cudaGraphNode_t* node, const void* func,
-                      dim3 grid, dim3 block, void** args, const cudaGraphNode_t* deps, int ndeps) {
+                      dim3 grid, dim3 block, void** args, const cudaGraphNode_t* deps, int ndeps,
+                      size_t smem = 0) {
     cudaKernelNodeParams kp;
     memset(&kp, 0, sizeof kp);
     kp.func = const_cast<void*>(func);
     kp.gridDim = grid;
     kp.blockDim = block;
-    kp.sharedMemBytes = 0;
+    kp.sharedMemBytes = (unsigned int)smem;
     kp.kernelParams = args;
     kp.extra = nullptr;
     return cuda_check(ctx, cudaGraphAddKernelNode(node, g, deps, (size_t)ndeps, &kp),
@@ -1296,6 +1450,14 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
     if (st == QED_OK) st = ensure_mirror(ctx, p->capacity);
     if (st != QED_OK) return st;
     QED_CUDA(ctx, cudaMalloc(&ctx->d_records, sizeof(qed_step_stats) * nsteps));
+    QED_CUDA(ctx, cudaMalloc(&ctx->d_step_base, sizeof(uint32_t)));
+    {
+        const uint32_t base = (uint32_t)first_step;
+        QED_CUDA(ctx, cudaMemcpyAsync(ctx->d_step_base, &base, sizeof base, cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    uint32_t* step_base = ctx->d_step_base;
     QED_CUDA(ctx, cudaMemsetAsync(ctx->d_records, 0, sizeof(qed_step_stats) * nsteps, ctx->stream));
     QED_CUDA(ctx, cudaGraphCreate(&ctx->graph, 0));
     cudaGraph_t g = ctx->graph;
@@ -1321,7 +1483,11 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         if (st != QED_OK) return st;
     }
     for (int k = 0; k < nsteps && st == QED_OK; ++k) {
-        StepParams SP = make_params(ctx->cfg, first_step + (uint64_t)k);
+        StepParams SP = make_params(ctx->cfg, (uint64_t)k);   // offset from the device base
+        SP.step_base = step_base;
+        SP.hot_min = ctx->hot_min;
+        st = sampler_params(ctx, &SP);
+        if (st != QED_OK) break;
         qed_step_stats* rec = ctx->d_records + k;
         cudaGraphNode_t init, wnode, n1, n2, n3, n4, n5, close;
         {
@@ -1351,8 +1517,10 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         }
         if (st == QED_OK) {
             void* a[] = {&D, &SP, &S, &ctl};
-            st = add_kernel(ctx, body, &bh, (const void*)k_hot, dim3(ctx->hot_blocks),
-                            dim3(kHotThreads), a, &bc, 1);
+            st = add_kernel(ctx, body, &bh,
+                            SP.sampler ? (const void*)k_hot<true> : (const void*)k_hot<false>,
+                            dim3(ctx->hot_blocks), dim3(kHotThreads), a, &bc, 1,
+                            SP.sampler ? sizeof(SamplerSmem) : 0);
         }
         if (st == QED_OK) {
             void* a[] = {&ctl, &count, &capacity, &more_allowed, &max_passes, &h, &use_handle};
@@ -1383,8 +1551,9 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
             void* a[] = {&D, &ctl};
             st = add_kernel(ctx, g, &n5, (const void*)k_compact_finish, dim3(1), dim3(1), a, &n4, 1);
         }
+        uint32_t advance = (k == nsteps - 1) ? (uint32_t)nsteps : 0u;
         if (st == QED_OK) {
-            void* a[] = {&ctl, &count, &rec};
+            void* a[] = {&ctl, &count, &rec, &step_base, &advance};
             st = add_kernel(ctx, g, &close, (const void*)k_step_close, dim3(1), dim3(1), a, &n5, 1);
         }
         prev = close;
@@ -1415,6 +1584,418 @@ qed_status qed_graph_read_stats(qed_ctx* ctx, qed_step_stats* out, int nsteps) {
     QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     for (int k = 0; k < nsteps; ++k)
         if (out[k].status != 0) return (qed_status)out[k].status;
+    return QED_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Learned sampler
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kCdfRows = 1024;      // rows of the exact CDF along log10 chi in [-2, 2]
+constexpr int kCdfM = 4096;         // x intervals per row
+constexpr int kEvalSub = 4;         // evaluation rows per error bin
+constexpr int kEvalU = 1024;        // evaluation points in u per row
+
+qed_status sampler_alloc(qed_ctx* ctx, int max_batch) {
+    if (!ctx->d_theta) {
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_theta, sizeof(float) * kMlpParams));
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_m1, sizeof(float) * kMlpParams));
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_m2, sizeof(float) * kMlpParams));
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_wbf, sizeof(__nv_bfloat16) * kMlpParams));
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_partial, sizeof(float) * kMlpParams * ctx->sms * 2));
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_loss, sizeof(float)));
+        QED_CUDA(ctx, cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)sizeof(TrainSmem)));
+    }
+    if (!ctx->d_cdf) {
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_cdf, sizeof(float) * kCdfRows * (kCdfM + 1)));
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_wtot, sizeof(float) * kCdfRows));
+        k_cdf_rows<<<kCdfRows, 256, 0, ctx->stream>>>(kMlpLog10Lo, kMlpLog10Hi, kCdfRows, kCdfM,
+                                                      ctx->d_cdf, ctx->d_wtot);
+        QED_CUDA(ctx, cudaGetLastError());
+    }
+    if (max_batch > 0 && ctx->d_batch && ctx->batch_cap < max_batch) {
+        cudaFree(ctx->d_batch);
+        ctx->d_batch = nullptr;
+    }
+    if (max_batch > 0 && !ctx->d_batch) {
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_batch, sizeof(float) * 4 * (size_t)max_batch));
+        ctx->batch_cap = max_batch;
+    }
+    return QED_OK;
+}
+
+qed_status sampler_params(qed_ctx* ctx, StepParams* SP) {
+    if (!ctx->cfg.sampler_mode) return QED_OK;
+    if (!ctx->net_ready || !ctx->d_wtot)
+        return set_err(ctx, QED_ERR_STATE, "sampler_mode set but no sampler trained or loaded");
+    SP->sampler = 1;
+    SP->net_rows = kCdfRows;
+    SP->net_bins = ctx->net_bins;
+    SP->net_w = ctx->d_wbf;
+    SP->net_wtot = ctx->d_wtot;
+    return QED_OK;
+}
+
+// Deterministic initial parameters: uniform(+-1/sqrt(fan_in)) from Philox on
+// the host (the same recipe for every run with the same seed).
+void sampler_init_host(uint64_t seed, float* th) {
+    uint64_t state = seed * 0x9E3779B97F4A7C15ull + 1;
+    auto next = [&state]() {
+        state ^= state << 13;
+        state ^= state >> 7;
+        state ^= state << 17;
+        return (double)(state >> 11) * 0x1p-53;
+    };
+    for (int i = 0; i < kMlpParams; ++i) {
+        double fan = (i < kMlpOffB1 || i < kMlpOffW2) ? 2.0 : 64.0;
+        const double lim = 1.0 / sqrt(fan);
+        th[i] = (float)((2.0 * next() - 1.0) * lim);
+    }
+}
+
+}  // namespace
+
+// Per-thread evaluation form of the network (same operation order as the
+// warp form, including the butterfly order of the output sum of lane 0).
+__device__ float mlp_infer_thread(const SamplerSmem& S, float v0, float v1) {
+    float h1[kMlpW], h2[kMlpW];
+    for (int n = 0; n < kMlpW; ++n)
+        h1[n] = siluf_(fmaf(S.W1[2 * n], v0, fmaf(S.W1[2 * n + 1], v1, S.b1[n])));
+    for (int n = 0; n < kMlpW; ++n) h2[n] = siluf_(neuron_dot(S.W2 + n * kBfPad, h1, S.b2[n]));
+    float part[32];
+    for (int l = 0; l < 32; ++l) {
+        float o = 0.0f;
+        for (int q = 0; q < 2; ++q) {
+            const int n = l + 32 * q;
+            o = fmaf(S.w4[n], siluf_(neuron_dot(S.W3 + n * kBfPad, h2, S.b3[n])), o);
+        }
+        part[l] = o;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        float nxt[32];
+        for (int l = 0; l < 32; ++l) nxt[l] = part[l] + part[l ^ off];
+        for (int l = 0; l < 32; ++l) part[l] = nxt[l];
+    }
+    return sigmoidf_(part[0] + S.b4 + anchor_of_v1(v1));
+}
+
+// Max |CDF(chi, x_net(chi, u)) - u| per bin over kEvalSub rows per bin and a
+// uniform grid of u; rows of `cdf` are the evaluation rows.
+__global__ void k_sampler_eval(const __nv_bfloat16* __restrict__ w, const float* __restrict__ cdf,
+                               int nrows, int M, float log10_lo, float log10_hi,
+                               unsigned int* __restrict__ bin_err_bits) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    SamplerSmem& S = *reinterpret_cast<SamplerSmem*>(dyn_smem);
+    stage_sampler(S, w, cdf, 0, 0ull);
+    __syncthreads();
+    const int row = blockIdx.x;
+    if (row >= nrows) return;
+    const float l10 = log10_lo + (log10_hi - log10_lo) * ((float)row + 0.5f) / (float)nrows;
+    const int bin = min(max((int)((l10 - kMlpLog10Lo) * 16.0f), 0), 63);
+    float worst = 0.0f;
+    for (int k = threadIdx.x; k < kEvalU; k += blockDim.x) {
+        const float u = ((float)k + 0.5f) / (float)kEvalU;
+        const float x = mlp_infer_thread(S, l10 * 0.5f, mlp_input_u(u));
+        const float c = cdf_row_at(cdf + (size_t)row * (M + 1), M, x);
+        worst = fmaxf(worst, fabsf(c - u));
+    }
+    atomicMax(&bin_err_bits[bin], __float_as_uint(worst));
+}
+
+// x = Q(chi, u): the exact table inverse (bilinear in log10 chi and the CDF
+// node interval) or the network in its per-thread form.
+__global__ void k_sampler_quantile(const __nv_bfloat16* __restrict__ w, const float* __restrict__ cdf,
+                                   int nrows, int M, const float* __restrict__ log10chi,
+                                   const float* __restrict__ u, float* __restrict__ x, long long n,
+                                   int use_net) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    SamplerSmem& S = *reinterpret_cast<SamplerSmem*>(dyn_smem);
+    if (use_net) stage_sampler(S, w, cdf, 0, 0ull);
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float l10 = fminf(fmaxf(log10chi[i], kMlpLog10Lo), kMlpLog10Hi);
+        if (use_net) {
+            x[i] = mlp_infer_thread(S, l10 * 0.5f, mlp_input_u(u[i]));
+        } else {
+            const float pos = (l10 - kMlpLog10Lo) / (kMlpLog10Hi - kMlpLog10Lo) * (float)(nrows - 1);
+            const int r = min((int)pos, nrows - 2);
+            const float wgt = pos - (float)r;
+            const float xa = cdf_row_inverse(cdf + (size_t)r * (M + 1), M, u[i]);
+            const float xb = cdf_row_inverse(cdf + (size_t)(r + 1) * (M + 1), M, u[i]);
+            x[i] = xa + wgt * (xb - xa);
+        }
+    }
+}
+
+extern "C" {
+
+qed_status qed_sampler_quantile(qed_ctx* ctx, const float* log10chi, const float* u, float* x,
+                                int64_t n, int use_net) {
+    if (!ctx || n < 0 || (n > 0 && (!log10chi || !u || !x)))
+        return set_err(ctx, QED_ERR_ARG, "qed_sampler_quantile: bad argument");
+    if (use_net && !ctx->net_ready) return set_err(ctx, QED_ERR_STATE, "no sampler trained or loaded");
+    qed_status st = sampler_alloc(ctx, 0);
+    if (st != QED_OK || n == 0) return st;
+    long long blocks = (n + 127) / 128;
+    if (blocks > ctx->sms * 8) blocks = ctx->sms * 8;
+    k_sampler_quantile<<<(int)blocks, 128, use_net ? sizeof(SamplerSmem) : 0, ctx->stream>>>(
+        ctx->d_wbf, ctx->d_cdf, kCdfRows, kCdfM, log10chi, u, x, n, use_net);
+    return cuda_check(ctx, cudaGetLastError(), "qed_sampler_quantile");
+}
+
+qed_status qed_sampler_train(qed_ctx* ctx, uint64_t seed, int64_t samples, int batch, float lr,
+                             float* final_loss) {
+    if (!ctx) return QED_ERR_ARG;
+    if (samples <= 0 || batch < kTileS || batch > (1 << 20) || !(lr > 0.0f))
+        return set_err(ctx, QED_ERR_ARG, "qed_sampler_train: bad argument");
+    qed_status st = sampler_alloc(ctx, batch);
+    if (st != QED_OK) return st;
+    if (!ctx->net_ready) {
+        float th[kMlpParams];
+        sampler_init_host(seed, th);
+        QED_CUDA(ctx, cudaMemcpyAsync(ctx->d_theta, th, sizeof th, cudaMemcpyHostToDevice,
+                                      ctx->stream));
+        QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_m1, 0, sizeof(float) * kMlpParams, ctx->stream));
+    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_m2, 0, sizeof(float) * kMlpParams, ctx->stream));
+    const long long steps = (samples + batch - 1) / batch;
+    const int ntiles = (batch + kTileS - 1) / kTileS;
+    const int grid = std::min(ntiles, ctx->sms * 2);
+    float* v = ctx->d_batch;
+    float* tgt = ctx->d_batch + 2 * (size_t)batch;
+    float* wgt = ctx->d_batch + 3 * (size_t)batch;
+    const float b1 = 0.9f, b2 = 0.999f;
+    double p1 = 1.0, p2 = 1.0;
+    for (long long k = 0; k < steps; ++k) {
+        k_sampler_batch<<<(batch + 255) / 256, 256, 0, ctx->stream>>>(
+            (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)k, batch, ctx->d_cdf, kCdfRows, kCdfM,
+            v, tgt, wgt);
+        const bool last = k + 1 == steps;
+        if (last) QED_CUDA(ctx, cudaMemsetAsync(ctx->d_loss, 0, sizeof(float), ctx->stream));
+        k_mlp_grad<<<grid, 256, sizeof(TrainSmem), ctx->stream>>>(
+            ctx->d_theta, v, tgt, wgt, batch, 1, ctx->d_cdf, kCdfRows, kCdfM, ctx->d_partial,
+            last ? ctx->d_loss : nullptr);
+        p1 *= b1;
+        p2 *= b2;
+        // cosine decay of the step size over the run
+        const float lr_k = lr * 0.5f * (1.0f + cosf(3.14159265f * (float)k / (float)steps));
+        k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, ctx->stream>>>(
+            ctx->d_partial, grid, ctx->d_theta, ctx->d_m1, ctx->d_m2, ctx->d_wbf, lr_k, b1, b2,
+            1e-8f, (float)(1.0 - p1), (float)(1.0 - p2), 1, nullptr);
+        QED_CUDA(ctx, cudaGetLastError());
+    }
+    ctx->adam_t += steps;
+    ctx->net_ready = 1;
+    ctx->net_bins = 0;   // evaluate before use
+    if (final_loss) {
+        QED_CUDA(ctx, cudaMemcpyAsync(final_loss, ctx->d_loss, sizeof(float), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    }
+    QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return QED_OK;
+}
+
+qed_status qed_sampler_evaluate(qed_ctx* ctx, float* bin_err, int nbins) {
+    if (!ctx || !bin_err || nbins != QED_SAMPLER_BINS) return QED_ERR_ARG;
+    if (!ctx->net_ready) return set_err(ctx, QED_ERR_STATE, "no sampler trained or loaded");
+    qed_status st = sampler_alloc(ctx, 0);
+    if (st != QED_OK) return st;
+    const int rows = QED_SAMPLER_BINS * kEvalSub;
+    float* cdf = nullptr;
+    float* tot = nullptr;
+    unsigned int* bits = nullptr;
+    QED_CUDA(ctx, cudaMalloc(&cdf, sizeof(float) * (size_t)rows * (kCdfM + 1)));
+    QED_CUDA(ctx, cudaMalloc(&tot, sizeof(float) * rows));
+    QED_CUDA(ctx, cudaMalloc(&bits, sizeof(unsigned int) * QED_SAMPLER_BINS));
+    QED_CUDA(ctx, cudaMemsetAsync(bits, 0, sizeof(unsigned int) * QED_SAMPLER_BINS, ctx->stream));
+    // rows at the centres of rows equal sub-intervals of [-2, 2]
+    const float half = 0.5f * (kMlpLog10Hi - kMlpLog10Lo) / rows;
+    k_cdf_rows<<<rows, 256, 0, ctx->stream>>>(kMlpLog10Lo + half, kMlpLog10Hi - half, rows, kCdfM,
+                                              cdf, tot);
+    k_sampler_eval<<<rows, 128, sizeof(SamplerSmem), ctx->stream>>>(
+        ctx->d_wbf, cdf, rows, kCdfM, kMlpLog10Lo, kMlpLog10Hi, bits);
+    unsigned int hb[QED_SAMPLER_BINS];
+    st = cuda_check(ctx, cudaMemcpyAsync(hb, bits, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream),
+                    "copy bins");
+    if (st == QED_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "evaluate");
+    cudaFree(cdf);
+    cudaFree(tot);
+    cudaFree(bits);
+    if (st != QED_OK) return st;
+    unsigned long long ok = 0;
+    for (int b = 0; b < QED_SAMPLER_BINS; ++b) {
+        float e;
+        memcpy(&e, &hb[b], sizeof e);
+        bin_err[b] = e;
+        if (e <= ctx->cfg.sampler_max_err) ok |= 1ull << b;
+    }
+    ctx->net_bins = ok;
+    return QED_OK;
+}
+
+qed_status qed_sampler_gradient(qed_ctx* ctx, const float* params, const float* v,
+                                const float* target, const float* weight, int64_t B, float* grad,
+                                float* loss) {
+    if (!ctx || !params || !v || !target || !grad || B < 1 || B > (1 << 24))
+        return set_err(ctx, QED_ERR_ARG, "qed_sampler_gradient: bad argument");
+    qed_status st = sampler_alloc(ctx, 0);
+    if (st != QED_OK) return st;
+    const int ntiles = (int)((B + kTileS - 1) / kTileS);
+    const int grid = std::min(ntiles, ctx->sms * 2);
+    if (loss) QED_CUDA(ctx, cudaMemsetAsync(loss, 0, sizeof(float), ctx->stream));
+    k_mlp_grad<<<grid, 256, sizeof(TrainSmem), ctx->stream>>>(params, v, target, weight, (int)B,
+                                                              0, nullptr, 0, 0, ctx->d_partial,
+                                                              loss);
+    k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, ctx->stream>>>(
+        ctx->d_partial, grid, nullptr, nullptr, nullptr, nullptr, 0.0f, 0.0f, 0.0f, 0.0f, 1.0f,
+        1.0f, 0, grad);
+    return cuda_check(ctx, cudaGetLastError(), "qed_sampler_gradient");
+}
+
+qed_status qed_sampler_load(qed_ctx* ctx, const float* params, int64_t n) {
+    if (!ctx || !params || n != kMlpParams) return QED_ERR_ARG;
+    qed_status st = sampler_alloc(ctx, 0);
+    if (st != QED_OK) return st;
+    QED_CUDA(ctx, cudaMemcpyAsync(ctx->d_theta, params, sizeof(float) * kMlpParams,
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    // refresh the BF16 copy with a zero-step Adam pass over a zero gradient
+    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_partial, 0, sizeof(float) * kMlpParams, ctx->stream));
+    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_m1, 0, sizeof(float) * kMlpParams, ctx->stream));
+    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_m2, 0, sizeof(float) * kMlpParams, ctx->stream));
+    k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, ctx->stream>>>(
+        ctx->d_partial, 1, ctx->d_theta, ctx->d_m1, ctx->d_m2, ctx->d_wbf, 0.0f, 0.9f, 0.999f, 1e-8f,
+        1.0f, 1.0f, 1, nullptr);
+    QED_CUDA(ctx, cudaGetLastError());
+    QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->net_ready = 1;
+    ctx->net_bins = 0;
+    return QED_OK;
+}
+
+qed_status qed_sampler_save(qed_ctx* ctx, float* params, int64_t n) {
+    if (!ctx || !params || n != kMlpParams) return QED_ERR_ARG;
+    if (!ctx->net_ready) return set_err(ctx, QED_ERR_STATE, "no sampler trained or loaded");
+    QED_CUDA(ctx, cudaMemcpyAsync(params, ctx->d_theta, sizeof(float) * kMlpParams,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return QED_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of the launch settings
+// ---------------------------------------------------------------------------
+namespace {
+
+// Copy rows [0, n) of every array between the store and the mirror.
+qed_status copy_store(qed_ctx* ctx, const qed_particles* p, long long n, bool to_mirror) {
+    float* f_store[] = {p->px, p->py, p->pz, p->Ex, p->Ey, p->Ez, p->Bx, p->By, p->Bz, p->w};
+    float* f_mirror[] = {ctx->mirror.px, ctx->mirror.py, ctx->mirror.pz, ctx->mirror.Ex,
+                         ctx->mirror.Ey, ctx->mirror.Ez, ctx->mirror.Bx, ctx->mirror.By,
+                         ctx->mirror.Bz, ctx->mirror.w};
+    for (int k = 0; k < 10; ++k) {
+        float* dst = to_mirror ? f_mirror[k] : f_store[k];
+        const float* src = to_mirror ? f_store[k] : f_mirror[k];
+        QED_CUDA(ctx, cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+    }
+    QED_CUDA(ctx, cudaMemcpyAsync(to_mirror ? ctx->mirror.id : p->id, to_mirror ? p->id : ctx->mirror.id,
+                                  sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    QED_CUDA(ctx, cudaMemcpyAsync(to_mirror ? ctx->mirror.type : p->type,
+                                  to_mirror ? p->type : ctx->mirror.type, n,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    if (!to_mirror)
+        QED_CUDA(ctx, cudaMemcpyAsync(p->count, &n, sizeof n, cudaMemcpyHostToDevice, ctx->stream));
+    QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return QED_OK;
+}
+
+}  // namespace
+
+qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, int cold_blocks_per_sm,
+                          int hot_blocks_per_sm) {
+    if (!ctx || cold_blocks_per_sm < 0 || hot_blocks_per_sm < 0) return QED_ERR_ARG;
+    if (hot_min) ctx->hot_min = hot_min;
+    if (cold_blocks_per_sm)
+        ctx->cold_blocks = std::min(ctx->sms * cold_blocks_per_sm, ctx->cold_blocks_max);
+    if (hot_blocks_per_sm)
+        ctx->hot_blocks = std::min(ctx->sms * hot_blocks_per_sm, ctx->hot_blocks_max);
+    return QED_OK;
+}
+
+qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                        const char* out_json) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!particles_ok(p)) return set_err(ctx, QED_ERR_ARG, "qed_autotune: bad argument");
+    qed_status st = ensure_mirror(ctx, p->capacity);
+    if (st != QED_OK) return st;
+    long long n = 0;
+    QED_CUDA(ctx, cudaMemcpyAsync(&n, p->count, sizeof n, cudaMemcpyDeviceToHost, ctx->stream));
+    QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (n < 0 || n > p->capacity) return set_err(ctx, QED_ERR_ARG, "qed_autotune: bad count");
+    st = copy_store(ctx, p, n, true);
+    if (st != QED_OK) return st;
+    cudaEvent_t e0, e1;
+    QED_CUDA(ctx, cudaEventCreate(&e0));
+    QED_CUDA(ctx, cudaEventCreate(&e1));
+    const int cold_max = ctx->cold_blocks_max / ctx->sms, hot_max = ctx->hot_blocks_max / ctx->sms;
+    struct Trial { uint32_t hot_min; int cold, hot; float ms; };
+    std::vector<Trial> trials;
+    auto run = [&](uint32_t hm, int cb, int hb, float* ms) -> qed_status {
+        qed_set_launch(ctx, hm, cb, hb);
+        qed_status s2 = copy_store(ctx, p, n, false);
+        if (s2 != QED_OK) return s2;
+        cudaEventRecord(e0, ctx->stream);
+        qed_step_stats stt;
+        s2 = qed_event_step(ctx, p, step_index, &stt);
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        if (s2 != QED_OK) return s2;
+        cudaEventElapsedTime(ms, e0, e1);
+        trials.push_back({hm, cb, hb, *ms});
+        return QED_OK;
+    };
+    float ms = 0.0f, best = 0.0f;
+    uint32_t b_hm = ctx->hot_min;
+    int b_cb = cold_max, b_hb = hot_max;
+    st = run(b_hm, b_cb, b_hb, &best);   // warm-up and reference
+    if (st == QED_OK) st = run(b_hm, b_cb, b_hb, &best);
+    const uint32_t hms[] = {16, 32, 64, 128};
+    for (uint32_t hm : hms) {
+        if (st != QED_OK) break;
+        st = run(hm, b_cb, b_hb, &ms);
+        if (st == QED_OK && ms < best) { best = ms; b_hm = hm; }
+    }
+    for (int cb = 1; cb <= cold_max && st == QED_OK; ++cb) {
+        st = run(b_hm, cb, b_hb, &ms);
+        if (st == QED_OK && ms < best) { best = ms; b_cb = cb; }
+    }
+    for (int hb = 2; hb <= hot_max && st == QED_OK; hb += 2) {
+        st = run(b_hm, b_cb, hb, &ms);
+        if (st == QED_OK && ms < best) { best = ms; b_hb = hb; }
+    }
+    qed_set_launch(ctx, b_hm, b_cb, b_hb);
+    const qed_status st_restore = copy_store(ctx, p, n, false);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != QED_OK) return st;
+    if (st_restore != QED_OK) return st_restore;
+    if (out_json) {
+        FILE* f = fopen(out_json, "w");
+        if (!f) return set_err(ctx, QED_ERR_ARG, "qed_autotune: cannot write the JSON file");
+        fprintf(f, "{\"hot_min\": %u, \"cold_blocks_per_sm\": %d, \"hot_blocks_per_sm\": %d, "
+                   "\"ms\": %.4f, \"trials\": [", b_hm, b_cb, b_hb, best);
+        for (size_t k = 0; k < trials.size(); ++k)
+            fprintf(f, "%s{\"hot_min\": %u, \"cold\": %d, \"hot\": %d, \"ms\": %.4f}",
+                    k ? ", " : "", trials[k].hot_min, trials[k].cold, trials[k].hot, trials[k].ms);
+        fprintf(f, "]}\n");
+        fclose(f);
+    }
     return QED_OK;
 }
 
@@ -1501,7 +2082,7 @@ qed_status noalloc_setup(int dev, NoAllocDevice* out) {
             return QED_ERR_CUDA;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_cold, k_cold, kColdThreads, 0) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot, kHotThreads, 0) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot<false>, kHotThreads, 0) !=
                 cudaSuccess)
             return QED_ERR_CUDA;
         d.base = static_cast<unsigned char*>(ptr);
@@ -1547,7 +2128,7 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     DevCtl h;
     for (int pass = 0; pass < max_passes; ++pass) {
         k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
-        k_hot<<<nd.hot_blocks, kHotThreads, 0, s>>>(D, SP, S, ctl);
+        k_hot<false><<<nd.hot_blocks, kHotThreads, 0, s>>>(D, SP, S, ctl);
         k_advance<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, cascade ? 1 : 0, max_passes, 0ull, 0);
         if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
         if (!cascade) break;

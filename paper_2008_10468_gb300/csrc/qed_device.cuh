@@ -144,11 +144,13 @@ __device__ __forceinline__ float chi_f32(bool photon, float px, float py, float 
 constexpr int kSynCoef = 2 * (QED_SYN_DEG + 1);   // F and G coefficients per piece
 constexpr int kSynStride = 32;                     // pieces padded to one bank row
 
-// Shared-memory form of the table: c[j][p] = (F_j, G_j) of piece p.  Lanes of a
-// warp reading power j of different pieces hit different banks (pieces p and
-// p + 16 share a bank pair), and one 64-bit load serves both functions.
+// Shared-memory form of the table: coefficient-major, c[j][p] is power j of
+// piece p (F in rows 0..DEG, G in rows DEG+1..2DEG+1).  Lanes of a warp
+// reading power j of different pieces hit different banks (22 pieces fit in
+// one row of 32 banks); 64-bit (F, G) pairs would share 16 bank pairs among
+// 22 pieces and conflict.
 struct SynTable {
-    float2 c[QED_SYN_DEG + 1][kSynStride];
+    float c[kSynCoef][kSynStride];
     unsigned int lam_mask;   // bit p set: piece p carries the exp(-x) envelope
 };
 
@@ -161,13 +163,12 @@ __device__ __forceinline__ void synchrotron_FG(const SynTable& tb, float x, floa
     const int piece = small ? 0 : k - QED_SYN_KMIN + 1;
     float t = small ? u * u : l2 - (float)k;
     t = fminf(t, 1.02f);
-    float2 c = tb.c[QED_SYN_DEG][piece];
-    float pf = c.x, pg = c.y;
+    float pf = tb.c[QED_SYN_DEG][piece];
+    float pg = tb.c[2 * QED_SYN_DEG + 1][piece];
 #pragma unroll
     for (int j = QED_SYN_DEG - 1; j >= 0; --j) {
-        c = tb.c[j][piece];
-        pf = fmaf(pf, t, c.x);
-        pg = fmaf(pg, t, c.y);
+        pf = fmaf(pf, t, tb.c[j][piece]);
+        pg = fmaf(pg, t, tb.c[QED_SYN_DEG + 1 + j][piece]);
     }
     const float lam = ((tb.lam_mask >> piece) & 1u) ? 1.0f : 0.0f;
     const float env = u * expf(-lam * x);
@@ -179,11 +180,9 @@ __device__ __forceinline__ void synchrotron_FG(const SynTable& tb, float x, floa
 // Copy the synchrotron table into shared memory (call with all threads of
 // the block, then __syncthreads()).
 __device__ __forceinline__ void stage_syn_table(SynTable& tb) {
-    for (int i = threadIdx.x; i < (QED_SYN_DEG + 1) * kSynStride; i += blockDim.x) {
+    for (int i = threadIdx.x; i < kSynCoef * kSynStride; i += blockDim.x) {
         const int j = i / kSynStride, p = i % kSynStride;
-        tb.c[j][p] = p < QED_SYN_NPIECE
-                         ? make_float2(qed_syn_table[p][j], qed_syn_table[p][QED_SYN_DEG + 1 + j])
-                         : make_float2(0.0f, 0.0f);
+        tb.c[j][p] = p < QED_SYN_NPIECE ? qed_syn_table[p][j] : 0.0f;
     }
     if (threadIdx.x == 0) {
         unsigned int m = 0;
@@ -209,6 +208,18 @@ __device__ __forceinline__ float bound_emission(float b, float c) {
     return c * (lead + 0.1f * b);
 }
 
+// The same bound from l2b = log2(b) (b > 0): the powers as exp2(a l2b) on the
+// special-function unit (relative error ~3e-7, far inside the planner's
+// 2e-5 safety band).
+__device__ __forceinline__ float bound_emission_l2(float b, float l2b, float c) {
+    float lead;
+    if (b < 0.1f) lead = 0.56f * kPi * b;
+    else if (b < 0.5f) lead = 0.45f * kPi * exp2f(l2b * (11.0f / 12.0f));
+    else if (b < 10.0f) lead = 0.42f * kPi * exp2f(l2b * (19.0f / 24.0f));
+    else lead = 0.55f * kPi * exp2f(l2b * (2.0f / 3.0f));
+    return c * (lead + 0.1f * b);
+}
+
 // x -> 0 limit of 3 x^2 P(x^3) over c b^{2/3}:  4 pi / (sqrt3 Gamma(1/3) 2^{1/3}).
 constexpr float kSmallF = 2.14952824153447863f;
 
@@ -225,15 +236,17 @@ struct ftime {
 
 __device__ __forceinline__ bool time_positive(ftime t) { return t.hi > 0.0f; }
 
-// t / N for an integer N >= 1, to float-float precision.
+// t / N for an integer N >= 1, to float-float precision: an approximate
+// reciprocal, one exact-residual correction of the leading part, then the
+// trailing part from the exact remainder (error-free products via FMA).
 __device__ __forceinline__ ftime time_div(ftime t, uint32_t N) {
     const float n = (float)N;                 // exact for N <= 2^24; N <= 2^30 rounds
-    const float q = __fdiv_rn(t.hi, n);
-    // residual t - q n, exact products through FMA
-    const float p = __fmul_rn(q, n);
-    const float pe = __fmaf_rn(q, n, -p);
-    const float r = __fadd_rn(__fsub_rn(__fsub_rn(t.hi, p), pe), t.lo);
-    const ff out = fast_two_sum(q, __fdiv_rn(r, n));
+    const float r = __fdividef(1.0f, n);
+    float q = t.hi * r;
+    q = __fmaf_rn(__fmaf_rn(-q, n, t.hi), r, q);
+    const ff qn = two_prod(q, n);
+    const float rem = __fadd_rn(__fsub_rn(__fsub_rn(t.hi, qn.hi), qn.lo), t.lo);
+    const ff out = fast_two_sum(q, rem * r);
     return {out.hi, out.lo};
 }
 
@@ -252,6 +265,14 @@ struct Plan {
     ftime h;         // sub-step length (periods)
     bool guard;      // N raised by the validity guard
     bool safe;       // N cannot change within +-1e-5 (relative) of chi and f
+    float chi, eps;  // quantum parameter and energy the plan was made from
+};
+
+// The step constants the planner reads, passed by value so that the
+// out-of-line slow path takes them in registers (a reference to the kernel's
+// parameter block would make the whole block addressable, i.e. a local copy).
+struct PlanConst {
+    float K, inv_Es, inv_p_max, pair_coeff;
 };
 
 struct StepParams {
@@ -260,8 +281,16 @@ struct StepParams {
     float K;             // sqrt3 R / pi  (1 / period)
     float inv_Es;        // 1 / Schwinger field (code units)
     float p_max;
+    float inv_p_max;     // 1 / p_max
     float pair_coeff;
     ftime t_step;        // dt as float-float
+    const uint32_t* step_base;  // graph runs: device step base added to `step`
+    uint32_t hot_min;           // plans with at least this many sub-steps use the warp path
+    int sampler;                // learned sampler on (e+- in usable bins)
+    int net_rows;               // rows of the total-probability table
+    unsigned long long net_bins;  // usable bins (64, uniform in log10 chi over [-2, 2))
+    const void* net_w;          // BF16 network weights (8577)
+    const float* net_wtot;      // total probability per c along log10 chi
     uint32_t step;       // global step index (Philox counter word 2)
     uint32_t process_mask;
     int recoil;
@@ -299,24 +328,32 @@ __device__ __forceinline__ int emission_piece(float b) {
     return b < 0.1f ? 0 : (b < 0.5f ? 1 : (b < 10.0f ? 2 : 3));
 }
 
-// Plan the sub-steps of the remaining time T (Algorithms 1/2, line 1).
+// Plan the sub-steps of the remaining time T (Algorithms 1/2, planning).
 // `safe` reports whether N is certain when chi carries a relative error of up
 // to 1e-5: every f(b) piece grows at most linearly in b, so f moves by less
 // than 2e-5 relative unless b crosses a piece boundary.
-__device__ __forceinline__ Plan make_plan(const StepParams& P, const float* __restrict__ sqz_e,
+__device__ __forceinline__ PlanConst plan_const(const StepParams& P) {
+    return PlanConst{P.K, P.inv_Es, P.inv_p_max, P.pair_coeff};
+}
+
+__device__ __forceinline__ Plan make_plan(const PlanConst& P, const float* __restrict__ sqz_e,
                                           const float* __restrict__ sqz_p, bool photon, float chi,
                                           float eps, ftime T) {
     constexpr float d = 2e-5f;
     Plan pl;
+    pl.chi = chi;
+    pl.eps = eps;
     pl.b = 1.5f * chi;
-    const float inv_eps = 1.0f / eps;
+    const float inv_eps = __fdividef(1.0f, eps);
     const float c_rem = P.K * T.hi * inv_eps;
     const float b = pl.b;
-    const float f = photon ? P.pair_coeff * c_rem * b : bound_emission(b, c_rem);
-    const float q = f / P.p_max;
+    const float l2b = __log2f(b);
+    const float f = photon ? P.pair_coeff * c_rem * b
+                           : (b > 0.0f ? bound_emission_l2(b, l2b, c_rem) : 0.0f);
+    const float q = f * P.inv_p_max;
     float N = fmaxf(1.0f, ceilf(q));
     float b23 = 0.0f;
-    if (b > 0.0f) b23 = exp2f(__log2f(b) * (2.0f / 3.0f));
+    if (b > 0.0f) b23 = exp2f(l2b * (2.0f / 3.0f));
     pl.guard = false;
     float graw = 0.0f;
     if (!photon) {
@@ -342,18 +379,17 @@ __device__ __forceinline__ Plan make_plan(const StepParams& P, const float* __re
 
 // Slow path of plan_particle: chi in float-float, then the plan.  Kept out of
 // line so that the common path does not carry its registers.
-__device__ __noinline__ Plan plan_slow(const StepParams& P, const float* __restrict__ sqz_e,
+__device__ __noinline__ Plan plan_slow(PlanConst P, const float* __restrict__ sqz_e,
                                        const float* __restrict__ sqz_p, bool photon, float px,
                                        float py, float pz, float Ex, float Ey, float Ez, float Bx,
-                                       float By, float Bz, ftime T, float* chi_out,
-                                       float* eps_out) {
+                                       float By, float Bz, ftime T) {
     float eps;
     const float chi = chi_ff(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps);
-    *chi_out = chi;
-    *eps_out = eps;
-    Plan pl;
     if (!(eps > 0.0f)) {
+        Plan pl;
         pl.N = 0;
+        pl.chi = chi;
+        pl.eps = eps;
         return pl;
     }
     return make_plan(P, sqz_e, sqz_p, photon, chi, eps, T);
@@ -361,11 +397,12 @@ __device__ __noinline__ Plan plan_slow(const StepParams& P, const float* __restr
 
 // chi and the plan of a particle: binary32 chi when it is well conditioned and
 // the plan is safe, otherwise chi in float-float (and the plan again).
-__device__ __forceinline__ Plan plan_particle(const StepParams& P, const float* __restrict__ sqz_e,
+__device__ __forceinline__ Plan plan_particle(const StepParams& SP, const float* __restrict__ sqz_e,
                                               const float* __restrict__ sqz_p, bool photon,
                                               float px, float py, float pz, float Ex, float Ey,
                                               float Ez, float Bx, float By, float Bz, ftime T,
                                               float* chi_out, float* eps_out) {
+    const PlanConst P = plan_const(SP);
     bool wc;
     float eps;
     const float chi = chi_f32(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps, &wc);
@@ -377,8 +414,10 @@ __device__ __forceinline__ Plan plan_particle(const StepParams& P, const float* 
             return pl;
         }
     }
-    return plan_slow(P, sqz_e, sqz_p, photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, T, chi_out,
-                     eps_out);
+    const Plan pl = plan_slow(P, sqz_e, sqz_p, photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, T);
+    *chi_out = pl.chi;
+    *eps_out = pl.eps;
+    return pl;
 }
 
 // Acceptance function of Algorithm 1 (emission, delta = x^3, Eq. 1):

@@ -21,6 +21,7 @@ ELECTRON, POSITRON, PHOTON, REMOVED = 0, 1, 2, 3
 FLOAT_FIELDS = ("px", "py", "pz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "w")
 KERNEL_KINDS = ("sweep", "generate", "plan", "cold", "hot", "control")
 SPECTRUM_BINS, SPECTRUM_LOG10_MIN, SPECTRUM_LOG10_MAX = 240, -4, 8
+SAMPLER_PARAMS, SAMPLER_BINS = 8577, 64
 
 
 class QEDError(RuntimeError):
@@ -33,7 +34,8 @@ class Config(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("dt_periods", C.c_double), ("lambda_m", C.c_double),
                 ("p_max", C.c_float), ("pair_bound_coeff", C.c_float),
                 ("process_mask", C.c_uint32), ("cascade_in_step", C.c_int32),
-                ("recoil", C.c_int32), ("max_passes", C.c_int32), ("drain_chi", C.c_float)]
+                ("recoil", C.c_int32), ("max_passes", C.c_int32), ("drain_chi", C.c_float),
+                ("sampler_mode", C.c_int32), ("sampler_max_err", C.c_float)]
 
 
 class Particles(C.Structure):
@@ -46,7 +48,8 @@ class StepStats(C.Structure):
                 ("children", C.c_uint64), ("guard_hits", C.c_uint64), ("plans", C.c_uint64),
                 ("candidates", C.c_uint64), ("max_N", C.c_uint32), ("status", C.c_int32),
                 ("required_capacity", C.c_int64), ("count", C.c_int64), ("passes", C.c_int32),
-                ("reserved", C.c_int32), ("substeps_warp", C.c_uint64)]
+                ("reserved", C.c_int32), ("substeps_warp", C.c_uint64),
+                ("sampler_events", C.c_uint64)]
 
 
 EVENT_DTYPE = np.dtype([("parent_id", np.uint64), ("child0", np.uint64), ("child1", np.uint64),
@@ -94,6 +97,23 @@ def lib():
         L.qed_graph_launch.restype = st
         L.qed_graph_read_stats.argtypes = [vp, C.POINTER(StepStats), C.c_int]
         L.qed_graph_read_stats.restype = st
+        fp = C.POINTER(C.c_float)
+        L.qed_sampler_train.argtypes = [vp, u64, i64, C.c_int, C.c_float, fp]
+        L.qed_sampler_train.restype = st
+        L.qed_sampler_evaluate.argtypes = [vp, fp, C.c_int]
+        L.qed_sampler_evaluate.restype = st
+        L.qed_sampler_gradient.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp]
+        L.qed_sampler_gradient.restype = st
+        L.qed_sampler_quantile.argtypes = [vp, vp, vp, vp, i64, C.c_int]
+        L.qed_sampler_quantile.restype = st
+        L.qed_sampler_load.argtypes = [vp, fp, i64]
+        L.qed_sampler_load.restype = st
+        L.qed_sampler_save.argtypes = [vp, fp, i64]
+        L.qed_sampler_save.restype = st
+        L.qed_set_launch.argtypes = [vp, C.c_uint32, C.c_int, C.c_int]
+        L.qed_set_launch.restype = st
+        L.qed_autotune.argtypes = [vp, C.POINTER(Particles), u64, C.c_char_p]
+        L.qed_autotune.restype = st
         L.qed_profile_enable.argtypes = [vp, C.c_int]
         L.qed_profile_enable.restype = st
         L.qed_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]
@@ -173,7 +193,8 @@ class Context:
 
     def __init__(self, seed=20081046, dt=0.1, lambda_m=1e-6, p_max=0.01, pair_coeff=0.1,
                  process_mask=PROC_EMISSION | PROC_PAIR, cascade=True, recoil=True,
-                 max_passes=64, drain_chi=0.0, stream=None):
+                 max_passes=64, drain_chi=0.0, sampler=False, sampler_max_err=1e-3,
+                 stream=None):
         L = lib()
         cfg = Config()
         L.qed_config_default(C.byref(cfg))
@@ -187,6 +208,8 @@ class Context:
         cfg.recoil = int(bool(recoil))
         cfg.max_passes = int(max_passes)
         cfg.drain_chi = float(drain_chi)
+        cfg.sampler_mode = int(bool(sampler))
+        cfg.sampler_max_err = float(sampler_max_err)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -286,6 +309,47 @@ class Context:
         if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_STATE):
             self._check(st)
         return [stats_dict(out[k]) for k in range(n)]
+
+    def sampler_train(self, seed, samples, batch=4096, lr=3e-3):
+        loss = C.c_float()
+        self._check(lib().qed_sampler_train(self._h, int(seed), int(samples), int(batch),
+                                            float(lr), C.byref(loss)))
+        return float(loss.value)
+
+    def sampler_evaluate(self):
+        err = (C.c_float * SAMPLER_BINS)()
+        self._check(lib().qed_sampler_evaluate(self._h, err, SAMPLER_BINS))
+        return np.array(err[:])
+
+    def sampler_gradient(self, params, v, target, grad, loss=None, weight=None):
+        self._check(lib().qed_sampler_gradient(self._h, _ptr(params), _ptr(v), _ptr(target),
+                                               _ptr(weight), int(target.numel()), _ptr(grad),
+                                               _ptr(loss)))
+
+    def sampler_quantile(self, log10chi, u, x, use_net=True):
+        self._check(lib().qed_sampler_quantile(self._h, _ptr(log10chi), _ptr(u), _ptr(x),
+                                               int(x.numel()), int(bool(use_net))))
+
+    def sampler_load(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(lib().qed_sampler_load(self._h, a.ctypes.data_as(C.POINTER(C.c_float)),
+                                           a.size))
+
+    def sampler_save(self):
+        a = np.empty(SAMPLER_PARAMS, dtype=np.float32)
+        self._check(lib().qed_sampler_save(self._h, a.ctypes.data_as(C.POINTER(C.c_float)),
+                                           a.size))
+        return a
+
+    def set_launch(self, hot_min=0, cold_blocks_per_sm=0, hot_blocks_per_sm=0):
+        self._check(lib().qed_set_launch(self._h, int(hot_min), int(cold_blocks_per_sm),
+                                         int(hot_blocks_per_sm)))
+
+    def autotune(self, store, step, out_json=None):
+        """Pick the fastest launch settings for `store` (left unchanged)."""
+        p = store.struct()
+        path = out_json.encode() if out_json else None
+        self._check(lib().qed_autotune(self._h, C.byref(p), int(step), path))
 
     def profile(self, enable=True):
         self._check(lib().qed_profile_enable(self._h, int(bool(enable))))

@@ -1,6 +1,6 @@
 """Event-by-event comparison of the CUDA event generator with the oracle.
 
-Protocol (the benchmark spec tolerances, readings in the design notes):
+Protocol:
   * Each particle's events (sub-step index s, kind, child ids) must be
     identical on both sides, up to the particle's first near-tie recorded by
     the oracle: a draw with |y - P| <= 1e-5, or a plan whose sub-step count

@@ -110,8 +110,8 @@ def test_graph_equals_eager_steps():
     e_stats = eager(50, 5)
     g_store, g_stats, ctx, store = _graph_steps(arr, cap, 50, 5, seed=99)
     _same(e_stats, g_stats, estore.to_numpy(), g_store)
-    # a second launch continues from the evolved store (same step indices)
-    e_stats2 = eager(50, 5)
+    # a second launch continues from the evolved store with steps 55..59
+    e_stats2 = eager(55, 5)
     ctx.graph_launch()
     g_stats2 = ctx.graph_read_stats()
     assert all(s["status"] == 0 for s in g_stats2), [s["status"] for s in g_stats2]

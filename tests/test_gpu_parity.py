@@ -120,7 +120,7 @@ def test_synchrotron_full_sweep_sampled():
 
 
 # --------------------------------------------------------------------------
-# Planner (Algorithms 1/2, line 1; Sec. 3.1.1)
+# Planner (Algorithms 1/2, planning; Sec. 3.1.1)
 # --------------------------------------------------------------------------
 def _oracle_plans(cf, arr, rows):
     chi = np.zeros(len(rows))

@@ -1,0 +1,128 @@
+"""The learned inverse-CDF sampler: gradients against the FP64 oracle
+network, the exact CDF tables against the oracle's spectrum, training to a
+per-bin error, and the statistics of events drawn through it.  GPU only."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import mlp
+from tests import refs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2008_10468_gb300 import qed  # noqa: E402
+
+SQRT3 = math.sqrt(3.0)
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def test_gradient_matches_oracle_network():
+    ctx = qed.Context()
+    rng = np.random.default_rng(4)
+    B = 1000                          # not a multiple of the 64-sample tile
+    th = mlp.init(5).astype(np.float32)
+    l10 = rng.uniform(-2, 2, B)
+    u = rng.uniform(0, 1, B)
+    v = mlp.inputs(l10, u).astype(np.float32)
+    t = rng.uniform(0.05, 0.95, B).astype(np.float32)
+    wt = rng.uniform(0.2, 5.0, B).astype(np.float32)
+    grad = torch.zeros(mlp.N_PARAMS, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    ctx.sampler_gradient(_dev(th), _dev(v), _dev(t), grad, loss, weight=_dev(wt))
+    lo, go = mlp.loss_and_grad(th.astype(np.float64), v.astype(np.float64), t.astype(np.float64),
+                               wt.astype(np.float64))
+    assert float(loss.item()) == pytest.approx(lo, rel=2e-5)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(g - go)) <= 2e-4 * np.max(np.abs(go))
+
+
+def _oracle_cdf(b, x):
+    """int_0^x 3x'^2 P(x'^3) dx' / int_0^1 (oracle acceptance function, Gauss-Legendre)."""
+    xs, ws = np.polynomial.legendre.leggauss(24)
+
+    def integ(a, c, panels):
+        edges = np.linspace(a, c, panels + 1)
+        tot = 0.0
+        for lo, hi in zip(edges[:-1], edges[1:]):
+            for xx, ww in zip(0.5 * (lo + hi) + 0.5 * (hi - lo) * xs, ws):
+                tot += 0.5 * (hi - lo) * ww * O.Pm(b, 1.0, float(xx))
+        return tot
+    return integ(0.0, x, 12) / integ(0.0, 1.0, 24)
+
+
+def test_exact_quantile_table_matches_oracle():
+    ctx = qed.Context()
+    rng = np.random.default_rng(9)
+    l10 = rng.uniform(-2, 2, 10).astype(np.float32)
+    u = rng.uniform(0.02, 0.98, 10).astype(np.float32)
+    x = torch.zeros(10, device="cuda")
+    ctx.sampler_quantile(_dev(l10), _dev(u), x, use_net=False)
+    xh = x.cpu().numpy()
+    for i in range(10):
+        b = 1.5 * 10.0 ** float(l10[i])
+        assert abs(_oracle_cdf(b, float(xh[i])) - float(u[i])) < 3e-5, (l10[i], u[i], xh[i])
+
+
+@pytest.fixture(scope="module")
+def trained():
+    ctx = qed.Context(seed=11, sampler=True, sampler_max_err=1e-2)
+    loss = ctx.sampler_train(2024, 1 << 25, batch=4096, lr=3e-3)
+    err = ctx.sampler_evaluate()
+    print("sampler: final loss %.3e, per-bin max CDF error: median %.2e max %.2e"
+          % (loss, np.median(err), err.max()))
+    return ctx, err
+
+
+def test_training_reaches_a_small_cdf_error(trained):
+    ctx, err = trained
+    assert np.median(err) < 5e-3
+    assert err.max() < 5e-2
+    # save / load round trip keeps the network
+    p = ctx.sampler_save()
+    ctx.sampler_load(p)
+    np.testing.assert_array_equal(ctx.sampler_save(), p)
+    assert np.allclose(ctx.sampler_evaluate(), err, rtol=0, atol=1e-7)
+
+
+def test_sampler_events_follow_the_spectrum(trained):
+    ctx, err = trained
+    # identical electrons at chi ~ 3 (an in-range bin), no recoil: the number of
+    # emissions is W dt and their energy fractions follow the exact spectrum
+    M, gamma, chi_t = 3000, 3000.0, 3.0
+    pm = math.sqrt(gamma * gamma - 1.0)
+    E0 = np.float32(chi_t * O.schwinger_field() / (gamma + pm))
+    f32 = np.float32
+    arr = {"px": np.full(M, -pm, f32), "py": np.zeros(M, f32), "pz": np.zeros(M, f32),
+           "Ex": np.zeros(M, f32), "Ey": np.full(M, E0, f32), "Ez": np.zeros(M, f32),
+           "Bx": np.zeros(M, f32), "By": np.zeros(M, f32), "Bz": np.full(M, E0, f32),
+           "w": np.ones(M, f32), "id": np.arange(M, dtype=np.uint64),
+           "type": np.zeros(M, np.uint8)}
+    chi, g = O.chi((-pm, 0.0, 0.0), (0.0, float(E0), 0.0), (0.0, 0.0, float(E0)))
+    bin_ = int((math.log10(chi) + 2) * 16)
+    assert err[bin_] <= 1e-2
+    sctx = qed.Context(seed=77, process_mask=1, cascade=False, recoil=False, sampler=True,
+                       sampler_max_err=1e-2)
+    sctx.sampler_load(ctx.sampler_save())
+    sctx.sampler_evaluate()
+    sctx.set_event_log(1 << 16)
+    store = qed.ParticleStore.from_numpy(arr, capacity=M * 20)
+    st = sctx.event_step(store, 3)
+    ev, _ = sctx.read_event_log()
+    assert st["sampler_events"] == st["emissions"] and st["emissions"] > 1000
+    b = 1.5 * chi
+    W_dt = SQRT3 / math.pi * O.rate_unit() * 0.1 / g * O.total_per_c(0, b)
+    assert abs(st["emissions"] / M - W_dt) < 4 * math.sqrt(W_dt / M)
+    xs = np.cbrt(ev["delta"].astype(np.float64))
+    grid = np.linspace(0, 1, 161)
+    cdf = np.array([_oracle_cdf(b, g_) if g_ > 0 else 0.0 for g_ in grid])
+    from scipy import stats
+    assert stats.kstest(xs, lambda v: np.interp(v, grid, cdf)).pvalue > 0.01

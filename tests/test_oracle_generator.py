@@ -81,7 +81,7 @@ def test_emission_spectrum_ks_against_scipy_cdf():
 
 
 def test_pair_decay_probability_and_spectrum():
-    # A photon is removed at its first pair event (Algorithm 2, line 8).  With
+    # A photon is removed at its first pair event (Algorithm 2).  With
     # a fixed plan of N sub-steps of probability q each, it survives with
     # probability (1 - q)^N.
     M, gamma, chi_t = 4000, 1500.0, 3.0
