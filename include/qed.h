@@ -286,7 +286,7 @@ qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, int cold_blocks_per_sm
                           int hot_blocks_per_sm);
 
 /* Time qed_event_step on `p` (step index step_index) for a coordinate search
- * over the launch settings (warp-path threshold 16/32/64/128, blocks per SM
+ * over the launch settings (warp-path threshold 16 ... 512, blocks per SM
  * of each pass), keep the fastest, and restore the store from a snapshot
  * after every trial (the store is unchanged on return).  Writes the chosen
  * settings and all trial timings as JSON to out_json (host file path,

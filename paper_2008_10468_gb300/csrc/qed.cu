@@ -43,13 +43,14 @@ constexpr double kPiD = 3.14159265358979323846;
 constexpr uint32_t kHotMinDefault = 64;  // plans with N >= hot_min go to the warp path
 
 // Minimum resident blocks per SM requested from the register allocator:
-// 3 x 256 and 6 x 128 threads keep both event kernels at 80 registers
-// (24 warps per SM) without spills.
+// 3 x 256 threads hold the thread pass at 80 registers (24 warps per SM);
+// 8 x 128 hold the warp pass at 64 (32 warps per SM), which measured faster
+// than 6 x 128 at 80 registers despite a few spilled values.
 #ifndef QED_COLD_MIN_BLOCKS
 #define QED_COLD_MIN_BLOCKS 3
 #endif
 #ifndef QED_HOT_MIN_BLOCKS
-#define QED_HOT_MIN_BLOCKS 6
+#define QED_HOT_MIN_BLOCKS 8
 #endif
 constexpr int kColdThreads = 256;
 constexpr int kHotThreads = 128;
@@ -292,64 +293,36 @@ __device__ __forceinline__ long long reserve_rows(const DevParticles& P, DevCtl*
     return slot;
 }
 
-__device__ __forceinline__ void write_child(const DevParticles& P, const Scratch& S, long long j,
-                                            long long parent, float px, float py, float pz,
-                                            uint64_t id, uint8_t type, ftime t_rem) {
-    P.px[j] = px;
-    P.py[j] = py;
-    P.pz[j] = pz;
-    P.Ex[j] = P.Ex[parent];
-    P.Ey[j] = P.Ey[parent];
-    P.Ez[j] = P.Ez[parent];
-    P.Bx[j] = P.Bx[parent];
-    P.By[j] = P.By[parent];
-    P.Bz[j] = P.Bz[parent];
-    P.w[j] = P.w[parent];
-    P.id[j] = id;
-    P.type[j] = type;
-    S.t_rem[j] = t_rem;
-}
-
-// Apply an accepted event (recoil or decay, children, log).  Returns true if
-// the particle was removed (photon decay).
 // The parent's fields, copied to its children.
 struct Fields {
     float Ex, Ey, Ez, Bx, By, Bz;
 };
 
-// Warp form of write_child: lanes 13 r + f (f < 13) store field f of child
-// row r (r < nrows), so the rows are written by one round of parallel stores.
-__device__ __forceinline__ void write_children_warp(const DevParticles& P, const Scratch& S,
-                                                   long long j, int nrows, long long parent,
-                                                   const Fields& F, const float (&p)[2][3],
-                                                   const uint64_t (&cid)[2],
-                                                   const uint8_t (&ctype)[2], ftime t_rem) {
-    const int lane = threadIdx.x & 31;
-    const int r = lane / 13, f = lane - 13 * r;
-    if (r >= nrows) return;
-    const long long d = j + r;
-    switch (f) {
-        case 0: P.px[d] = p[r][0]; break;
-        case 1: P.py[d] = p[r][1]; break;
-        case 2: P.pz[d] = p[r][2]; break;
-        case 3: P.Ex[d] = F.Ex; break;
-        case 4: P.Ey[d] = F.Ey; break;
-        case 5: P.Ez[d] = F.Ez; break;
-        case 6: P.Bx[d] = F.Bx; break;
-        case 7: P.By[d] = F.By; break;
-        case 8: P.Bz[d] = F.Bz; break;
-        case 9: P.w[d] = P.w[parent]; break;
-        case 10: P.id[d] = cid[r]; break;
-        case 11: P.type[d] = ctype[r]; break;
-        default: S.t_rem[d] = t_rem; break;
-    }
+__device__ __forceinline__ void write_child(const DevParticles& P, const Scratch& S, long long j,
+                                            const Fields& F, float w, float px, float py, float pz,
+                                            uint64_t id, uint8_t type, ftime t_rem) {
+    P.px[j] = px;
+    P.py[j] = py;
+    P.pz[j] = pz;
+    P.Ex[j] = F.Ex;
+    P.Ey[j] = F.Ey;
+    P.Ez[j] = F.Ez;
+    P.Bx[j] = F.Bx;
+    P.By[j] = F.By;
+    P.Bz[j] = F.Bz;
+    P.w[j] = w;
+    P.id[j] = id;
+    P.type[j] = type;
+    S.t_rem[j] = t_rem;
 }
+
 
 // Apply an accepted event (recoil or decay, children, log).  Returns true if
 // the particle was removed (photon decay).  Thread callers (write_rows) do
 // everything themselves, sharing one reservation atomic per warp; warp
-// callers (all 32 lanes, identical arguments) reserve on lane 0 and store the
-// child rows across lanes.  The reservation is issued first so that its
+// callers (all 32 lanes, identical arguments) reserve and store on lane 0
+// (13 stores from one lane measured faster than a 13-way divergent split of
+// the stores across lanes).  The reservation is issued first so that its
 // latency overlaps the child-id computation.
 __device__ __forceinline__ bool apply_event(const DevParticles& P, const Scratch& S, const StepParams& SP,
                             DevCtl* ctl, long long i, uint64_t id, bool photon, float x,
@@ -392,13 +365,10 @@ __device__ __forceinline__ bool apply_event(const DevParticles& P, const Scratch
         const uint64_t cids[2] = {id0, id1};
         const uint8_t ctypes[2] = {photon ? (uint8_t)QED_ELECTRON : (uint8_t)QED_PHOTON,
                                    (uint8_t)QED_POSITRON};
-        if (warp_caller) {
-            write_children_warp(P, S, j, nch, i, F, cp, cids, ctypes, t_after);
-        } else {
+        if (!warp_caller || lane == 0)
             for (int r = 0; r < nch; ++r)
-                write_child(P, S, j + r, i, cp[r][0], cp[r][1], cp[r][2], cids[r], ctypes[r],
-                            t_after);
-        }
+                write_child(P, S, j + r, F, P.w[i], cp[r][0], cp[r][1], cp[r][2], cids[r],
+                            ctypes[r], t_after);
     }
     if (!photon) {
         if (SP.recoil) {
@@ -472,92 +442,177 @@ __device__ __forceinline__ uint32_t step_index(const StepParams& SP) {
     return SP.step_base ? SP.step + *SP.step_base : SP.step;
 }
 
-// One thread per particle.  First generation of a step: rows [0, pass_end)
-// with the full step; later generations: rows [pass_begin, pass_end)
-// (children) with their stored remaining time.  Particles whose plan reaches
+// One thread per particle for planning and events, one warp for the draws.
+// First generation of a step: rows [0, pass_end) with the full step; later
+// generations: rows [pass_begin, pass_end) (children) with their stored
+// remaining time.  Each lane plans its row; particles whose plan reaches
 // hot_min sub-steps (or, with the sampler, e+- in a usable chi bin) go to the
-// warp queue at that point.
+// warp queue.  The Philox blocks of the planned sub-steps of all lanes are
+// then laid end to end and drawn 32 at a time by the whole warp (lane f of a
+// round takes block f of the concatenation), so that a warp whose particles
+// plan 1 to 30 sub-steps keeps its lanes busy.  Each particle takes its
+// earliest accepted sub-step (a shared-memory minimum): the same decision as
+// testing its sub-steps in order and stopping at the first acceptance.  Lanes
+// with an event apply it, re-plan the remaining time and take part in the
+// next round.
 __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevParticles P, StepParams SP, Scratch S,
                                                        DevCtl* ctl) {
     const uint32_t step = step_index(SP);
     __shared__ SharedTables sm;
+    __shared__ uint32_t first_acc[kColdThreads];
     stage_tables(sm);
     __syncthreads();
     if (ctl->status == (int)QED_ERR_TIMEOUT) return;
     const int first_pass = ctl->first_pass;
     const long long begin = first_pass ? 0 : ctl->pass_begin;
     const long long end = ctl->pass_end;
-    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    uint32_t* facc = first_acc + (threadIdx.x & ~31);
+    constexpr unsigned int kAll = 0xffffffffu;
+    constexpr uint32_t kNone = 0xffffffffu;
     Stats stats;
     const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
-    for (long long i = begin + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < end;
-         i += stride) {
-        const uint8_t type = P.type[i];
-        if (type > QED_PHOTON) continue;
-        const bool photon = type == QED_PHOTON;
-        if (!process_enabled(SP, photon)) continue;
-        ftime t_rem = first_pass ? SP.t_step : S.t_rem[i];
-        if (!time_positive(t_rem)) continue;
-        const uint64_t id = P.id[i];
-        PState st{P.px[i], P.py[i], P.pz[i]};
-        const float Ex = P.Ex[i], Ey = P.Ey[i], Ez = P.Ez[i];
-        const float Bx = P.Bx[i], By = P.By[i], Bz = P.Bz[i];
-        bool changed = false, removed = false;
-        uint32_t s = 0;
-        uint4 blk = make_uint4(0, 0, 0, 0);
-        uint32_t blk_idx = 0xffffffffu;
-        while (time_positive(t_rem)) {
-            float eps, chi;
-            const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
-                                          Ey, Ez, Bx, By, Bz, t_rem, &chi, &eps);
-            if (!(eps > 0.0f)) break;
-            stats.max_N = max(stats.max_N, pl.N);
-            if (pl.N >= SP.hot_min || (!photon && sampler_bin_ok(SP, chi))) {
-                if (changed) {
-                    P.px[i] = st.px;
-                    P.py[i] = st.py;
-                    P.pz[i] = st.pz;
-                    changed = false;
+    for (long long base = begin + warp * 32; base < end; base += nwarps * 32) {
+        const long long i = base + lane;
+        bool active = false, photon = false, changed = false, removed = false;
+        uint64_t id = 0;
+        PState st{0.0f, 0.0f, 0.0f};
+        float Ex = 0.0f, Ey = 0.0f, Ez = 0.0f, Bx = 0.0f, By = 0.0f, Bz = 0.0f;
+        ftime t_rem{0.0f, 0.0f};
+        if (i < end) {
+            const uint8_t type = P.type[i];
+            photon = type == QED_PHOTON;
+            if (type <= QED_PHOTON && process_enabled(SP, photon)) {
+                t_rem = first_pass ? SP.t_step : S.t_rem[i];
+                if (time_positive(t_rem)) {
+                    active = true;
+                    id = P.id[i];
+                    st = PState{P.px[i], P.py[i], P.pz[i]};
+                    Ex = P.Ex[i]; Ey = P.Ey[i]; Ez = P.Ez[i];
+                    Bx = P.Bx[i]; By = P.By[i]; Bz = P.Bz[i];
                 }
-                push_hot(S, ctl, i, s, t_rem);
-                t_rem = ftime{0.0f, 0.0f};
-                break;
             }
-            stats.plans++;
-            stats.guard += pl.guard ? 1 : 0;
-            bool event = false;
-            for (uint32_t k = 0; k < pl.N; ++k) {
-                const uint32_t b = s >> 1;
-                if (b != blk_idx) {
-                    blk = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, b),
-                                        k0, k1);
-                    blk_idx = b;
-                }
-                const uint32_t rx = (s & 1u) ? blk.z : blk.x;
-                const uint32_t ry = (s & 1u) ? blk.w : blk.y;
-                stats.substeps++;
-                if ((ry >> 9) < pl.T) {
-                    stats.cand++;
-                    const float x = u01(rx);
-                    float delta;
-                    const float Pa = acceptance(sm.syn, photon, pl.b, pl.c_h, x, &delta);
-                    if (u01(ry) < Pa) {
-                        const ftime t_after = (k + 1 == pl.N) ? ftime{0.0f, 0.0f}
-                                                              : time_sub_mul(t_rem, k + 1, pl.h);
-                        removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s,
-                                              t_after, st, stats, true, false,
-                                              Fields{Ex, Ey, Ez, Bx, By, Bz});
-                        changed = true;
-                        ++s;
-                        t_rem = t_after;
-                        event = true;
-                        break;
+        }
+        Plan pl;
+        pl.N = 0;
+        pl.T = 0;
+        pl.b = pl.c_h = 0.0f;
+        float chi = 0.0f, eps = 0.0f;
+        uint32_t s = 0;
+        bool need_plan = active;
+        while (__any_sync(kAll, active)) {
+            if (need_plan) {
+                need_plan = false;
+                pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex, Ey, Ez,
+                                   Bx, By, Bz, t_rem, &chi, &eps);
+                if (!(eps > 0.0f)) {
+                    active = false;
+                } else {
+                    stats.max_N = max(stats.max_N, pl.N);
+                    if (pl.N >= SP.hot_min || (!photon && sampler_bin_ok(SP, chi))) {
+                        if (changed) {
+                            P.px[i] = st.px;
+                            P.py[i] = st.py;
+                            P.pz[i] = st.pz;
+                            changed = false;
+                        }
+                        push_hot(S, ctl, i, s, t_rem);   // the warp path plans again
+                        active = false;
+                    } else {
+                        stats.plans++;
+                        stats.guard += pl.guard ? 1 : 0;
+                        if (pl.T == 0u) {
+                            // a zero squeeze threshold admits no candidate:
+                            // the sub-steps pass without an event
+                            stats.substeps += pl.N;
+                            s += pl.N;
+                            active = false;
+                        }
                     }
                 }
-                ++s;
             }
-            if (removed) break;
-            if (!event) t_rem = ftime{0.0f, 0.0f};
+            // this lane's Philox blocks: those of sub-steps [s, s + N)
+            const uint32_t s_end = active ? s + pl.N : 0u;
+            const uint32_t b0 = s >> 1;
+            const uint32_t nblk = active ? ((s_end - 1u) >> 1) - b0 + 1u : 0u;
+            uint32_t incl = nblk;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kAll, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t total = __shfl_sync(kAll, incl, 31);
+            const uint32_t excl = incl - nblk;
+            facc[lane] = kNone;
+            __syncwarp();
+            for (uint32_t fb = 0; fb < total; fb += 32) {
+                const uint32_t f = fb + (uint32_t)lane;
+                // owner: the last lane whose first block index is <= f (it has blocks)
+                int owner = 0;
+#pragma unroll
+                for (int stp = 16; stp > 0; stp >>= 1) {
+                    const uint32_t e = __shfl_sync(kAll, excl, owner + stp);
+                    if (e <= f) owner += stp;
+                }
+                const uint32_t blk = __shfl_sync(kAll, b0, owner) + (f - __shfl_sync(kAll, excl, owner));
+                const uint32_t o_s = __shfl_sync(kAll, s, owner);
+                const uint32_t o_end = __shfl_sync(kAll, s_end, owner);
+                const uint32_t o_T = __shfl_sync(kAll, pl.T, owner);
+                const float o_b = __shfl_sync(kAll, pl.b, owner);
+                const float o_ch = __shfl_sync(kAll, pl.c_h, owner);
+                const uint32_t o_lo = __shfl_sync(kAll, (uint32_t)id, owner);
+                const uint32_t o_hi = __shfl_sync(kAll, (uint32_t)(id >> 32), owner);
+                const bool o_photon = __shfl_sync(kAll, photon ? 1 : 0, owner) != 0;
+                if (f < total) {
+                    const uint4 r = philox4x32_10(make_uint4(o_lo, o_hi, step, blk), k0, k1);
+                    const uint32_t sA = 2u * blk;
+                    const bool cA = sA >= o_s && sA < o_end && (r.y >> 9) < o_T;
+                    const bool cB = sA + 1u >= o_s && sA + 1u < o_end && (r.w >> 9) < o_T;
+                    stats.cand += (unsigned)cA + (unsigned)cB;
+                    bool aA = false, aB = false;
+                    float dtmp;
+                    if (cA || cB) {
+                        const bool first = cA;
+                        const float y = u01(first ? r.y : r.w);
+                        const bool acc = y < acceptance(sm.syn, o_photon, o_b, o_ch,
+                                                        u01(first ? r.x : r.z), &dtmp);
+                        aA = first && acc;
+                        aB = !first && acc;
+                    }
+                    if (cA && cB && !aA)
+                        aB = u01(r.w) < acceptance(sm.syn, o_photon, o_b, o_ch, u01(r.z), &dtmp);
+                    if (aA) atomicMin(&facc[owner], sA);
+                    else if (aB) atomicMin(&facc[owner], sA + 1u);
+                }
+            }
+            __syncwarp();
+            if (active) {
+                const uint32_t s_ev = facc[lane];
+                if (s_ev == kNone) {
+                    stats.substeps += pl.N;
+                    s = s_end;
+                    active = false;   // the plan ran out without an event
+                } else {
+                    const uint32_t k = s_ev - s;
+                    stats.substeps += k + 1u;
+                    const uint4 r = philox4x32_10(
+                        make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, s_ev >> 1), k0, k1);
+                    const float x = u01((s_ev & 1u) ? r.z : r.x);
+                    const ftime t_after = (k + 1u == pl.N) ? ftime{0.0f, 0.0f}
+                                                           : time_sub_mul(t_rem, k + 1u, pl.h);
+                    removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
+                                          t_after, st, stats, true, false,
+                                          Fields{Ex, Ey, Ez, Bx, By, Bz});
+                    changed = true;
+                    s = s_ev + 1u;
+                    t_rem = t_after;
+                    if (removed || !time_positive(t_rem)) active = false;
+                    else need_plan = true;
+                }
+            }
+            __syncwarp();   // facc is reset by the next round
         }
         if (removed) {
             P.type[i] = QED_REMOVED;
@@ -621,6 +676,11 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
             const float thr = use_net ? pl.c_h * sampler_wtot(net, chi) : 0.0f;
             uint32_t kdone = 0;
             bool event = false;
+            if (!use_net && pl.T == 0u) {   // no candidates: count without drawing
+                if (lane == 0) stats.substeps += pl.N;
+                s += pl.N;
+                kdone = pl.N;
+            }
             while (kdone < pl.N) {
                 const uint32_t sb = s;
                 const uint32_t sa = sb & ~1u;
@@ -638,9 +698,19 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
                 } else {
                     c0 = v0 && (r.y >> 9) < pl.T;
                     c1 = v1 && (r.w >> 9) < pl.T;
+                    // one acceptance evaluation per lane: the earlier candidate
+                    // of the pair; the later one only if the earlier is rejected
                     float dtmp;
-                    if (c0) a0 = u01(r.y) < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(r.x), &dtmp);
-                    if (c1) a1 = u01(r.w) < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(r.z), &dtmp);
+                    if (c0 || c1) {
+                        const bool first = c0;
+                        const float y = u01(first ? r.y : r.w);
+                        const bool acc =
+                            y < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(first ? r.x : r.z), &dtmp);
+                        a0 = first && acc;
+                        a1 = !first && acc;
+                    }
+                    if (c0 && c1 && !a0)
+                        a1 = u01(r.w) < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(r.z), &dtmp);
                 }
                 const unsigned int m0 = __ballot_sync(0xffffffffu, a0);
                 const unsigned int m1 = __ballot_sync(0xffffffffu, a1);
@@ -1965,7 +2035,7 @@ qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_inde
     int b_cb = cold_max, b_hb = hot_max;
     st = run(b_hm, b_cb, b_hb, &best);   // warm-up and reference
     if (st == QED_OK) st = run(b_hm, b_cb, b_hb, &best);
-    const uint32_t hms[] = {16, 32, 64, 128};
+    const uint32_t hms[] = {16, 32, 64, 128, 256, 512};
     for (uint32_t hm : hms) {
         if (st != QED_OK) break;
         st = run(hm, b_cb, b_hb, &ms);

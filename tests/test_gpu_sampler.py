@@ -74,8 +74,9 @@ def test_exact_quantile_table_matches_oracle():
 
 @pytest.fixture(scope="module")
 def trained():
-    ctx = qed.Context(seed=11, sampler=True, sampler_max_err=1e-2)
-    loss = ctx.sampler_train(2024, 1 << 25, batch=4096, lr=3e-3)
+    # the benchmark's recipe: 2^26 exact-CDF samples in batches of 2048
+    ctx = qed.Context(seed=11, sampler=True, sampler_max_err=1e-3)
+    loss = ctx.sampler_train(2024, 1 << 26, batch=2048, lr=3e-3)
     err = ctx.sampler_evaluate()
     print("sampler: final loss %.3e, per-bin max CDF error: median %.2e max %.2e"
           % (loss, np.median(err), err.max()))
@@ -84,8 +85,9 @@ def trained():
 
 def test_training_reaches_a_small_cdf_error(trained):
     ctx, err = trained
-    assert np.median(err) < 5e-3
-    assert err.max() < 5e-2
+    # every chi bin within the 1e-3 spectrum (CDF) error, with margin in the bulk
+    assert err.max() <= 1e-3
+    assert np.median(err) < 5e-4
     # save / load round trip keeps the network
     p = ctx.sampler_save()
     ctx.sampler_load(p)
@@ -108,9 +110,9 @@ def test_sampler_events_follow_the_spectrum(trained):
            "type": np.zeros(M, np.uint8)}
     chi, g = O.chi((-pm, 0.0, 0.0), (0.0, float(E0), 0.0), (0.0, 0.0, float(E0)))
     bin_ = int((math.log10(chi) + 2) * 16)
-    assert err[bin_] <= 1e-2
+    assert err[bin_] <= 1e-3
     sctx = qed.Context(seed=77, process_mask=1, cascade=False, recoil=False, sampler=True,
-                       sampler_max_err=1e-2)
+                       sampler_max_err=1e-3)
     sctx.sampler_load(ctx.sampler_save())
     sctx.sampler_evaluate()
     sctx.set_event_log(1 << 16)
@@ -126,3 +128,14 @@ def test_sampler_events_follow_the_spectrum(trained):
     cdf = np.array([_oracle_cdf(b, g_) if g_ > 0 else 0.0 for g_ in grid])
     from scipy import stats
     assert stats.kstest(xs, lambda v: np.interp(v, grid, cdf)).pvalue > 0.01
+    # what the network saves: the plain path evaluates the acceptance function
+    # (F1, F2) at every squeeze candidate, the sampler path at none, for the same
+    # event rate and spectrum
+    pctx = qed.Context(seed=77, process_mask=1, cascade=False, recoil=False)
+    pctx.set_event_log(1 << 16)
+    pst = pctx.event_step(qed.ParticleStore.from_numpy(arr, capacity=M * 20), 3)
+    pev, _ = pctx.read_event_log()
+    assert st["candidates"] == 0 and pst["candidates"] > pst["emissions"]
+    assert abs(st["emissions"] - pst["emissions"]) < 5 * math.sqrt(2 * W_dt * M)
+    px_ = np.cbrt(pev["delta"].astype(np.float64))
+    assert stats.ks_2samp(xs, px_).pvalue > 0.01
