@@ -278,15 +278,19 @@ qed_status qed_sampler_quantile(qed_ctx* ctx, const float* log10chi, const float
 qed_status qed_sampler_load(qed_ctx* ctx, const float* params, int64_t n);
 qed_status qed_sampler_save(qed_ctx* ctx, float* params, int64_t n);
 
-/* Launch settings: the sub-step count from which a particle is stepped by a
- * whole warp (default 64), and the resident blocks per SM of the thread and
- * warp passes (default: the occupancy maximum; larger values are clamped to
- * it).  0 keeps a setting.  Errors: QED_ERR_ARG. */
-qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, int cold_blocks_per_sm,
-                          int hot_blocks_per_sm);
+/* Launch settings.  hot_min: plans of at least this many sub-steps leave the
+ * thread pass for the hot pass (default 32); long_min: hot plans of at least
+ * this many sub-steps are stepped by a whole warp each, the others one lane
+ * each (default 256; the sampler mode steps every hot particle by a warp);
+ * the resident blocks per SM of the thread and hot passes (default: the
+ * occupancy maximum; larger values are clamped to it).  0 keeps a setting.
+ * No setting changes a result.  Errors: QED_ERR_ARG. */
+qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, uint32_t long_min,
+                          int cold_blocks_per_sm, int hot_blocks_per_sm);
 
 /* Time qed_event_step on `p` (step index step_index) for a coordinate search
- * over the launch settings (warp-path threshold 16 ... 512, blocks per SM
+ * over the launch settings (hot_min 16 ... 256, long_min 128 ... 2048 or
+ * never, blocks per SM
  * of each pass), keep the fastest, and restore the store from a snapshot
  * after every trial (the store is unchanged on return).  Writes the chosen
  * settings and all trial timings as JSON to out_json (host file path,

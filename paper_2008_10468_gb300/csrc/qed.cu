@@ -40,7 +40,10 @@ constexpr double kTauC = 1.2880886664441626e-21;    // hbar / (m c^2), s
 constexpr double kCLight = 299792458.0;             // m / s
 constexpr double kPiD = 3.14159265358979323846;
 
-constexpr uint32_t kHotMinDefault = 64;  // plans with N >= hot_min go to the warp path
+// Defaults measured on the 2^24 clumped population (coordinate search over
+// hot_min 32..128 and long_min 128..2048)
+constexpr uint32_t kHotMinDefault = 32;    // plans with N >= hot_min go to the hot pass
+constexpr uint32_t kLongMinDefault = 256;  // ... and with N >= long_min to its warp mode
 
 // Minimum resident blocks per SM requested from the register allocator:
 // 3 x 256 threads hold the thread pass at 80 registers (24 warps per SM);
@@ -49,10 +52,14 @@ constexpr uint32_t kHotMinDefault = 64;  // plans with N >= hot_min go to the wa
 #ifndef QED_COLD_MIN_BLOCKS
 #define QED_COLD_MIN_BLOCKS 3
 #endif
+#ifndef QED_LANES_MIN_BLOCKS
+#define QED_LANES_MIN_BLOCKS 3
+#endif
 #ifndef QED_HOT_MIN_BLOCKS
 #define QED_HOT_MIN_BLOCKS 8
 #endif
 constexpr int kColdThreads = 256;
+constexpr int kLaneThreads = 256;
 constexpr int kHotThreads = 128;
 constexpr int kSweepThreads = 256;
 
@@ -64,7 +71,8 @@ struct DevCtl {
     int status;
     long long required;
     long long pass_begin, pass_end;
-    unsigned int hot_tail, hot_head;
+    unsigned int hot_tail, hot_head;   // long plans: front of the queue array
+    unsigned int med_tail, med_head;   // medium plans: back of the queue array
     int more, passes;
     int first_pass;      // 1 until the first generation of the step is done
     int sticky;          // first error of a multi-step graph run: later steps do nothing
@@ -89,7 +97,10 @@ struct DevParticles {
 
 struct Scratch {
     ftime* t_rem;           // remaining time of appended children (capacity)
-    HotItem* hot;           // queue of warp-path particles (capacity)
+    HotItem* hot;           // queue of hot-pass particles (hot_cap entries), filled
+                            // from both ends: long plans from the front,
+                            // medium plans from the back
+    long long hot_cap;
     qed_event_record* log;  // optional
     long long log_cap;
     long long* log_count;
@@ -419,15 +430,17 @@ __device__ __forceinline__ bool process_enabled(const StepParams& SP, bool photo
 }
 
 __device__ __forceinline__ void push_hot(const Scratch& S, DevCtl* ctl, long long i, uint32_t s,
-                                         ftime t_rem) {
-    const unsigned int k = atomicAdd(&ctl->hot_tail, 1u);
+                                         ftime t_rem, bool long_plan) {
     HotItem it;
     it.idx = (uint32_t)i;
     it.s = s;
     it.t_rem = t_rem;
-    S.hot[k] = it;
+    if (long_plan) {
+        S.hot[atomicAdd(&ctl->hot_tail, 1u)] = it;
+    } else {
+        S.hot[S.hot_cap - 1 - (long long)atomicAdd(&ctl->med_tail, 1u)] = it;
+    }
 }
-
 // With the learned sampler on, e+- whose chi lies in a usable bin of its
 // range are stepped on the warp path, where the network is evaluated.
 __device__ __forceinline__ bool sampler_bin_ok(const StepParams& SP, float chi) {
@@ -442,19 +455,97 @@ __device__ __forceinline__ uint32_t step_index(const StepParams& SP) {
     return SP.step_base ? SP.step + *SP.step_base : SP.step;
 }
 
-// One thread per particle for planning and events, one warp for the draws.
-// First generation of a step: rows [0, pass_end) with the full step; later
-// generations: rows [pass_begin, pass_end) (children) with their stored
-// remaining time.  Each lane plans its row; particles whose plan reaches
-// hot_min sub-steps (or, with the sampler, e+- in a usable chi bin) go to the
-// warp queue.  The Philox blocks of the planned sub-steps of all lanes are
-// then laid end to end and drawn 32 at a time by the whole warp (lane f of a
-// round takes block f of the concatenation), so that a warp whose particles
-// plan 1 to 30 sub-steps keeps its lanes busy.  Each particle takes its
-// earliest accepted sub-step (a shared-memory minimum): the same decision as
-// testing its sub-steps in order and stopping at the first acceptance.  Lanes
-// with an event apply it, re-plan the remaining time and take part in the
-// next round.
+// One round of warp-shared draws.  Every active lane has the sub-steps
+// [s, s_end) of its current plan to test; the Philox blocks of those ranges
+// are laid end to end (prefix sum of the per-lane block counts) and drawn 32
+// at a time, lane f of a round taking block f.  Its owner is the last lane
+// whose first block index is <= f (5-step binary search over the lanes), whose
+// plan parameters come by shuffle.  Accepted sub-steps are reduced per owner
+// with a shared-memory minimum: on return facc[lane] holds the lane's earliest
+// accepted sub-step in its range, or kNoEvent.  Called by all 32 lanes.
+constexpr uint32_t kNoEvent = 0xffffffffu;
+__device__ __forceinline__ void warp_draw_round(const SharedTables& sm, uint32_t* facc,
+                                                bool active, uint32_t s, uint32_t s_end,
+                                                uint32_t T, float b, float c_h, uint64_t id,
+                                                bool photon, uint32_t step, uint32_t k0,
+                                                uint32_t k1, unsigned int& cand) {
+    constexpr unsigned int kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t b0 = s >> 1;
+    const uint32_t nblk = (active && s_end > s) ? ((s_end - 1u) >> 1) - b0 + 1u : 0u;
+    uint32_t incl = nblk;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kAll, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(kAll, incl, 31);
+    const uint32_t excl = incl - nblk;
+    facc[lane] = kNoEvent;
+    __syncwarp();
+    for (uint32_t fb = 0; fb < total; fb += 32) {
+        const uint32_t f = fb + (uint32_t)lane;
+        int owner = 0;
+#pragma unroll
+        for (int stp = 16; stp > 0; stp >>= 1) {
+            const uint32_t e = __shfl_sync(kAll, excl, owner + stp);
+            if (e <= f) owner += stp;
+        }
+        const uint32_t blk = __shfl_sync(kAll, b0, owner) + (f - __shfl_sync(kAll, excl, owner));
+        const uint32_t o_s = __shfl_sync(kAll, s, owner);
+        const uint32_t o_end = __shfl_sync(kAll, s_end, owner);
+        const uint32_t o_T = __shfl_sync(kAll, T, owner);
+        const float o_b = __shfl_sync(kAll, b, owner);
+        const float o_ch = __shfl_sync(kAll, c_h, owner);
+        const uint32_t o_lo = __shfl_sync(kAll, (uint32_t)id, owner);
+        const uint32_t o_hi = __shfl_sync(kAll, (uint32_t)(id >> 32), owner);
+        const bool o_photon = __shfl_sync(kAll, photon ? 1 : 0, owner) != 0;
+        if (f < total) {
+            const uint4 r = philox4x32_10(make_uint4(o_lo, o_hi, step, blk), k0, k1);
+            const uint32_t sA = 2u * blk;
+            const bool cA = sA >= o_s && sA < o_end && (r.y >> 9) < o_T;
+            const bool cB = sA + 1u >= o_s && sA + 1u < o_end && (r.w >> 9) < o_T;
+            cand += (unsigned)cA + (unsigned)cB;
+            bool aA = false, aB = false;
+            float dtmp;
+            if (cA || cB) {
+                // one acceptance evaluation per lane: the earlier candidate of
+                // the pair; the later one only if the earlier is rejected
+                const bool first = cA;
+                const float y = u01(first ? r.y : r.w);
+                const bool acc =
+                    y < acceptance(sm.syn, o_photon, o_b, o_ch, u01(first ? r.x : r.z), &dtmp);
+                aA = first && acc;
+                aB = !first && acc;
+            }
+            if (cA && cB && !aA)
+                aB = u01(r.w) < acceptance(sm.syn, o_photon, o_b, o_ch, u01(r.z), &dtmp);
+            if (aA) atomicMin(&facc[owner], sA);
+            else if (aB) atomicMin(&facc[owner], sA + 1u);
+        }
+    }
+    __syncwarp();
+}
+
+// x of sub-step s (the first word of its draw pair).
+__device__ __forceinline__ float draw_x(uint64_t id, uint32_t step, uint32_t s, uint32_t k0,
+                                        uint32_t k1) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, s >> 1),
+                                  k0, k1);
+    return u01((s & 1u) ? r.z : r.x);
+}
+
+// Thread pass: one lane per row for planning and events, the warp's lanes
+// together for the draws (warp_draw_round).  First generation of a step:
+// rows [0, pass_end) with the full step; later generations: rows
+// [pass_begin, pass_end) (children) with their stored remaining time.  Each
+// lane plans its row; particles whose plan reaches hot_min sub-steps (or,
+// with the sampler, e+- in a usable chi bin) go to the hot queue.  A round
+// draws every remaining planned sub-step of the warp's rows, so that a warp
+// whose particles plan 1 to 30 sub-steps keeps its lanes busy; each particle
+// takes its earliest accepted sub-step, the decision of testing its
+// sub-steps in order and stopping at the first acceptance.  Lanes with an
+// event apply it, re-plan the remaining time and join the next round.
 __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevParticles P, StepParams SP, Scratch S,
                                                        DevCtl* ctl) {
     const uint32_t step = step_index(SP);
@@ -471,7 +562,6 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     uint32_t* facc = first_acc + (threadIdx.x & ~31);
     constexpr unsigned int kAll = 0xffffffffu;
-    constexpr uint32_t kNone = 0xffffffffu;
     Stats stats;
     const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
     for (long long base = begin + warp * 32; base < end; base += nwarps * 32) {
@@ -518,7 +608,9 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                             P.pz[i] = st.pz;
                             changed = false;
                         }
-                        push_hot(S, ctl, i, s, t_rem);   // the warp path plans again
+                        // the hot pass plans again; the sampler mode steps
+                        // every hot particle with a whole warp
+                        push_hot(S, ctl, i, s, t_rem, SP.sampler || pl.N >= SP.long_min);
                         active = false;
                     } else {
                         stats.plans++;
@@ -533,73 +625,19 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                     }
                 }
             }
-            // this lane's Philox blocks: those of sub-steps [s, s + N)
             const uint32_t s_end = active ? s + pl.N : 0u;
-            const uint32_t b0 = s >> 1;
-            const uint32_t nblk = active ? ((s_end - 1u) >> 1) - b0 + 1u : 0u;
-            uint32_t incl = nblk;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kAll, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const uint32_t total = __shfl_sync(kAll, incl, 31);
-            const uint32_t excl = incl - nblk;
-            facc[lane] = kNone;
-            __syncwarp();
-            for (uint32_t fb = 0; fb < total; fb += 32) {
-                const uint32_t f = fb + (uint32_t)lane;
-                // owner: the last lane whose first block index is <= f (it has blocks)
-                int owner = 0;
-#pragma unroll
-                for (int stp = 16; stp > 0; stp >>= 1) {
-                    const uint32_t e = __shfl_sync(kAll, excl, owner + stp);
-                    if (e <= f) owner += stp;
-                }
-                const uint32_t blk = __shfl_sync(kAll, b0, owner) + (f - __shfl_sync(kAll, excl, owner));
-                const uint32_t o_s = __shfl_sync(kAll, s, owner);
-                const uint32_t o_end = __shfl_sync(kAll, s_end, owner);
-                const uint32_t o_T = __shfl_sync(kAll, pl.T, owner);
-                const float o_b = __shfl_sync(kAll, pl.b, owner);
-                const float o_ch = __shfl_sync(kAll, pl.c_h, owner);
-                const uint32_t o_lo = __shfl_sync(kAll, (uint32_t)id, owner);
-                const uint32_t o_hi = __shfl_sync(kAll, (uint32_t)(id >> 32), owner);
-                const bool o_photon = __shfl_sync(kAll, photon ? 1 : 0, owner) != 0;
-                if (f < total) {
-                    const uint4 r = philox4x32_10(make_uint4(o_lo, o_hi, step, blk), k0, k1);
-                    const uint32_t sA = 2u * blk;
-                    const bool cA = sA >= o_s && sA < o_end && (r.y >> 9) < o_T;
-                    const bool cB = sA + 1u >= o_s && sA + 1u < o_end && (r.w >> 9) < o_T;
-                    stats.cand += (unsigned)cA + (unsigned)cB;
-                    bool aA = false, aB = false;
-                    float dtmp;
-                    if (cA || cB) {
-                        const bool first = cA;
-                        const float y = u01(first ? r.y : r.w);
-                        const bool acc = y < acceptance(sm.syn, o_photon, o_b, o_ch,
-                                                        u01(first ? r.x : r.z), &dtmp);
-                        aA = first && acc;
-                        aB = !first && acc;
-                    }
-                    if (cA && cB && !aA)
-                        aB = u01(r.w) < acceptance(sm.syn, o_photon, o_b, o_ch, u01(r.z), &dtmp);
-                    if (aA) atomicMin(&facc[owner], sA);
-                    else if (aB) atomicMin(&facc[owner], sA + 1u);
-                }
-            }
-            __syncwarp();
+            warp_draw_round(sm, facc, active, s, s_end, pl.T, pl.b, pl.c_h, id, photon, step, k0,
+                            k1, stats.cand);
             if (active) {
                 const uint32_t s_ev = facc[lane];
-                if (s_ev == kNone) {
+                if (s_ev == kNoEvent) {
                     stats.substeps += pl.N;
                     s = s_end;
                     active = false;   // the plan ran out without an event
                 } else {
                     const uint32_t k = s_ev - s;
                     stats.substeps += k + 1u;
-                    const uint4 r = philox4x32_10(
-                        make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, s_ev >> 1), k0, k1);
-                    const float x = u01((s_ev & 1u) ? r.z : r.x);
+                    const float x = draw_x(id, step, s_ev, k0, k1);
                     const ftime t_after = (k + 1u == pl.N) ? ftime{0.0f, 0.0f}
                                                            : time_sub_mul(t_rem, k + 1u, pl.h);
                     removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
@@ -625,11 +663,129 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
     flush_stats(stats, ctl);
 }
 
-// One warp per queued particle.
+
+// One queued particle stepped by the whole warp (all 32 lanes, identical
+// arguments): 64 sub-steps per iteration (lane l draws the Philox block of
+// sub-steps 2l and 2l+1), the first accepted sub-step found with two ballots.
+// Statistics are counted on lane 0, candidates per lane.
 // kSampler: e+- in a usable bin of the sampler's chi range decide events from
 // the tabulated total probability c_h W(b) and take the energy fraction from
 // the network (x = delta^{1/3} at the event's uniform); the others use
 // rejection as usual.
+template <bool kSampler>
+__device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& S,
+                                          const StepParams& SP, DevCtl* ctl,
+                                          const SharedTables& sm, SamplerSmem& net,
+                                          const HotItem& it, uint32_t step, uint32_t k0,
+                                          uint32_t k1, Stats& stats, unsigned int& cand) {
+    const int lane = threadIdx.x & 31;
+    const long long i = it.idx;
+    const bool photon = P.type[i] == QED_PHOTON;
+    const uint64_t id = P.id[i];
+    PState st{P.px[i], P.py[i], P.pz[i]};
+    const float Ex = P.Ex[i], Ey = P.Ey[i], Ez = P.Ez[i];
+    const float Bx = P.Bx[i], By = P.By[i], Bz = P.Bz[i];
+    uint32_t s = it.s;
+    ftime t_rem = it.t_rem;
+    bool removed = false, changed = false;
+    while (time_positive(t_rem)) {
+        float eps, chi;
+        const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
+                                      Ey, Ez, Bx, By, Bz, t_rem, &chi, &eps);
+        if (!(eps > 0.0f)) break;
+        if (lane == 0) {
+            stats.plans++;
+            stats.guard += pl.guard ? 1 : 0;
+            stats.max_N = max(stats.max_N, pl.N);
+        }
+        const bool use_net = kSampler && !photon && sampler_bin_ok(SP, chi);
+        const float thr = use_net ? pl.c_h * sampler_wtot(net, chi) : 0.0f;
+        uint32_t kdone = 0;
+        bool event = false;
+        if (!use_net && pl.T == 0u) {   // no candidates: count without drawing
+            if (lane == 0) stats.substeps += pl.N;
+            s += pl.N;
+            kdone = pl.N;
+        }
+        while (kdone < pl.N) {
+            const uint32_t sb = s;
+            const uint32_t sa = sb & ~1u;
+            const uint32_t lim = sb + (pl.N - kdone);
+            const uint32_t s0 = sa + 2u * (uint32_t)lane;
+            const uint4 r = philox4x32_10(
+                make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, (sa >> 1) + lane), k0, k1);
+            const bool v0 = s0 >= sb && s0 < lim;
+            const bool v1 = s0 + 1 >= sb && s0 + 1 < lim;
+            bool c0, c1, a0 = false, a1 = false;
+            if (use_net) {
+                c0 = c1 = false;
+                a0 = v0 && u01(r.y) < thr;
+                a1 = v1 && u01(r.w) < thr;
+            } else {
+                c0 = v0 && (r.y >> 9) < pl.T;
+                c1 = v1 && (r.w >> 9) < pl.T;
+                // one acceptance evaluation per lane: the earlier candidate
+                // of the pair; the later one only if the earlier is rejected
+                float dtmp;
+                if (c0 || c1) {
+                    const bool first = c0;
+                    const float y = u01(first ? r.y : r.w);
+                    const bool acc =
+                        y < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(first ? r.x : r.z), &dtmp);
+                    a0 = first && acc;
+                    a1 = !first && acc;
+                }
+                if (c0 && c1 && !a0)
+                    a1 = u01(r.w) < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(r.z), &dtmp);
+            }
+            const unsigned int m0 = __ballot_sync(0xffffffffu, a0);
+            const unsigned int m1 = __ballot_sync(0xffffffffu, a1);
+            cand += (unsigned)c0 + (unsigned)c1;
+            if ((m0 | m1) == 0u) {
+                const uint32_t chunk_end = min(sa + 64u, lim);
+                if (lane == 0) stats.substeps += chunk_end - sb;
+                kdone += chunk_end - sb;
+                s = chunk_end;
+                continue;
+            }
+            const int p0 = m0 ? 2 * (__ffs(m0) - 1) : 1 << 30;
+            const int p1 = m1 ? 2 * (__ffs(m1) - 1) + 1 : 1 << 30;
+            const int pos = min(p0, p1);
+            const uint32_t s_ev = sa + (uint32_t)pos;
+            const float xo = (pos & 1) ? u01(r.z) : u01(r.x);
+            float x = __shfl_sync(0xffffffffu, xo, pos >> 1);
+            if (use_net) {
+                // inverse sampling: the event's uniform goes through the network
+                x = mlp_infer_warp(net, log10f(chi) * 0.5f, mlp_input_u(x));
+                if (lane == 0) stats.sampled++;
+            }
+            const uint32_t k_ev = kdone + (s_ev - sb);
+            if (lane == 0) stats.substeps += s_ev - sb + 1;
+            const ftime t_after = (k_ev + 1 == pl.N) ? ftime{0.0f, 0.0f}
+                                                     : time_sub_mul(t_rem, k_ev + 1, pl.h);
+            removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev, t_after,
+                                  st, stats, lane == 0, true, Fields{Ex, Ey, Ez, Bx, By, Bz});
+            changed = true;
+            s = s_ev + 1;
+            t_rem = t_after;
+            event = true;
+            break;
+        }
+        if (removed) break;
+        if (!event) t_rem = ftime{0.0f, 0.0f};
+    }
+    if (lane == 0) {
+        if (removed) P.type[i] = QED_REMOVED;
+        else if (changed) {
+            P.px[i] = st.px;
+            P.py[i] = st.py;
+            P.pz[i] = st.pz;
+        }
+    }
+}
+
+// Hot pass of the sampler mode: every queued particle stepped by a whole warp
+// (warp_item), so that the network can be evaluated by the warp.
 template <bool kSampler>
 __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevParticles P, StepParams SP, Scratch S,
                                                      DevCtl* ctl) {
@@ -652,114 +808,174 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
         if (lane == 0) q = atomicAdd(&ctl->hot_head, 1u);
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= tail) break;
-        const HotItem it = S.hot[q];
-        const long long i = it.idx;
-        const bool photon = P.type[i] == QED_PHOTON;
-        const uint64_t id = P.id[i];
-        PState st{P.px[i], P.py[i], P.pz[i]};
-        const float Ex = P.Ex[i], Ey = P.Ey[i], Ez = P.Ez[i];
-        const float Bx = P.Bx[i], By = P.By[i], Bz = P.Bz[i];
-        uint32_t s = it.s;
-        ftime t_rem = it.t_rem;
-        bool removed = false, changed = false;
-        while (time_positive(t_rem)) {
-            float eps, chi;
-            const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
-                                          Ey, Ez, Bx, By, Bz, t_rem, &chi, &eps);
-            if (!(eps > 0.0f)) break;
-            if (lane == 0) {
-                stats.plans++;
-                stats.guard += pl.guard ? 1 : 0;
-                stats.max_N = max(stats.max_N, pl.N);
-            }
-            const bool use_net = kSampler && !photon && sampler_bin_ok(SP, chi);
-            const float thr = use_net ? pl.c_h * sampler_wtot(net, chi) : 0.0f;
-            uint32_t kdone = 0;
-            bool event = false;
-            if (!use_net && pl.T == 0u) {   // no candidates: count without drawing
-                if (lane == 0) stats.substeps += pl.N;
-                s += pl.N;
-                kdone = pl.N;
-            }
-            while (kdone < pl.N) {
-                const uint32_t sb = s;
-                const uint32_t sa = sb & ~1u;
-                const uint32_t lim = sb + (pl.N - kdone);
-                const uint32_t s0 = sa + 2u * (uint32_t)lane;
-                const uint4 r = philox4x32_10(
-                    make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, (sa >> 1) + lane), k0, k1);
-                const bool v0 = s0 >= sb && s0 < lim;
-                const bool v1 = s0 + 1 >= sb && s0 + 1 < lim;
-                bool c0, c1, a0 = false, a1 = false;
-                if (use_net) {
-                    c0 = c1 = false;
-                    a0 = v0 && u01(r.y) < thr;
-                    a1 = v1 && u01(r.w) < thr;
-                } else {
-                    c0 = v0 && (r.y >> 9) < pl.T;
-                    c1 = v1 && (r.w >> 9) < pl.T;
-                    // one acceptance evaluation per lane: the earlier candidate
-                    // of the pair; the later one only if the earlier is rejected
-                    float dtmp;
-                    if (c0 || c1) {
-                        const bool first = c0;
-                        const float y = u01(first ? r.y : r.w);
-                        const bool acc =
-                            y < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(first ? r.x : r.z), &dtmp);
-                        a0 = first && acc;
-                        a1 = !first && acc;
-                    }
-                    if (c0 && c1 && !a0)
-                        a1 = u01(r.w) < acceptance(sm.syn, photon, pl.b, pl.c_h, u01(r.z), &dtmp);
-                }
-                const unsigned int m0 = __ballot_sync(0xffffffffu, a0);
-                const unsigned int m1 = __ballot_sync(0xffffffffu, a1);
-                cand += (unsigned)c0 + (unsigned)c1;
-                if ((m0 | m1) == 0u) {
-                    const uint32_t chunk_end = min(sa + 64u, lim);
-                    if (lane == 0) stats.substeps += chunk_end - sb;
-                    kdone += chunk_end - sb;
-                    s = chunk_end;
-                    continue;
-                }
-                const int p0 = m0 ? 2 * (__ffs(m0) - 1) : 1 << 30;
-                const int p1 = m1 ? 2 * (__ffs(m1) - 1) + 1 : 1 << 30;
-                const int pos = min(p0, p1);
-                const uint32_t s_ev = sa + (uint32_t)pos;
-                const float xo = (pos & 1) ? u01(r.z) : u01(r.x);
-                float x = __shfl_sync(0xffffffffu, xo, pos >> 1);
-                if (use_net) {
-                    // inverse sampling: the event's uniform goes through the network
-                    x = mlp_infer_warp(net, log10f(chi) * 0.5f, mlp_input_u(x));
-                    if (lane == 0) stats.sampled++;
-                }
-                const uint32_t k_ev = kdone + (s_ev - sb);
-                if (lane == 0) stats.substeps += s_ev - sb + 1;
-                const ftime t_after = (k_ev + 1 == pl.N) ? ftime{0.0f, 0.0f}
-                                                         : time_sub_mul(t_rem, k_ev + 1, pl.h);
-                removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev, t_after,
-                                      st, stats, lane == 0, true, Fields{Ex, Ey, Ez, Bx, By, Bz});
-                changed = true;
-                s = s_ev + 1;
-                t_rem = t_after;
-                event = true;
-                break;
-            }
-            if (removed) break;
-            if (!event) t_rem = ftime{0.0f, 0.0f};
-        }
-        if (lane == 0) {
-            if (removed) P.type[i] = QED_REMOVED;
-            else if (changed) {
-                P.px[i] = st.px;
-                P.py[i] = st.py;
-                P.pz[i] = st.pz;
-            }
-        }
+        warp_item<kSampler>(P, S, SP, ctl, sm, net, S.hot[q], step, k0, k1, stats, cand);
     }
     if (lane != 0) stats = Stats();
     stats.cand = cand;
     stats.warp_substeps = stats.substeps;
+    flush_stats(stats, ctl);
+}
+
+// Hot pass (rejection).  Long plans (N >= long_min, front of the queue) first,
+// one warp each (warp_item), so that their long chains start early; then the
+// medium plans (back of the queue), one lane each, with the same warp-shared
+// draws as the thread pass but at most kWindow sub-steps per lane and round,
+// so that the draws wasted after an event stay short.  Lanes with an event in
+// the round apply it and re-plan together, so that the event path is paid
+// once per round rather than once per event; lanes whose particle is done
+// take the next queue entries (one atomic per warp).  Persistent: the grid is
+// the resident block count, and a warp leaves when the queue is empty and its
+// lanes are idle.
+constexpr uint32_t kWindow = 64;
+__global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lanes(DevParticles P, StepParams SP,
+                                                                 Scratch S, DevCtl* ctl) {
+    const uint32_t step = step_index(SP);
+    __shared__ SharedTables sm;
+    __shared__ uint32_t first_acc[kLaneThreads];
+    stage_tables(sm);
+    __syncthreads();
+    if (ctl->status == (int)QED_ERR_TIMEOUT) return;
+    constexpr unsigned int kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    uint32_t* facc = first_acc + (threadIdx.x & ~31);
+    const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
+    Stats stats;
+    {
+        // long plans first, one warp each, so that their long chains start early
+        const unsigned int long_tail = ctl->hot_tail;
+        Stats wstats;                 // counted on lane 0
+        unsigned int wcand = 0;
+        extern __shared__ __align__(16) unsigned char dyn_smem[];
+        SamplerSmem& none = *reinterpret_cast<SamplerSmem*>(dyn_smem);   // unused
+        while (true) {
+            unsigned int q = 0;
+            if (lane == 0) q = atomicAdd(&ctl->hot_head, 1u);
+            q = __shfl_sync(kAll, q, 0);
+            if (q >= long_tail) break;
+            warp_item<false>(P, S, SP, ctl, sm, none, S.hot[q], step, k0, k1, wstats, wcand);
+        }
+        if (lane == 0) stats = wstats;
+        stats.cand = wcand;
+    }
+    // medium plans, one lane each, from the back of the queue array
+    const unsigned int tail = ctl->med_tail;
+    bool active = false, photon = false, changed = false, removed = false;
+    long long i = 0;
+    uint64_t id = 0;
+    PState st{0.0f, 0.0f, 0.0f};
+    float Ex = 0.0f, Ey = 0.0f, Ez = 0.0f, Bx = 0.0f, By = 0.0f, Bz = 0.0f;
+    ftime t_rem{0.0f, 0.0f};
+    uint32_t s = 0, k_done = 0;
+    Plan pl;
+    pl.N = 0;
+    pl.T = 0;
+    pl.b = pl.c_h = 0.0f;
+    float chi = 0.0f, eps = 0.0f;
+    bool more = true;   // the queue may hold entries (warp-uniform)
+    while (true) {
+        bool planned = false;
+        if (more) {
+            const unsigned int idle = __ballot_sync(kAll, !active);
+            if (idle) {
+                unsigned int base = 0;
+                if (lane == 0) base = atomicAdd(&ctl->med_head, (unsigned int)__popc(idle));
+                base = __shfl_sync(kAll, base, 0);
+                if (base + (unsigned int)__popc(idle) >= tail) more = false;
+                if (!active) {
+                    const unsigned int q = base + (unsigned int)__popc(idle & ((1u << lane) - 1u));
+                    if (q < tail) {
+                        const HotItem it = S.hot[S.hot_cap - 1 - (long long)q];
+                        i = it.idx;
+                        s = it.s;
+                        t_rem = it.t_rem;
+                        photon = P.type[i] == QED_PHOTON;
+                        id = P.id[i];
+                        st = PState{P.px[i], P.py[i], P.pz[i]};
+                        Ex = P.Ex[i]; Ey = P.Ey[i]; Ez = P.Ez[i];
+                        Bx = P.Bx[i]; By = P.By[i]; Bz = P.Bz[i];
+                        changed = removed = false;
+                        planned = true;
+                    }
+                }
+            }
+        }
+        if (planned) {
+            pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex, Ey, Ez,
+                               Bx, By, Bz, t_rem, &chi, &eps);
+            if (eps > 0.0f) {
+                active = true;
+                k_done = 0;
+                stats.plans++;
+                stats.guard += pl.guard ? 1 : 0;
+                stats.max_N = max(stats.max_N, pl.N);
+                if (pl.T == 0u) {   // no candidates: the plan passes without an event
+                    stats.substeps += pl.N;
+                    s += pl.N;
+                    active = false;
+                }
+            }
+        }
+        if (!__any_sync(kAll, active)) {
+            if (!more) break;
+            continue;
+        }
+        const uint32_t n_win = active ? min(kWindow, pl.N - k_done) : 0u;
+        const uint32_t s_end = s + n_win;
+        warp_draw_round(sm, facc, active, s, s_end, pl.T, pl.b, pl.c_h, id, photon, step, k0, k1,
+                        stats.cand);
+        if (active) {
+            const uint32_t s_ev = facc[lane];
+            bool done = false;
+            if (s_ev == kNoEvent) {
+                stats.substeps += n_win;
+                s = s_end;
+                k_done += n_win;
+                done = k_done == pl.N;   // the plan ran out without an event
+            } else {
+                const uint32_t k = k_done + (s_ev - s);
+                stats.substeps += s_ev - s + 1u;
+                const float x = draw_x(id, step, s_ev, k0, k1);
+                const ftime t_after = (k + 1u == pl.N) ? ftime{0.0f, 0.0f}
+                                                       : time_sub_mul(t_rem, k + 1u, pl.h);
+                removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
+                                      t_after, st, stats, true, false,
+                                      Fields{Ex, Ey, Ez, Bx, By, Bz});
+                changed = true;
+                s = s_ev + 1u;
+                t_rem = t_after;
+                done = removed || !time_positive(t_rem);
+                if (!done) {
+                    pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
+                                       Ey, Ez, Bx, By, Bz, t_rem, &chi, &eps);
+                    k_done = 0;
+                    if (!(eps > 0.0f)) {
+                        done = true;
+                    } else {
+                        stats.plans++;
+                        stats.guard += pl.guard ? 1 : 0;
+                        stats.max_N = max(stats.max_N, pl.N);
+                        if (pl.T == 0u) {
+                            stats.substeps += pl.N;
+                            s += pl.N;
+                            done = true;
+                        }
+                    }
+                }
+            }
+            if (done) {
+                if (removed) {
+                    P.type[i] = QED_REMOVED;
+                } else if (changed) {
+                    P.px[i] = st.px;
+                    P.py[i] = st.py;
+                    P.pz[i] = st.pz;
+                }
+                active = false;
+            }
+        }
+        __syncwarp();   // facc is reset by the next round
+    }
+    stats.warp_substeps = stats.substeps;   // every sub-step of this kernel is a hot-pass one
     flush_stats(stats, ctl);
 }
 
@@ -794,6 +1010,8 @@ __global__ void k_advance(DevCtl* ctl, long long* count, long long capacity, int
     ctl->pass_end = ctl->sticky ? 0 : n;
     ctl->hot_head = 0;
     ctl->hot_tail = 0;
+    ctl->med_head = 0;
+    ctl->med_tail = 0;
     ctl->passes += 1;
     ctl->first_pass = 0;
     int more = (more_allowed && ctl->pass_end > ctl->pass_begin && ctl->status == 0) ? 1 : 0;
@@ -1016,7 +1234,8 @@ struct qed_ctx {
     long long* log_count;
     int cold_blocks, hot_blocks;
     int cold_blocks_max, hot_blocks_max;
-    uint32_t hot_min;
+    int net_blocks;           // grid of the sampler's warp-per-particle pass
+    uint32_t hot_min, long_min;
     // compaction
     Mirror mirror;
     long long mirror_cap;
@@ -1090,6 +1309,7 @@ StepParams make_params(const qed_config& c, uint64_t step) {
     P.pair_coeff = c.pair_bound_coeff;
     P.step_base = nullptr;
     P.hot_min = kHotMinDefault;
+    P.long_min = kLongMinDefault;
     P.sampler = 0;
     P.net_rows = 0;
     P.net_bins = 0;
@@ -1209,6 +1429,7 @@ Scratch make_scratch(const qed_ctx* ctx) {
     Scratch S;
     S.t_rem = ctx->d_trem;
     S.hot = ctx->d_hot;
+    S.hot_cap = ctx->scratch_cap;
     S.log = ctx->log;
     S.log_cap = ctx->log_cap;
     S.log_count = ctx->log_count;
@@ -1278,9 +1499,14 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cold, kColdThreads, 0);
         ctx->cold_blocks = ctx->cold_blocks_max = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot<false>, kHotThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes, kLaneThreads, 0);
         ctx->hot_blocks = ctx->hot_blocks_max = ctx->sms * (per_sm > 0 ? per_sm : 1);
+        per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot<true>, kHotThreads,
+                                                      sizeof(SamplerSmem));
+        ctx->net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         ctx->hot_min = kHotMinDefault;
+        ctx->long_min = kLongMinDefault;
         st = cuda_check(ctx, cudaGetLastError(), "occupancy");
     }
     if (st != QED_OK) {
@@ -1387,6 +1613,7 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
     if (st != QED_OK) return st;
     StepParams SP = make_params(ctx->cfg, step_index);
     SP.hot_min = ctx->hot_min;
+    SP.long_min = ctx->long_min;
     st = sampler_params(ctx, &SP);
     if (st != QED_OK) return st;
     const DevParticles D = to_dev(p);
@@ -1404,10 +1631,10 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
         {
             LaunchScope ls(ctx, QED_KERNEL_HOT);
             if (SP.sampler)
-                k_hot<true><<<ctx->hot_blocks, kHotThreads, sizeof(SamplerSmem), ctx->stream>>>(
+                k_hot<true><<<ctx->net_blocks, kHotThreads, sizeof(SamplerSmem), ctx->stream>>>(
                     D, SP, S, ctx->d_ctl);
             else
-                k_hot<false><<<ctx->hot_blocks, kHotThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+                k_hot_lanes<<<ctx->hot_blocks, kLaneThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
         }
         {
             LaunchScope ls(ctx, QED_KERNEL_CONTROL);
@@ -1556,6 +1783,8 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         StepParams SP = make_params(ctx->cfg, (uint64_t)k);   // offset from the device base
         SP.step_base = step_base;
         SP.hot_min = ctx->hot_min;
+        SP.long_min = ctx->long_min;
+    SP.long_min = ctx->long_min;
         st = sampler_params(ctx, &SP);
         if (st != QED_OK) break;
         qed_step_stats* rec = ctx->d_records + k;
@@ -1588,8 +1817,9 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         if (st == QED_OK) {
             void* a[] = {&D, &SP, &S, &ctl};
             st = add_kernel(ctx, body, &bh,
-                            SP.sampler ? (const void*)k_hot<true> : (const void*)k_hot<false>,
-                            dim3(ctx->hot_blocks), dim3(kHotThreads), a, &bc, 1,
+                            SP.sampler ? (const void*)k_hot<true> : (const void*)k_hot_lanes,
+                            dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks),
+                            dim3(SP.sampler ? kHotThreads : kLaneThreads), a, &bc, 1,
                             SP.sampler ? sizeof(SamplerSmem) : 0);
         }
         if (st == QED_OK) {
@@ -1987,10 +2217,11 @@ qed_status copy_store(qed_ctx* ctx, const qed_particles* p, long long n, bool to
 
 }  // namespace
 
-qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, int cold_blocks_per_sm,
-                          int hot_blocks_per_sm) {
+qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, uint32_t long_min,
+                          int cold_blocks_per_sm, int hot_blocks_per_sm) {
     if (!ctx || cold_blocks_per_sm < 0 || hot_blocks_per_sm < 0) return QED_ERR_ARG;
     if (hot_min) ctx->hot_min = hot_min;
+    if (long_min) ctx->long_min = long_min;
     if (cold_blocks_per_sm)
         ctx->cold_blocks = std::min(ctx->sms * cold_blocks_per_sm, ctx->cold_blocks_max);
     if (hot_blocks_per_sm)
@@ -2014,10 +2245,11 @@ qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_inde
     QED_CUDA(ctx, cudaEventCreate(&e0));
     QED_CUDA(ctx, cudaEventCreate(&e1));
     const int cold_max = ctx->cold_blocks_max / ctx->sms, hot_max = ctx->hot_blocks_max / ctx->sms;
-    struct Trial { uint32_t hot_min; int cold, hot; float ms; };
+    struct Setting { uint32_t hot_min, long_min; int cold, hot; };
+    struct Trial { Setting c; float ms; };
     std::vector<Trial> trials;
-    auto run = [&](uint32_t hm, int cb, int hb, float* ms) -> qed_status {
-        qed_set_launch(ctx, hm, cb, hb);
+    auto run = [&](const Setting& c, float* ms) -> qed_status {
+        qed_set_launch(ctx, c.hot_min, c.long_min, c.cold, c.hot);
         qed_status s2 = copy_store(ctx, p, n, false);
         if (s2 != QED_OK) return s2;
         cudaEventRecord(e0, ctx->stream);
@@ -2027,29 +2259,33 @@ qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_inde
         cudaEventSynchronize(e1);
         if (s2 != QED_OK) return s2;
         cudaEventElapsedTime(ms, e0, e1);
-        trials.push_back({hm, cb, hb, *ms});
+        trials.push_back({c, *ms});
         return QED_OK;
     };
     float ms = 0.0f, best = 0.0f;
-    uint32_t b_hm = ctx->hot_min;
-    int b_cb = cold_max, b_hb = hot_max;
-    st = run(b_hm, b_cb, b_hb, &best);   // warm-up and reference
-    if (st == QED_OK) st = run(b_hm, b_cb, b_hb, &best);
-    const uint32_t hms[] = {16, 32, 64, 128, 256, 512};
-    for (uint32_t hm : hms) {
-        if (st != QED_OK) break;
-        st = run(hm, b_cb, b_hb, &ms);
-        if (st == QED_OK && ms < best) { best = ms; b_hm = hm; }
-    }
-    for (int cb = 1; cb <= cold_max && st == QED_OK; ++cb) {
-        st = run(b_hm, cb, b_hb, &ms);
-        if (st == QED_OK && ms < best) { best = ms; b_cb = cb; }
-    }
-    for (int hb = 2; hb <= hot_max && st == QED_OK; hb += 2) {
-        st = run(b_hm, b_cb, hb, &ms);
-        if (st == QED_OK && ms < best) { best = ms; b_hb = hb; }
-    }
-    qed_set_launch(ctx, b_hm, b_cb, b_hb);
+    Setting b{ctx->hot_min, ctx->long_min, cold_max, hot_max};
+    st = run(b, &best);   // warm-up and reference
+    if (st == QED_OK) st = run(b, &best);
+    // coordinate search: one setting at a time, keeping the best so far
+    auto sweep = [&](auto assign, const auto& values) {
+        for (const auto v : values) {
+            if (st != QED_OK) return;
+            Setting c = b;
+            assign(c, v);
+            st = run(c, &ms);
+            if (st == QED_OK && ms < best) { best = ms; b = c; }
+        }
+    };
+    const uint32_t hot_mins[] = {16, 32, 64, 128, 256};
+    const uint32_t long_mins[] = {128, 256, 512, 1024, 2048, 1u << 30};
+    std::vector<int> colds, hots;
+    for (int v = 1; v <= cold_max; ++v) colds.push_back(v);
+    for (int v = 1; v <= hot_max; ++v) hots.push_back(v);
+    sweep([](Setting& c, uint32_t v) { c.hot_min = v; }, hot_mins);
+    sweep([](Setting& c, uint32_t v) { c.long_min = v; }, long_mins);
+    sweep([](Setting& c, int v) { c.cold = v; }, colds);
+    sweep([](Setting& c, int v) { c.hot = v; }, hots);
+    qed_set_launch(ctx, b.hot_min, b.long_min, b.cold, b.hot);
     const qed_status st_restore = copy_store(ctx, p, n, false);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2058,11 +2294,14 @@ qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_inde
     if (out_json) {
         FILE* f = fopen(out_json, "w");
         if (!f) return set_err(ctx, QED_ERR_ARG, "qed_autotune: cannot write the JSON file");
-        fprintf(f, "{\"hot_min\": %u, \"cold_blocks_per_sm\": %d, \"hot_blocks_per_sm\": %d, "
-                   "\"ms\": %.4f, \"trials\": [", b_hm, b_cb, b_hb, best);
+        fprintf(f, "{\"hot_min\": %u, \"long_min\": %u, \"cold_blocks_per_sm\": %d, "
+                   "\"hot_blocks_per_sm\": %d, \"ms\": %.4f, \"trials\": [",
+                b.hot_min, b.long_min, b.cold, b.hot, best);
         for (size_t k = 0; k < trials.size(); ++k)
-            fprintf(f, "%s{\"hot_min\": %u, \"cold\": %d, \"hot\": %d, \"ms\": %.4f}",
-                    k ? ", " : "", trials[k].hot_min, trials[k].cold, trials[k].hot, trials[k].ms);
+            fprintf(f, "%s{\"hot_min\": %u, \"long_min\": %u, \"cold\": %d, \"hot\": %d, "
+                       "\"ms\": %.4f}",
+                    k ? ", " : "", trials[k].c.hot_min, trials[k].c.long_min, trials[k].c.cold,
+                    trials[k].c.hot, trials[k].ms);
         fprintf(f, "]}\n");
         fclose(f);
     }
@@ -2128,6 +2367,7 @@ constexpr size_t kNoAllocHotOffset =
 constexpr size_t kNoAllocBytes = kNoAllocHotOffset + sizeof(HotItem) * (size_t)QED_NOALLOC_MAX_ROWS;
 static_assert(sizeof(DevCtl) <= kNoAllocCtlBytes, "control block does not fit");
 static_assert(kNoAllocHotOffset % 16 == 0, "queue alignment");
+static_assert(sizeof(DevCtl) <= kNoAllocCtlBytes, "control block fits its slot");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -2152,7 +2392,7 @@ qed_status noalloc_setup(int dev, NoAllocDevice* out) {
             return QED_ERR_CUDA;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_cold, k_cold, kColdThreads, 0) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot<false>, kHotThreads, 0) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot_lanes, kLaneThreads, 0) !=
                 cudaSuccess)
             return QED_ERR_CUDA;
         d.base = static_cast<unsigned char*>(ptr);
@@ -2188,6 +2428,7 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     Scratch S;
     S.t_rem = reinterpret_cast<ftime*>(nd.base + kNoAllocTremOffset);
     S.hot = reinterpret_cast<HotItem*>(nd.base + kNoAllocHotOffset);
+    S.hot_cap = QED_NOALLOC_MAX_ROWS;
     S.log = nullptr;
     S.log_cap = 0;
     S.log_count = nullptr;
@@ -2198,7 +2439,7 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     DevCtl h;
     for (int pass = 0; pass < max_passes; ++pass) {
         k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
-        k_hot<false><<<nd.hot_blocks, kHotThreads, 0, s>>>(D, SP, S, ctl);
+        k_hot_lanes<<<nd.hot_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
         k_advance<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, cascade ? 1 : 0, max_passes, 0ull, 0);
         if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
         if (!cascade) break;

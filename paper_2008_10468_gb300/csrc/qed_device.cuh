@@ -285,7 +285,8 @@ struct StepParams {
     float pair_coeff;
     ftime t_step;        // dt as float-float
     const uint32_t* step_base;  // graph runs: device step base added to `step`
-    uint32_t hot_min;           // plans with at least this many sub-steps use the warp path
+    uint32_t hot_min;           // plans with at least this many sub-steps go to the hot pass
+    uint32_t long_min;          // ... and with at least this many to its warp mode
     int sampler;                // learned sampler on (e+- in usable bins)
     int net_rows;               // rows of the total-probability table
     unsigned long long net_bins;  // usable bins (64, uniform in log10 chi over [-2, 2))

@@ -440,7 +440,7 @@ struct SamplerSmem {
     float wtot[1024];                 // total probability per c along log10 chi
     unsigned long long bin_ok;        // bit k: chi bin k within the error limit
     int nrows;
-    float h[8][kMlpW];                // per-warp activation buffer (up to 8 warps)
+    __align__(16) float h[8][kMlpW];  // per-warp activation buffer (up to 8 warps)
 };
 
 __device__ __forceinline__ void stage_sampler(SamplerSmem& S, const __nv_bfloat16* __restrict__ w,
@@ -473,36 +473,51 @@ __device__ __forceinline__ float neuron_dot(const __nv_bfloat16* __restrict__ ro
     return acc;
 }
 
+// Two neurons of one lane, sharing the activation loads: weights read as
+// BF16 pairs, products accumulated in FP32 in the order j = 0..63 (the order
+// of neuron_dot, so both forms give identical results).
+__device__ __forceinline__ void neuron_dot2(const __nv_bfloat16* __restrict__ row0,
+                                            const __nv_bfloat16* __restrict__ row1,
+                                            const float* __restrict__ h, float& acc0,
+                                            float& acc1) {
+#pragma unroll 8
+    for (int j = 0; j < kMlpW; j += 2) {
+        const float2 hv = *reinterpret_cast<const float2*>(h + j);
+        const __nv_bfloat162 w0 = *reinterpret_cast<const __nv_bfloat162*>(row0 + j);
+        const __nv_bfloat162 w1 = *reinterpret_cast<const __nv_bfloat162*>(row1 + j);
+        acc0 = fmaf(__low2float(w0), hv.x, acc0);
+        acc0 = fmaf(__high2float(w0), hv.y, acc0);
+        acc1 = fmaf(__low2float(w1), hv.x, acc1);
+        acc1 = fmaf(__high2float(w1), hv.y, acc1);
+    }
+}
+
 // All 32 lanes of a warp evaluate x(v0, v1) together; every lane gets x.
+// Lane l owns neurons l and l + 32 of each hidden layer.
 __device__ __forceinline__ float mlp_infer_warp(SamplerSmem& S, float v0, float v1) {
     const int lane = threadIdx.x & 31;
     float* h = S.h[(threadIdx.x >> 5) & 7];
-    float a[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int n = lane + 32 * q;
-        a[q] = siluf_(fmaf(S.W1[2 * n], v0, fmaf(S.W1[2 * n + 1], v1, S.b1[n])));
-    }
+    float a0 = siluf_(fmaf(S.W1[2 * lane], v0, fmaf(S.W1[2 * lane + 1], v1, S.b1[lane])));
+    float a1 = siluf_(fmaf(S.W1[2 * (lane + 32)], v0,
+                           fmaf(S.W1[2 * (lane + 32) + 1], v1, S.b1[lane + 32])));
     __syncwarp();
-    h[lane] = a[0];
-    h[lane + 32] = a[1];
+    h[lane] = a0;
+    h[lane + 32] = a1;
     __syncwarp();
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int n = lane + 32 * q;
-        a[q] = siluf_(neuron_dot(S.W2 + n * kBfPad, h, S.b2[n]));
-    }
+    a0 = S.b2[lane];
+    a1 = S.b2[lane + 32];
+    neuron_dot2(S.W2 + lane * kBfPad, S.W2 + (lane + 32) * kBfPad, h, a0, a1);
+    a0 = siluf_(a0);
+    a1 = siluf_(a1);
     __syncwarp();
-    h[lane] = a[0];
-    h[lane + 32] = a[1];
+    h[lane] = a0;
+    h[lane + 32] = a1;
     __syncwarp();
-    float o = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int n = lane + 32 * q;
-        const float z = siluf_(neuron_dot(S.W3 + n * kBfPad, h, S.b3[n]));
-        o = fmaf(S.w4[n], z, o);
-    }
+    a0 = S.b3[lane];
+    a1 = S.b3[lane + 32];
+    neuron_dot2(S.W3 + lane * kBfPad, S.W3 + (lane + 32) * kBfPad, h, a0, a1);
+    float o = fmaf(S.w4[lane], siluf_(a0), 0.0f);
+    o = fmaf(S.w4[lane + 32], siluf_(a1), o);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) o += __shfl_xor_sync(0xffffffffu, o, off);
     __syncwarp();

@@ -39,18 +39,20 @@ def test_autotune_restores_store_and_writes_record(tmp_path):
     for k in arr:
         np.testing.assert_array_equal(after[k], arr[k])
     rec = json.loads(out.read_text())
-    assert rec["hot_min"] in (16, 32, 64, 128, 256, 512)
+    assert rec["hot_min"] in (16, 32, 64, 128, 256)
+    assert rec["long_min"] in (128, 256, 512, 1024, 2048, 1 << 30)
     assert rec["cold_blocks_per_sm"] >= 1 and rec["hot_blocks_per_sm"] >= 1
     assert len(rec["trials"]) >= 6 and all(t["ms"] > 0 for t in rec["trials"])
 
 
-@pytest.mark.parametrize("hot_min,cold,hot", [(16, 1, 2), (128, 2, 4), (1 << 20, 0, 0)])
-def test_launch_settings_change_no_result(hot_min, cold, hot):
+@pytest.mark.parametrize("hot_min,long_min,cold,hot", [(16, 128, 1, 2), (128, 1 << 30, 2, 1),
+                                                       (1 << 20, 0, 0, 0), (32, 32, 0, 1)])
+def test_launch_settings_change_no_result(hot_min, long_min, cold, hot):
     arr = I.clumped_mixed(20000, 78, hot_fraction=0.03)
     cap = 400000
     ref_st, ref = _step(qed.Context(seed=8), arr, cap, 11)
     ctx = qed.Context(seed=8)
-    ctx.set_launch(hot_min, cold, hot)
+    ctx.set_launch(hot_min, long_min, cold, hot)
     st, got = _step(ctx, arr, cap, 11)
     for k in ("substeps", "emissions", "pairs", "children", "max_N", "status"):
         assert st[k] == ref_st[k], k
