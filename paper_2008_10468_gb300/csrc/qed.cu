@@ -4,13 +4,15 @@
 //   k_sweep / k_generate   synchrotron functions over an array or over
 //                          in-kernel arguments (Sec. 3.2.1)
 //   k_plan                 chi and the sub-step count (planning, Algorithms 1/2)
-//   k_cold                 one thread per particle: plan, sub-step loop,
-//                          events, children; particles whose plan exceeds
-//                          hot_min sub-steps are pushed to the hot queue
-//   k_hot                  persistent kernel: one warp per queued particle,
-//                          64 sub-steps per iteration (lane l draws the
-//                          Philox block of sub-steps 2l, 2l+1), first accepted
-//                          sub-step found with ballots
+//   k_cold                 thread pass: one lane per row for the plan and
+//                          events, the warp's lanes together for the draws;
+//                          plans of at least hot_min sub-steps are queued
+//   k_hot_lanes            hot pass (persistent): long plans one warp each
+//                          (64 sub-steps per iteration, lane l drawing the
+//                          Philox block of sub-steps 2l, 2l+1), medium plans
+//                          one lane each with warp-shared draws; in sampler
+//                          mode the network runs on the tensor cores for all
+//                          lanes with an event
 //   k_advance              closes a cascade generation
 //
 // Every sub-step draws (x, y) from Philox4x32-10 at counter
@@ -46,21 +48,16 @@ constexpr uint32_t kHotMinDefault = 32;    // plans with N >= hot_min go to the 
 constexpr uint32_t kLongMinDefault = 256;  // ... and with N >= long_min to its warp mode
 
 // Minimum resident blocks per SM requested from the register allocator:
-// 3 x 256 threads hold the thread pass at 80 registers (24 warps per SM);
-// 8 x 128 hold the warp pass at 64 (32 warps per SM), which measured faster
-// than 6 x 128 at 80 registers despite a few spilled values.
+// 3 x 256 threads hold the thread and hot passes at 80 registers (24 warps
+// per SM).
 #ifndef QED_COLD_MIN_BLOCKS
 #define QED_COLD_MIN_BLOCKS 3
 #endif
 #ifndef QED_LANES_MIN_BLOCKS
 #define QED_LANES_MIN_BLOCKS 3
 #endif
-#ifndef QED_HOT_MIN_BLOCKS
-#define QED_HOT_MIN_BLOCKS 8
-#endif
 constexpr int kColdThreads = 256;
 constexpr int kLaneThreads = 256;
-constexpr int kHotThreads = 128;
 constexpr int kSweepThreads = 256;
 
 struct DevCtl {
@@ -608,9 +605,11 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                             P.pz[i] = st.pz;
                             changed = false;
                         }
-                        // the hot pass plans again; the sampler mode steps
-                        // every hot particle with a whole warp
-                        push_hot(S, ctl, i, s, t_rem, SP.sampler || pl.N >= SP.long_min);
+                        // the hot pass plans again; long plans and the
+                        // sampler's particles are stepped by a whole warp,
+                        // the others by a lane
+                        push_hot(S, ctl, i, s, t_rem,
+                                 pl.N >= SP.long_min || (!photon && sampler_bin_ok(SP, chi)));
                         active = false;
                     } else {
                         stats.plans++;
@@ -668,10 +667,9 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
 // arguments): 64 sub-steps per iteration (lane l draws the Philox block of
 // sub-steps 2l and 2l+1), the first accepted sub-step found with two ballots.
 // Statistics are counted on lane 0, candidates per lane.
-// kSampler: e+- in a usable bin of the sampler's chi range decide events from
-// the tabulated total probability c_h W(b) and take the energy fraction from
-// the network (x = delta^{1/3} at the event's uniform); the others use
-// rejection as usual.
+// kSampler: an e+- in a usable bin of the sampler's chi range decides events
+// from the tabulated total probability c_h W(b) and takes the energy fraction
+// from the network at the event's uniform, evaluated by the warp (FP32).
 template <bool kSampler>
 __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& S,
                                           const StepParams& SP, DevCtl* ctl,
@@ -754,8 +752,8 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
             const uint32_t s_ev = sa + (uint32_t)pos;
             const float xo = (pos & 1) ? u01(r.z) : u01(r.x);
             float x = __shfl_sync(0xffffffffu, xo, pos >> 1);
-            if (use_net) {
-                // inverse sampling: the event's uniform goes through the network
+            if (kSampler && use_net) {
+                // inverse sampling: the event's uniform through the network
                 x = mlp_infer_warp(net, log10f(chi) * 0.5f, mlp_input_u(x));
                 if (lane == 0) stats.sampled++;
             }
@@ -784,37 +782,6 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
     }
 }
 
-// Hot pass of the sampler mode: every queued particle stepped by a whole warp
-// (warp_item), so that the network can be evaluated by the warp.
-template <bool kSampler>
-__global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevParticles P, StepParams SP, Scratch S,
-                                                     DevCtl* ctl) {
-    const uint32_t step = step_index(SP);
-    __shared__ SharedTables sm;
-    extern __shared__ __align__(16) unsigned char dyn_smem[];
-    SamplerSmem& net = *reinterpret_cast<SamplerSmem*>(dyn_smem);
-    stage_tables(sm);
-    if (kSampler)
-        stage_sampler(net, reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
-                      SP.net_rows, SP.net_bins);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const unsigned int tail = ctl->hot_tail;
-    const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
-    Stats stats;              // counted on lane 0 only
-    unsigned int cand = 0;    // candidates, counted per lane
-    while (true) {
-        unsigned int q = 0;
-        if (lane == 0) q = atomicAdd(&ctl->hot_head, 1u);
-        q = __shfl_sync(0xffffffffu, q, 0);
-        if (q >= tail) break;
-        warp_item<kSampler>(P, S, SP, ctl, sm, net, S.hot[q], step, k0, k1, stats, cand);
-    }
-    if (lane != 0) stats = Stats();
-    stats.cand = cand;
-    stats.warp_substeps = stats.substeps;
-    flush_stats(stats, ctl);
-}
 
 // Hot pass (rejection).  Long plans (N >= long_min, front of the queue) first,
 // one warp each (warp_item), so that their long chains start early; then the
@@ -826,13 +793,22 @@ __global__ void __launch_bounds__(kHotThreads, QED_HOT_MIN_BLOCKS) k_hot(DevPart
 // take the next queue entries (one atomic per warp).  Persistent: the grid is
 // the resident block count, and a warp leaves when the queue is empty and its
 // lanes are idle.
+// kSampler: the sampler's particles (e+- in a usable bin of its chi range)
+// are queued for the warp mode, which evaluates the network (warp_item).
 constexpr uint32_t kWindow = 64;
+
+template <bool kSampler>
 __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lanes(DevParticles P, StepParams SP,
                                                                  Scratch S, DevCtl* ctl) {
     const uint32_t step = step_index(SP);
     __shared__ SharedTables sm;
     __shared__ uint32_t first_acc[kLaneThreads];
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    SamplerSmem& net = *reinterpret_cast<SamplerSmem*>(dyn_smem);
     stage_tables(sm);
+    if (kSampler)
+        stage_sampler(net, reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
+                      SP.net_rows, SP.net_bins);
     __syncthreads();
     if (ctl->status == (int)QED_ERR_TIMEOUT) return;
     constexpr unsigned int kAll = 0xffffffffu;
@@ -845,14 +821,12 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
         const unsigned int long_tail = ctl->hot_tail;
         Stats wstats;                 // counted on lane 0
         unsigned int wcand = 0;
-        extern __shared__ __align__(16) unsigned char dyn_smem[];
-        SamplerSmem& none = *reinterpret_cast<SamplerSmem*>(dyn_smem);   // unused
         while (true) {
             unsigned int q = 0;
             if (lane == 0) q = atomicAdd(&ctl->hot_head, 1u);
             q = __shfl_sync(kAll, q, 0);
             if (q >= long_tail) break;
-            warp_item<false>(P, S, SP, ctl, sm, none, S.hot[q], step, k0, k1, wstats, wcand);
+            warp_item<kSampler>(P, S, SP, ctl, sm, net, S.hot[q], step, k0, k1, wstats, wcand);
         }
         if (lane == 0) stats = wstats;
         stats.cand = wcand;
@@ -1234,7 +1208,7 @@ struct qed_ctx {
     long long* log_count;
     int cold_blocks, hot_blocks;
     int cold_blocks_max, hot_blocks_max;
-    int net_blocks;           // grid of the sampler's warp-per-particle pass
+    int net_blocks;           // grid of the hot pass in sampler mode
     uint32_t hot_min, long_min;
     // compaction
     Mirror mirror;
@@ -1499,10 +1473,12 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cold, kColdThreads, 0);
         ctx->cold_blocks = ctx->cold_blocks_max = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes, kLaneThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<false>, kLaneThreads, 0);
         ctx->hot_blocks = ctx->hot_blocks_max = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot<true>, kHotThreads,
+        cudaFuncSetAttribute(k_hot_lanes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SamplerSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<true>, kLaneThreads,
                                                       sizeof(SamplerSmem));
         ctx->net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         ctx->hot_min = kHotMinDefault;
@@ -1631,10 +1607,11 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
         {
             LaunchScope ls(ctx, QED_KERNEL_HOT);
             if (SP.sampler)
-                k_hot<true><<<ctx->net_blocks, kHotThreads, sizeof(SamplerSmem), ctx->stream>>>(
-                    D, SP, S, ctx->d_ctl);
+                k_hot_lanes<true><<<ctx->net_blocks, kLaneThreads, sizeof(SamplerSmem),
+                                    ctx->stream>>>(D, SP, S, ctx->d_ctl);
             else
-                k_hot_lanes<<<ctx->hot_blocks, kLaneThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+                k_hot_lanes<false><<<ctx->hot_blocks, kLaneThreads, 0, ctx->stream>>>(D, SP, S,
+                                                                                     ctx->d_ctl);
         }
         {
             LaunchScope ls(ctx, QED_KERNEL_CONTROL);
@@ -1817,10 +1794,9 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         if (st == QED_OK) {
             void* a[] = {&D, &SP, &S, &ctl};
             st = add_kernel(ctx, body, &bh,
-                            SP.sampler ? (const void*)k_hot<true> : (const void*)k_hot_lanes,
-                            dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks),
-                            dim3(SP.sampler ? kHotThreads : kLaneThreads), a, &bc, 1,
-                            SP.sampler ? sizeof(SamplerSmem) : 0);
+                            SP.sampler ? (const void*)k_hot_lanes<true> : (const void*)k_hot_lanes<false>,
+                            dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks), dim3(kLaneThreads),
+                            a, &bc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
         }
         if (st == QED_OK) {
             void* a[] = {&ctl, &count, &capacity, &more_allowed, &max_passes, &h, &use_handle};
@@ -2392,7 +2368,7 @@ qed_status noalloc_setup(int dev, NoAllocDevice* out) {
             return QED_ERR_CUDA;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_cold, k_cold, kColdThreads, 0) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot_lanes, kLaneThreads, 0) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot_lanes<false>, kLaneThreads, 0) !=
                 cudaSuccess)
             return QED_ERR_CUDA;
         d.base = static_cast<unsigned char*>(ptr);
@@ -2439,7 +2415,7 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     DevCtl h;
     for (int pass = 0; pass < max_passes; ++pass) {
         k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
-        k_hot_lanes<<<nd.hot_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
+        k_hot_lanes<false><<<nd.hot_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
         k_advance<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, cascade ? 1 : 0, max_passes, 0ull, 0);
         if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
         if (!cascade) break;

@@ -45,6 +45,26 @@ def test_gradient_matches_oracle_network():
     assert np.max(np.abs(g - go)) <= 2e-4 * np.max(np.abs(go))
 
 
+def test_network_inference_matches_oracle_network():
+    # the event kernels' arithmetic for the network (BF16 weights, FP32
+    # activations and accumulation) against the FP64 oracle network with the
+    # same BF16-rounded weights
+    ctx = qed.Context()
+    rng = np.random.default_rng(12)
+    th = mlp.init(21)
+    th_bf = torch.from_numpy(th.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    ctx.sampler_load(th.astype(np.float32))
+    n = 4099
+    l10 = rng.uniform(-2, 2, n).astype(np.float32)
+    u = rng.uniform(1e-6, 1 - 1e-6, n).astype(np.float32)
+    x = torch.zeros(n, device="cuda")
+    ctx.sampler_quantile(_dev(l10), _dev(u), x, use_net=True)
+    ref, _ = mlp.forward(th_bf, mlp.inputs(l10.astype(np.float64), u.astype(np.float64)))
+    d = np.abs(x.cpu().numpy().astype(np.float64) - ref)
+    print("network inference vs FP64 network: median %.2e max %.2e" % (np.median(d), d.max()))
+    assert np.median(d) < 1e-5 and d.max() < 1e-4
+
+
 def _oracle_cdf(b, x):
     """int_0^x 3x'^2 P(x'^3) dx' / int_0^1 (oracle acceptance function, Gauss-Legendre)."""
     xs, ws = np.polynomial.legendre.leggauss(24)
