@@ -1232,6 +1232,13 @@ struct qed_ctx {
     // multi-step graph
     cudaGraph_t graph;
     cudaGraphExec_t graph_exec;
+    // one event step as a graph (generations in a device-side loop), rebuilt
+    // when its key (store, scratch, parameters, grids) changes
+    cudaGraph_t step_graph;
+    cudaGraphExec_t step_exec;
+    uint64_t step_key[48];
+    int step_key_n;
+    uint32_t* d_step_idx;
     qed_step_stats* d_records;
     uint32_t* d_step_base;
     int graph_steps;
@@ -1495,6 +1502,9 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
 
 qed_status qed_destroy(qed_ctx* ctx) {
     if (!ctx) return QED_ERR_ARG;
+    if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+    if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+    if (ctx->d_step_idx) cudaFree(ctx->d_step_idx);
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     if (ctx->stream || ctx->d_ctl) cudaStreamSynchronize(ctx->stream);
     if (ctx->d_ctl) cudaFree(ctx->d_ctl);
@@ -1580,6 +1590,11 @@ qed_status qed_set_event_log(qed_ctx* ctx, qed_event_record* records, int64_t ca
     return QED_OK;
 }
 
+}  // extern "C"
+static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& D, StepParams SP,
+                                 const Scratch& S, uint32_t step);
+extern "C" {
+
 qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
                           qed_step_stats* out) {
     if (!ctx) return QED_ERR_ARG;
@@ -1595,6 +1610,14 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
     const DevParticles D = to_dev(p);
     const Scratch S = make_scratch(ctx);
     const bool cascade = cascade_enabled(ctx->cfg);
+    if (cascade && !ctx->prof_on) {
+        // the generations run in a device-side loop: no host round trip per
+        // generation (per-kernel timing needs the host loop below)
+        st = run_step_graph(ctx, D, SP, S, (uint32_t)step_index);
+        if (st != QED_OK) return st;
+        if (out) return qed_read_stats(ctx, out);
+        return QED_OK;
+    }
     {
         LaunchScope ls(ctx, QED_KERNEL_CONTROL);
         k_step_init<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, 0);
@@ -1761,7 +1784,6 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         SP.step_base = step_base;
         SP.hot_min = ctx->hot_min;
         SP.long_min = ctx->long_min;
-    SP.long_min = ctx->long_min;
         st = sampler_params(ctx, &SP);
         if (st != QED_OK) break;
         qed_step_stats* rec = ctx->d_records + k;
@@ -1864,6 +1886,110 @@ qed_status qed_graph_read_stats(qed_ctx* ctx, qed_step_stats* out, int nsteps) {
 }
 
 }  // extern "C"
+
+__global__ void k_set_step(uint32_t* p, uint32_t v) { *p = v; }
+
+// Build (when its key changed) and launch the one-step graph: step-init, then
+// a conditional WHILE node whose body is one cascade generation (thread
+// pass, hot pass, generation control; the control kernel sets the
+// condition).  The step index reaches the kernels through a device word
+// written by a kernel launched just before the graph.
+static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepParams SPin,
+                                 const Scratch& Sin, uint32_t step) {
+    if (!ctx->d_step_idx) QED_CUDA(ctx, cudaMalloc(&ctx->d_step_idx, sizeof(uint32_t)));
+    SPin.step = 0;
+    SPin.step_base = ctx->d_step_idx;
+    uint64_t key[48];
+    int nk = 0;
+    auto put = [&](uint64_t v) { if (nk < 48) key[nk++] = v; };
+    auto putf = [&](float v) { uint32_t b; memcpy(&b, &v, 4); put(b); };
+    auto putp = [&](const void* v) { put((uint64_t)(uintptr_t)v); };
+    for (const void* q : {(const void*)Din.px, (const void*)Din.py, (const void*)Din.pz,
+                          (const void*)Din.Ex, (const void*)Din.Ey, (const void*)Din.Ez,
+                          (const void*)Din.Bx, (const void*)Din.By, (const void*)Din.Bz,
+                          (const void*)Din.w, (const void*)Din.id, (const void*)Din.type,
+                          (const void*)Din.count})
+        putp(q);
+    put((uint64_t)Din.capacity);
+    putp(Sin.t_rem); putp(Sin.hot); put((uint64_t)Sin.hot_cap); putp(Sin.log);
+    put((uint64_t)Sin.log_cap); putp(Sin.log_count);
+    put(SPin.seed);
+    { uint64_t b; memcpy(&b, &SPin.dt, 8); put(b); }
+    putf(SPin.K); putf(SPin.inv_Es); putf(SPin.p_max); putf(SPin.inv_p_max); putf(SPin.pair_coeff);
+    putf(SPin.t_step.hi); putf(SPin.t_step.lo);
+    put(SPin.hot_min); put(SPin.long_min); put((uint64_t)SPin.sampler); put((uint64_t)SPin.net_rows);
+    put(SPin.net_bins); putp(SPin.net_w); putp(SPin.net_wtot); put(SPin.process_mask);
+    put((uint64_t)SPin.recoil); put((uint64_t)SPin.cascade);
+    put((uint64_t)ctx->cold_blocks); put((uint64_t)ctx->hot_blocks); put((uint64_t)ctx->net_blocks);
+    put((uint64_t)ctx->cfg.max_passes);
+    const bool same = ctx->step_exec && nk == ctx->step_key_n &&
+                      memcmp(key, ctx->step_key, sizeof(uint64_t) * nk) == 0;
+    if (!same) {
+        if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+        if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+        ctx->step_exec = nullptr;
+        ctx->step_graph = nullptr;
+        QED_CUDA(ctx, cudaGraphCreate(&ctx->step_graph, 0));
+        cudaGraph_t g = ctx->step_graph;
+        // node arguments live in this frame until the graph is instantiated
+        DevParticles D = Din;
+        StepParams SP = SPin;
+        Scratch S = Sin;
+        DevCtl* ctl = ctx->d_ctl;
+        long long* count = D.count;
+        long long capacity = D.capacity;
+        int keep_sticky = 0, more_allowed = 1, max_passes = ctx->cfg.max_passes, use_handle = 1;
+        cudaGraphNode_t init, wnode, bc, bh, ba;
+        qed_status st;
+        {
+            void* a[] = {&ctl, &count, &capacity, &keep_sticky};
+            st = add_kernel(ctx, g, &init, (const void*)k_step_init, dim3(1), dim3(1), a, nullptr, 0);
+        }
+        cudaGraphConditionalHandle h;
+        if (st == QED_OK)
+            st = cuda_check(ctx, cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault),
+                            "cudaGraphConditionalHandleCreate");
+        cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+        if (st == QED_OK) {
+            memset(&cp.conditional, 0, sizeof cp.conditional);
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            st = cuda_check(ctx, cudaGraphAddNode(&wnode, g, &init, nullptr, 1, &cp),
+                            "cudaGraphAddNode");
+        }
+        if (st == QED_OK) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            void* a[] = {&D, &SP, &S, &ctl};
+            st = add_kernel(ctx, body, &bc, (const void*)k_cold, dim3(ctx->cold_blocks),
+                            dim3(kColdThreads), a, nullptr, 0);
+            if (st == QED_OK)
+                st = add_kernel(ctx, body, &bh,
+                                SP.sampler ? (const void*)k_hot_lanes<true>
+                                           : (const void*)k_hot_lanes<false>,
+                                dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks),
+                                dim3(kLaneThreads), a, &bc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
+            if (st == QED_OK) {
+                void* b[] = {&ctl, &count, &capacity, &more_allowed, &max_passes, &h, &use_handle};
+                st = add_kernel(ctx, body, &ba, (const void*)k_advance, dim3(1), dim3(1), b, &bh, 1);
+            }
+        }
+        if (st == QED_OK)
+            st = cuda_check(ctx, cudaGraphInstantiate(&ctx->step_exec, g, 0), "cudaGraphInstantiate");
+        if (st != QED_OK) {
+            if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+            ctx->step_graph = nullptr;
+            ctx->step_exec = nullptr;
+            return st;
+        }
+        memcpy(ctx->step_key, key, sizeof(uint64_t) * nk);
+        ctx->step_key_n = nk;
+    }
+    k_set_step<<<1, 1, 0, ctx->stream>>>(ctx->d_step_idx, step);
+    QED_CUDA(ctx, cudaGetLastError());
+    ctx->launches[QED_KERNEL_CONTROL] += 1;
+    return cuda_check(ctx, cudaGraphLaunch(ctx->step_exec, ctx->stream), "cudaGraphLaunch");
+}
 
 // ---------------------------------------------------------------------------
 // Learned sampler
