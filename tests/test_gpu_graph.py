@@ -141,3 +141,24 @@ def test_cascade_batch_graph_small():
     assert stats[-1]["count"] > 0
     assert sum(s["substeps"] for s in stats) > n
     assert ctx.read_spectrum().sum() > 0
+
+
+def test_host_loop_equals_graph_step():
+    # with per-kernel timing the step runs generation by generation from the
+    # host; without, as the cached one-step graph: same results
+    arr = I.clumped_mixed(30000, 33, hot_fraction=0.03)
+    cap = 30000 * 40
+    out = []
+    for profile in (False, True):
+        ctx = qed.Context(seed=17)
+        ctx.profile(profile)
+        store = qed.ParticleStore.from_numpy(arr, capacity=cap)
+        sts = [ctx.event_step(store, 40 + k) for k in range(2)]
+        out.append((sts, _sorted(store.to_numpy())))
+    (sa, ga), (sb, gb) = out
+    for a, b in zip(sa, sb):
+        for k in ("substeps", "emissions", "pairs", "children", "plans", "max_N", "passes",
+                  "status", "count"):
+            assert a[k] == b[k], (k, a[k], b[k])
+    for k in ga:
+        np.testing.assert_array_equal(ga[k], gb[k])

@@ -219,6 +219,106 @@ def test_event_step_pairs_only():
     _check(arr, 2, capacity=2000 * 4, seed=8, mask=2, cascade=False)
 
 
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 64])
+def test_tiny_populations_over_several_steps(n):
+    # brute force on tiny stores: every particle, every event, three global
+    # steps, each started from the GPU's own result (children included)
+    arr = I.clumped_mixed(max(n, 4), 500 + n, hot_fraction=0.5)
+    arr = {k: v[:n] for k, v in arr.items()}
+    for step in range(3):
+        g_store, g_st, g_ev = _run_gpu(arr, step, n * 4000, seed=31 + n, process_mask=3,
+                                       cascade=True)
+        cf = O.make_config(31 + n, process_mask=3, cascade=1)
+        o_store, o_st, o_ev, o_ties = O.event_step(cf, arr, step, capacity=n * 4000)
+        rep = parity.compare(g_ev, o_ev, o_ties, g_store, o_store, arr["id"])
+        assert g_st["status"] == 0 and o_st["status"] == 0
+        assert not rep["mismatches"], (step, rep["mismatches"][:3])
+        if len(o_ties) == 0:
+            for k in ("substeps", "emissions", "pairs", "children", "plans"):
+                assert g_st[k] == o_st[k], (step, k)
+        arr = g_store
+
+
+def _crossed_beam(M, gamma, chi_t, photon=False):
+    """M identical particles meeting a crossed field head-on (E0 y, B0 z, moving -x)."""
+    f32 = np.float32
+    pm = gamma if photon else math.sqrt(gamma * gamma - 1.0)
+    E0 = np.float32(chi_t * O.schwinger_field() / (gamma + pm))
+    arr = {"px": np.full(M, -pm, f32), "py": np.zeros(M, f32), "pz": np.zeros(M, f32),
+           "Ex": np.zeros(M, f32), "Ey": np.full(M, E0, f32), "Ez": np.zeros(M, f32),
+           "Bx": np.zeros(M, f32), "By": np.zeros(M, f32), "Bz": np.full(M, E0, f32),
+           "w": np.ones(M, f32), "id": np.arange(M, dtype=np.uint64),
+           "type": np.full(M, 2 if photon else 0, np.uint8)}
+    chi, g = O.chi((-pm, 0.0, 0.0), (0.0, float(E0), 0.0), (0.0, 0.0, float(E0)), photon=photon)
+    return arr, chi, g
+
+
+def _x_cdf(kind, b, x):
+    """Normalised CDF of the event variable at x from the oracle's acceptance
+    function (Gauss-Legendre): x = delta^{1/3} for emission, delta_e for pairs."""
+    xs, ws = np.polynomial.legendre.leggauss(24)
+    f = O.Pm if kind == 0 else O.Pp
+
+    def integ(a, c, panels):
+        edges = np.linspace(a, c, panels + 1)
+        tot = 0.0
+        for lo, hi in zip(edges[:-1], edges[1:]):
+            for xx, ww in zip(0.5 * (lo + hi) + 0.5 * (hi - lo) * xs, ws):
+                tot += 0.5 * (hi - lo) * ww * f(b, 1.0, float(xx))
+        return tot
+    return integ(0.0, x, 12) / integ(0.0, 1.0, 24)
+
+
+def test_emission_spectrum_ks_against_oracle_and_closed_form():
+    # no recoil: every event is an independent draw from the spectrum at fixed
+    # (chi, gamma); GPU and oracle run with different seeds
+    from scipy import stats
+    arr, chi, g = _crossed_beam(20000, 1000.0, 1.0)
+    _, g_st, g_ev = _run_gpu(arr, 0, 20000 * 40, seed=101, process_mask=1, cascade=False,
+                             recoil=False)
+    small = I.subset(arr, np.arange(3000))
+    cf = O.make_config(202, process_mask=1, cascade=0, recoil=0)
+    _, o_st, o_ev, _ = O.event_step(cf, small, 0, capacity=3000 * 40)
+    xg = np.cbrt(g_ev["delta"].astype(np.float64))
+    xo = np.cbrt(o_ev["delta"].astype(np.float64))
+    assert len(xg) > 20000 and len(xo) > 3000
+    p2 = stats.ks_2samp(xg, xo).pvalue
+    grid = np.linspace(0.0, 1.0, 161)
+    cdf = np.array([_x_cdf(0, 1.5 * chi, v) if v > 0 else 0.0 for v in grid])
+    p1 = stats.kstest(xg, lambda v: np.interp(v, grid, cdf)).pvalue
+    print("emission spectrum: KS GPU vs oracle p=%.3f, GPU vs closed form p=%.3f" % (p2, p1))
+    assert p2 > 0.01 and p1 > 0.01
+
+
+def test_pair_spectrum_ks_and_symmetry():
+    # photons at chi_gamma ~ 5, pairs only, no recoil (the photon is kept, so
+    # its decays are independent draws); the electron fraction is symmetric
+    # about 1/2
+    from scipy import stats
+    arr, chi, g = _crossed_beam(20000, 2000.0, 5.0, photon=True)
+    _, g_st, g_ev = _run_gpu(arr, 0, 20000 * 40, seed=303, process_mask=2, cascade=False,
+                             recoil=False)
+    small = I.subset(arr, np.arange(3000))
+    cf = O.make_config(404, process_mask=2, cascade=0, recoil=0)
+    _, o_st, o_ev, _ = O.event_step(cf, small, 0, capacity=3000 * 40)
+    dg = g_ev["delta"].astype(np.float64)
+    do = o_ev["delta"].astype(np.float64)
+    assert len(dg) > 5000 and len(do) > 500
+    p2 = stats.ks_2samp(dg, do).pvalue
+    # symmetry about 1/2, on independent data: the distances from 1/2 of the
+    # events below and above it have one distribution, and each side holds
+    # half of the events (binomial)
+    left, right = 0.5 - dg[dg < 0.5], dg[dg > 0.5] - 0.5
+    ps = min(stats.ks_2samp(left, right).pvalue,
+             stats.binomtest(len(left), len(left) + len(right), 0.5).pvalue)
+    grid = np.linspace(0.0, 1.0, 161)
+    cdf = np.array([_x_cdf(1, 1.5 * chi, v) if v > 0 else 0.0 for v in grid])
+    p1 = stats.kstest(dg, lambda v: np.interp(v, grid, cdf)).pvalue
+    print("pair spectrum: KS GPU vs oracle p=%.3f, vs closed form p=%.3f, symmetry p=%.3f"
+          % (p2, p1, ps))
+    assert p2 > 0.01 and p1 > 0.01 and ps > 0.01
+
+
 def _sampled_full_size(arr, capacity, seed, mask, roots, log_cap):
     g_store, g_st, g_ev = _run_gpu(arr, 0, capacity, log_cap=log_cap, seed=seed,
                                    process_mask=mask, cascade=True)
