@@ -38,10 +38,26 @@ SEED_CASCADE = 20081046 + 4
 CASCADE_CELLS = 4096
 CASCADE_CAPACITY = 1 << 26
 CASCADE_DRAIN_CHI = 0.05
+# DRAM bytes (read + write) per launch of the hot pass on the 2^24 clumped
+# population, from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum over every launch of two profiled steps; see
+# profiles/k_hot_lanes_traffic_clumped_2p24.md), valid for the kernel sources
+# whose SHA-256 is given; any other source reports traffic as unknown.
+HOT_TRAFFIC = {"bytes_per_launch": None, "sources_sha256": None}
+
 METRIC = "particle-steps/sec (sub-stepped)"
 UNIT = "substeps/s"
 WORKLOAD = ("clumped mixed population 2^24 (25% e-, 25% e+, 50% photons; 1% hot clump "
             "chi 10-100), emission + pairs + in-step cascade, one global step dt = 0.1 T")
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("qed.cu", "qed_device.cuh", "qed_sampler.cuh", "synchro_coeffs.h"):
+        with open(os.path.join(ROOT, "paper_2008_10468_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def peaks():
@@ -309,8 +325,10 @@ def run_gb300(args):
         t_launch = kern["hot"][0] / kern["hot"][1] / 1e3
         per_launch = 20.0 * pagg["substeps_warp"] / kern["hot"][1]
         achieved = per_launch / t_launch / 1e12
+        traffic = (HOT_TRAFFIC["bytes_per_launch"]
+                   if HOT_TRAFFIC["sources_sha256"] == kernel_sources_sha256() else None)
         roof = {"kernel": "k_hot_lanes", "bound": "alu", "achieved": achieved, "peak": mul_peak,
-                "unit": "T int32-mul/s", "frac": achieved / mul_peak, "traffic": None,
+                "unit": "T int32-mul/s", "frac": achieved / mul_peak, "traffic": traffic,
                 "peak_kind": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz"}
 
     # synchrotron sweep, array mode and generation mode
@@ -498,7 +516,10 @@ def run_sampler(arr, pristine, store, cap, n, dev, args, restore, plain_value):
 
 def run_e2e(ctx, arr, cap, dev, args):
     """Same metric through the API with host buffers: per step copy the
-    population from pinned host memory, step, copy every row back."""
+    population from pinned host memory, step, and copy the result back: the
+    momenta and types of the original rows (the only fields a step changes
+    there) and every field of the appended children, so that the host holds
+    the whole updated store."""
     import torch
     from paper_2008_10468_gb300 import qed
     n = len(arr["px"])
@@ -508,6 +529,8 @@ def run_e2e(ctx, arr, cap, dev, args):
     host["id"] = torch.from_numpy(arr["id"].view(np.int64)).pin_memory()
     host["type"] = torch.from_numpy(arr["type"]).pin_memory()
     out = {k: torch.empty(cap, dtype=v.dtype).pin_memory() for k, v in host.items()}
+    for k, v in host.items():   # fields the step leaves unchanged on the original rows
+        out[k][:n].copy_(v)
     store = qed.ParticleStore(cap, device=dev)
     stream = torch.cuda.current_stream()
     steps = max(2, min(args.steps, 5))
@@ -529,8 +552,9 @@ def run_e2e(ctx, arr, cap, dev, args):
         m = st["count"]
         b_out = 0
         for key in host:
-            src = getattr(store, key)[:m]
-            out[key][:m].copy_(src, non_blocking=True)
+            lo = 0 if key in ("px", "py", "pz", "type") else n
+            src = getattr(store, key)[lo:m]
+            out[key][lo:m].copy_(src, non_blocking=True)
             b_out += src.numel() * src.element_size()
         e1.record(stream)
         torch.cuda.synchronize()
