@@ -43,7 +43,8 @@ CASCADE_DRAIN_CHI = 0.05
 # dram__bytes_write.sum over every launch of two profiled steps; see
 # profiles/k_hot_lanes_traffic_clumped_2p24.md), valid for the kernel sources
 # whose SHA-256 is given; any other source reports traffic as unknown.
-HOT_TRAFFIC = {"bytes_per_launch": None, "sources_sha256": None}
+HOT_TRAFFIC = {"bytes_per_launch": 39.09e6,
+               "sources_sha256": "c58a226b0e881fc2282ecc8b53bf193e6e2d41d961ac35ac4fc4c5ea2e65534f"}
 
 METRIC = "particle-steps/sec (sub-stepped)"
 UNIT = "substeps/s"
