@@ -438,8 +438,10 @@ __device__ __forceinline__ void push_hot(const Scratch& S, DevCtl* ctl, long lon
         S.hot[S.hot_cap - 1 - (long long)atomicAdd(&ctl->med_tail, 1u)] = it;
     }
 }
+
 // With the learned sampler on, e+- whose chi lies in a usable bin of its
-// range are stepped on the warp path, where the network is evaluated.
+// range (64 bins uniform in log10 chi over [-2, 2)) are stepped in the hot
+// pass's warp mode, where the network is evaluated.
 __device__ __forceinline__ bool sampler_bin_ok(const StepParams& SP, float chi) {
     if (!SP.sampler || !(chi >= 1e-2f && chi < 1e2f)) return false;
     const int bin = min(max((int)((log10f(chi) - kMlpLog10Lo) * 16.0f), 0), 63);

@@ -199,17 +199,8 @@ __device__ __forceinline__ void stage_syn_table(SynTable& tb) {
 // ---------------------------------------------------------------------------
 constexpr float kPi = 3.14159265358979f;
 
-__device__ __forceinline__ float bound_emission(float b, float c) {
-    float lead;
-    if (b < 0.1f) lead = 0.56f * kPi * b;
-    else if (b < 0.5f) lead = 0.45f * kPi * powf(b, 11.0f / 12.0f);
-    else if (b < 10.0f) lead = 0.42f * kPi * powf(b, 19.0f / 24.0f);
-    else lead = 0.55f * kPi * powf(b, 2.0f / 3.0f);
-    return c * (lead + 0.1f * b);
-}
-
-// The same bound from l2b = log2(b) (b > 0): the powers as exp2(a l2b) on the
-// special-function unit (relative error ~3e-7, far inside the planner's
+// The emission bound from l2b = log2(b) (b > 0): the powers as exp2(a l2b) on
+// the special-function unit (relative error ~3e-7, far inside the planner's
 // 2e-5 safety band).
 __device__ __forceinline__ float bound_emission_l2(float b, float l2b, float c) {
     float lead;

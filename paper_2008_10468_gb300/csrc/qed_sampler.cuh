@@ -533,12 +533,4 @@ __device__ __forceinline__ float sampler_wtot(const SamplerSmem& S, float chi) {
     return __expf((1.0f - w) * __logf(S.wtot[i]) + w * __logf(S.wtot[i + 1]));
 }
 
-// The sampler replaces rejection for e+- with chi in its range and an
-// accepted error bin (64 bins uniform in log10 chi).
-__device__ __forceinline__ bool sampler_usable(const SamplerSmem& S, float chi) {
-    if (!(chi >= 1e-2f && chi < 1e2f)) return false;
-    const int bin = min(max((int)((log10f(chi) - kMlpLog10Lo) * 16.0f), 0), 63);
-    return (S.bin_ok >> bin) & 1ull;
-}
-
 }  // namespace qed
