@@ -40,11 +40,11 @@ CASCADE_CAPACITY = 1 << 26
 CASCADE_DRAIN_CHI = 0.05
 # DRAM bytes (read + write) per launch of the hot pass on the 2^24 clumped
 # population, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum over every launch of two profiled steps; see
+# dram__bytes_write.sum over every launch of three profiled steps; see
 # profiles/k_hot_lanes_traffic_clumped_2p24.md), valid for the kernel sources
 # whose SHA-256 is given; any other source reports traffic as unknown.
-HOT_TRAFFIC = {"bytes_per_launch": 39.09e6,
-               "sources_sha256": "c58a226b0e881fc2282ecc8b53bf193e6e2d41d961ac35ac4fc4c5ea2e65534f"}
+HOT_TRAFFIC = {"bytes_per_launch": 37.72e6,
+               "sources_sha256": "63f473d16c03a12fe0143fe1920caa851c3202874de542501973bb8ac4480d16"}
 
 METRIC = "particle-steps/sec (sub-stepped)"
 UNIT = "substeps/s"

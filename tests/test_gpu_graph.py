@@ -153,7 +153,11 @@ def test_host_loop_equals_graph_step():
         ctx = qed.Context(seed=17)
         ctx.profile(profile)
         store = qed.ParticleStore.from_numpy(arr, capacity=cap)
-        sts = [ctx.event_step(store, 40 + k) for k in range(2)]
+        sts = []
+        for k in range(2):
+            sts.append(ctx.event_step(store, 40 + k))
+            assert sts[-1]["count"] == store.n()   # the count after the step's children
+        assert sts[0]["children"] > 0
         out.append((sts, _sorted(store.to_numpy())))
     (sa, ga), (sb, gb) = out
     for a, b in zip(sa, sb):
