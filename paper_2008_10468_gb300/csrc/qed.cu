@@ -340,8 +340,8 @@ __device__ __forceinline__ bool apply_event(const DevParticles& P, const Scratch
     const int lane = threadIdx.x & 31;
     long long j = -1;
     if (warp_caller) {
+        // lane 0 reserves and stores; its result is first needed at the stores
         if (lane == 0) j = reserve_rows(P, ctl, nch, false);
-        j = __shfl_sync(0xffffffffu, j, 0);
     } else if (write_rows) {
         j = reserve_rows(P, ctl, nch, true);
     }
