@@ -164,8 +164,9 @@ qed_status qed_plan(qed_ctx* ctx, const qed_particles* p, int64_t n, float* chi,
  * Philox4x32-10 draws keyed by (id, step_index, sub-step), emits photons /
  * decays (photons are marked removed, type 3), recoils, and is re-planned
  * after every event over the remaining time.  Children are appended at rows
- * count.. and, if cascade_in_step, processed in the same step.
- * If out != NULL the call synchronises the stream and fills *out; if NULL it
+ * count.. and, if cascade_in_step, processed in the same step: generation by
+ * generation while the generations are large, then (qed_set_tail) the rest
+ * in one tail pass.  If out != NULL the call synchronises the stream and fills *out; if NULL it
  * returns without waiting (statistics readable with qed_read_stats).
  * Capacity: if the children do not fit, status QED_ERR_CAPACITY is returned
  * (in *out and as the return value when out != NULL) with the rows needed;
@@ -203,8 +204,8 @@ qed_status qed_read_spectrum(qed_ctx* ctx, double* out, int nbins, int reset);
 /* Record `nsteps` consecutive global steps (step indices first_step ..
  * first_step + nsteps - 1) on store `p` as one CUDA graph: per step, the
  * cascade generations run in a device-side loop (a conditional WHILE node
- * whose condition the last kernel of each generation sets), then the store is
- * compacted (qed_compact), then the step's statistics are recorded on the
+ * whose condition the last kernel of each generation sets), then the tail
+ * pass (qed_set_tail), then the store is compacted (qed_compact), then the step's statistics are recorded on the
  * device.  No host synchronisation inside.  Each launch continues the step
  * numbering: the first launch runs steps first_step .. first_step + nsteps - 1,
  * the next one the following nsteps indices (fresh draws and child ids).
@@ -288,10 +289,20 @@ qed_status qed_sampler_save(qed_ctx* ctx, float* params, int64_t n);
 qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, uint32_t long_min,
                           int cold_blocks_per_sm, int hot_blocks_per_sm);
 
+/* Tail pass of the cascade (Sec. 2: the events of one step form a cascade
+ * whose generations shrink).  Once a generation has fewer than tail_rows rows
+ * the generations stop: one thread pass over that generation, then one
+ * persistent kernel takes its queue and every child appended after it as
+ * they come, so that the step is not bound by the longest chain of each
+ * small generation in turn.  0 turns it off; default 262144 rows.  No
+ * setting changes a result (the passes count counts the tail as one).
+ * Errors: QED_ERR_ARG (ctx null, tail_rows < 0). */
+qed_status qed_set_tail(qed_ctx* ctx, int64_t tail_rows);
+
 /* Time qed_event_step on `p` (step index step_index) for a coordinate search
  * over the launch settings (hot_min 16 ... 256, long_min 128 ... 2048 or
- * never, blocks per SM
- * of each pass), keep the fastest, and restore the store from a snapshot
+ * never, blocks per SM of each pass, tail_rows 0 or 2^14 ... 2^22), keep the
+ * fastest, and restore the store from a snapshot
  * after every trial (the store is unchanged on return).  Writes the chosen
  * settings and all trial timings as JSON to out_json (host file path,
  * nullable).  Uses the compaction mirror as snapshot.  Synchronises.
@@ -329,7 +340,7 @@ qed_status qed_profile_read(qed_ctx* ctx, double* ms, int64_t* launches, int n);
  * runs while a CUDA stream is being captured, hosts that hand out a fixed
  * memory budget in advance, and plug-ins living inside another program's
  * memory pool.  No context: the run configuration is passed directly, and the
- * step's scratch (about 1.5 MB) lives in a device array built into this
+ * step's scratch (about 2.5 MB) lives in a device array built into this
  * library, which every GPU that loads the library keeps until the process
  * exits.  The paper has no counterpart; this is a packaging of the same step.
  *

@@ -11,9 +11,15 @@
 //                          (64 sub-steps per iteration, lane l drawing the
 //                          Philox block of sub-steps 2l, 2l+1), medium plans
 //                          one lane each with warp-shared draws; in sampler
-//                          mode the network runs on the tensor cores for all
-//                          lanes with an event
-//   k_advance              closes a cascade generation
+//                          mode the warp of a sampler particle evaluates the
+//                          network for its events
+//   k_advance              closes a cascade generation; below tail_rows rows
+//                          it hands the rest of the step to the tail pass
+//   k_tail_begin / k_step / k_tail_end
+//                          tail pass: after one more thread pass, a persistent
+//                          kernel takes the queue and every child appended
+//                          later (no generations), children published by
+//                          their writers
 //
 // Every sub-step draws (x, y) from Philox4x32-10 at counter
 // (id_lo, id_hi, step, s/2) under key = seed (even s: words 0,1; odd s:
@@ -46,6 +52,7 @@ constexpr double kPiD = 3.14159265358979323846;
 // hot_min 32..128 and long_min 128..2048)
 constexpr uint32_t kHotMinDefault = 32;    // plans with N >= hot_min go to the hot pass
 constexpr uint32_t kLongMinDefault = 256;  // ... and with N >= long_min to its warp mode
+constexpr long long kTailRowsDefault = 1ll << 18;   // generations below this go to the tail pass
 
 // Minimum resident blocks per SM requested from the register allocator:
 // 3 x 256 threads hold the thread and hot passes at 80 registers (24 warps
@@ -75,8 +82,22 @@ struct DevCtl {
     int sticky;          // first error of a multi-step graph run: later steps do nothing
     long long live;      // rows kept by the last compaction
     int compact_needed;  // the last compaction found removed rows
-    int pad_;
+    int tail;            // the generations stopped below tail_rows: the tail pass finishes the step
+    unsigned int hot_hw;            // long-plan queue entries written by this step's generations
+    // tail pass (persistent kernel)
+    long long n0;                   // first child row of the tail (rows before it are done)
+    unsigned long long child_head;  // next child row (from n0) to take
+    unsigned long long finished;    // work units (queue entries, children) complete
+    unsigned int step_tail;         // long plans queued by the persistent kernel, stored
+                                    // after the thread pass's hot_tail entries
+    int skip;                       // the tail pass does nothing
 };
+
+// Type byte of a child row that has been reserved but not yet written: in the
+// tail pass the writer stores the row, fences, then stores its real type.
+constexpr uint8_t kNotReady = 0xFF;
+// Row index of a long-plan queue entry that has not been written yet.
+constexpr uint32_t kNoItem = 0xFFFFFFFFu;
 
 struct HotItem {
     uint32_t idx;
@@ -291,8 +312,9 @@ __device__ __forceinline__ long long reserve_rows(const DevParticles& P, DevCtl*
     }
     if (slot + n > P.capacity) {
         for (long long j = slot; j < slot + n && j < P.capacity; ++j) {
-            P.type[j] = QED_REMOVED;
             P.id[j] = 0;
+            __threadfence();   // a tail-pass lane may be waiting for this row
+            *reinterpret_cast<volatile uint8_t*>(P.type + j) = QED_REMOVED;
         }
         atomicMax(&ctl->required, slot + n);
         atomicExch(&ctl->status, (int)QED_ERR_CAPACITY);
@@ -306,9 +328,11 @@ struct Fields {
     float Ex, Ey, Ez, Bx, By, Bz;
 };
 
-__device__ __forceinline__ void write_child(const DevParticles& P, const Scratch& S, long long j,
-                                            const Fields& F, float w, float px, float py, float pz,
-                                            uint64_t id, uint8_t type, ftime t_rem) {
+// Every field of a child row but its type byte, which the caller stores last.
+__device__ __forceinline__ void write_child_fields(const DevParticles& P, const Scratch& S,
+                                                   long long j, const Fields& F, float w,
+                                                   float px, float py, float pz, uint64_t id,
+                                                   ftime t_rem) {
     P.px[j] = px;
     P.py[j] = py;
     P.pz[j] = pz;
@@ -320,7 +344,6 @@ __device__ __forceinline__ void write_child(const DevParticles& P, const Scratch
     P.Bz[j] = F.Bz;
     P.w[j] = w;
     P.id[j] = id;
-    P.type[j] = type;
     S.t_rem[j] = t_rem;
 }
 
@@ -335,7 +358,8 @@ __device__ __forceinline__ void write_child(const DevParticles& P, const Scratch
 __device__ __forceinline__ bool apply_event(const DevParticles& P, const Scratch& S, const StepParams& SP,
                             DevCtl* ctl, long long i, uint64_t id, bool photon, float x,
                             float eps, float chi, uint32_t step, uint32_t s, ftime t_after, PState& st,
-                            Stats& stats, bool write_rows, bool warp_caller, const Fields& F) {
+                            Stats& stats, bool write_rows, bool warp_caller, const Fields& F,
+                            bool publish) {
     const int nch = photon ? 2 : 1;
     const int lane = threadIdx.x & 31;
     long long j = -1;
@@ -373,10 +397,17 @@ __device__ __forceinline__ bool apply_event(const DevParticles& P, const Scratch
         const uint64_t cids[2] = {id0, id1};
         const uint8_t ctypes[2] = {photon ? (uint8_t)QED_ELECTRON : (uint8_t)QED_PHOTON,
                                    (uint8_t)QED_POSITRON};
-        if (!warp_caller || lane == 0)
+        if (!warp_caller || lane == 0) {
+            const float w = P.w[i];
             for (int r = 0; r < nch; ++r)
-                write_child(P, S, j + r, F, P.w[i], cp[r][0], cp[r][1], cp[r][2], cids[r],
-                            ctypes[r], t_after);
+                write_child_fields(P, S, j + r, F, w, cp[r][0], cp[r][1], cp[r][2], cids[r],
+                                   t_after);
+            // in the tail pass another warp may be waiting for these rows:
+            // one fence for the event's children, then their type bytes
+            if (publish) __threadfence();
+            for (int r = 0; r < nch; ++r)
+                *reinterpret_cast<volatile uint8_t*>(P.type + j + r) = ctypes[r];
+        }
     }
     if (!photon) {
         if (SP.recoil) {
@@ -396,12 +427,16 @@ __device__ __forceinline__ bool apply_event(const DevParticles& P, const Scratch
                 st.pz *= omd;
             }
         }
-        stats.emissions++;
-        stats.children++;
+        if (!warp_caller || lane == 0) {   // a warp caller counts on lane 0
+            stats.emissions++;
+            stats.children++;
+        }
     } else {
         removed = SP.recoil != 0;
-        stats.pairs++;
-        stats.children += 2;
+        if (!warp_caller || lane == 0) {
+            stats.pairs++;
+            stats.children += 2;
+        }
     }
     const bool logger = warp_caller ? lane == 0 : write_rows;
     if (logger && S.log) {
@@ -552,7 +587,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
     __shared__ uint32_t first_acc[kColdThreads];
     stage_tables(sm);
     __syncthreads();
-    if (ctl->status == (int)QED_ERR_TIMEOUT) return;
+    if (ctl->status == (int)QED_ERR_TIMEOUT || ctl->skip) return;
     const int first_pass = ctl->first_pass;
     const long long begin = first_pass ? 0 : ctl->pass_begin;
     const long long end = ctl->pass_end;
@@ -643,7 +678,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                                                            : time_sub_mul(t_rem, k + 1u, pl.h);
                     removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
                                           t_after, st, stats, true, false,
-                                          Fields{Ex, Ey, Ez, Bx, By, Bz});
+                                          Fields{Ex, Ey, Ez, Bx, By, Bz}, false);
                     changed = true;
                     s = s_ev + 1u;
                     t_rem = t_after;
@@ -677,7 +712,8 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
                                           const StepParams& SP, DevCtl* ctl,
                                           const SharedTables& sm, SamplerSmem& net,
                                           const HotItem& it, uint32_t step, uint32_t k0,
-                                          uint32_t k1, Stats& stats, unsigned int& cand) {
+                                          uint32_t k1, Stats& stats, unsigned int& cand,
+                                          bool publish) {
     const int lane = threadIdx.x & 31;
     const long long i = it.idx;
     const bool photon = P.type[i] == QED_PHOTON;
@@ -688,6 +724,7 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
     uint32_t s = it.s;
     ftime t_rem = it.t_rem;
     bool removed = false, changed = false;
+    const unsigned int sub0 = stats.substeps;
     while (time_positive(t_rem)) {
         float eps, chi;
         const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
@@ -764,7 +801,8 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
             const ftime t_after = (k_ev + 1 == pl.N) ? ftime{0.0f, 0.0f}
                                                      : time_sub_mul(t_rem, k_ev + 1, pl.h);
             removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev, t_after,
-                                  st, stats, lane == 0, true, Fields{Ex, Ey, Ez, Bx, By, Bz});
+                                  st, stats, lane == 0, true, Fields{Ex, Ey, Ez, Bx, By, Bz},
+                                  publish);
             changed = true;
             s = s_ev + 1;
             t_rem = t_after;
@@ -775,6 +813,7 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
         if (!event) t_rem = ftime{0.0f, 0.0f};
     }
     if (lane == 0) {
+        stats.warp_substeps += stats.substeps - sub0;
         if (removed) P.type[i] = QED_REMOVED;
         else if (changed) {
             P.px[i] = st.px;
@@ -828,7 +867,8 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
             if (lane == 0) q = atomicAdd(&ctl->hot_head, 1u);
             q = __shfl_sync(kAll, q, 0);
             if (q >= long_tail) break;
-            warp_item<kSampler>(P, S, SP, ctl, sm, net, S.hot[q], step, k0, k1, wstats, wcand);
+            warp_item<kSampler>(P, S, SP, ctl, sm, net, S.hot[q], step, k0, k1, wstats, wcand,
+                                false);
         }
         if (lane == 0) stats = wstats;
         stats.cand = wcand;
@@ -915,7 +955,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
                                                        : time_sub_mul(t_rem, k + 1u, pl.h);
                 removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
                                       t_after, st, stats, true, false,
-                                      Fields{Ex, Ey, Ez, Bx, By, Bz});
+                                      Fields{Ex, Ey, Ez, Bx, By, Bz}, false);
                 changed = true;
                 s = s_ev + 1u;
                 t_rem = t_after;
@@ -955,6 +995,357 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
     flush_stats(stats, ctl);
 }
 
+// ---------------------------------------------------------------------------
+// Tail pass.  Once a cascade generation falls below tail_rows rows, the
+// generations stop: a thread pass (k_cold) over that generation, then one
+// launch of this persistent kernel finishes the step, taking the thread pass's
+// queue and every child appended from then on (rows n0 and up) as they come.
+// Each warp takes, in order,
+//   1. a long plan from the queue (N >= long_min, or a sampler particle), stepped
+//      by the whole warp (warp_item);
+//   2. for its idle lanes, child rows appended so far, then the thread pass's
+//      medium plans, one lane each, drawn with the warp-shared rounds in windows
+//      of kWindow sub-steps.
+// A child row is published by its writer (type byte last, after a fence); a
+// lane that takes a row still being written waits for it.  Work units are the
+// thread pass's queue entries and the child rows; the pass ends when every
+// unit known so far (the children: the store count, capped at the capacity,
+// less n0) is complete.  Warps add their completed units to the control block
+// when they run out of work, so the count is exact whenever the test can
+// succeed.  Every wait is bounded: past kIdleLimit polls the kernel records
+// QED_ERR_TIMEOUT and returns.
+// ---------------------------------------------------------------------------
+constexpr unsigned int kIdleLimit = 1u << 22;    // polls of ~0.25 us: about 1 s
+
+__device__ __forceinline__ unsigned long long stored_rows(const DevParticles& P) {
+    const long long c = *reinterpret_cast<volatile long long*>(P.count);
+    return (unsigned long long)min(c, P.capacity);
+}
+
+// Queue a long plan: the entry's row index is written last (readers wait for it).
+__device__ __forceinline__ void push_long(const Scratch& S, DevCtl* ctl, unsigned int cold_long,
+                                          long long i, uint32_t s, ftime t_rem) {
+    const unsigned int k = cold_long + atomicAdd(&ctl->step_tail, 1u);
+    HotItem* e = S.hot + k;
+    e->s = s;
+    e->t_rem = t_rem;
+    __threadfence();
+    *reinterpret_cast<volatile uint32_t*>(&e->idx) = (uint32_t)i;
+}
+
+template <bool kSampler>
+__global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(DevParticles P, StepParams SP,
+                                                            Scratch S, DevCtl* ctl) {
+    const uint32_t step = step_index(SP);
+    __shared__ SharedTables sm;
+    __shared__ uint32_t first_acc[kLaneThreads];
+    __shared__ float fld[6][kLaneThreads];   // E, B at the lane's row (read at plans and events)
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    SamplerSmem& net = *reinterpret_cast<SamplerSmem*>(dyn_smem);
+    stage_tables(sm);
+    if (kSampler)
+        stage_sampler(net, reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
+                      SP.net_rows, SP.net_bins);
+    __syncthreads();
+    if (ctl->skip) return;
+    constexpr unsigned int kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    uint32_t* facc = first_acc + (threadIdx.x & ~31);
+    const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
+    const unsigned long long n0 = (unsigned long long)ctl->n0;
+    const bool cascade = SP.cascade != 0;
+    // the thread pass's queue (fixed during this kernel)
+    const unsigned int cold_long = ctl->hot_tail, cold_med = ctl->med_tail;
+    const unsigned long long units0 = (unsigned long long)cold_long + cold_med;
+    Stats stats;                 // per lane; the warp mode counts on lane 0
+    unsigned int done = 0;       // units this lane completed, not yet added to ctl->finished
+    bool active = false, waiting = false, child = false;
+    bool photon = false, changed = false, removed = false;
+    long long i = 0;
+    uint64_t id = 0;
+    PState st{0.0f, 0.0f, 0.0f};
+    ftime t_rem{0.0f, 0.0f};
+    uint32_t s = 0, k_done = 0;
+    Plan pl;
+    pl.N = 0;
+    pl.T = 0;
+    pl.b = pl.c_h = 0.0f;
+    float chi = 0.0f, eps = 0.0f;
+    unsigned int idle = 0;
+    unsigned int ticket = kNoItem;   // lane 0: long-queue entry taken, not yet pushed
+    unsigned long long pend_lo = 0, pend_hi = 0;   // lane 0: child indices taken, not handed out
+    bool timed_out = false;
+    while (true) {
+        // ---- 1. a long plan, stepped by the whole warp.  Lane 0 takes a ticket
+        // with one atomic add when the queue looks non-empty; a ticket past the
+        // tail is kept until its entry is pushed (void if the step ends first).
+        {
+            int got = 0;
+            unsigned int q = 0;
+            if (lane == 0) {
+                if (ticket == kNoItem &&
+                    *reinterpret_cast<volatile unsigned int*>(&ctl->hot_head) <
+                        cold_long + *reinterpret_cast<volatile unsigned int*>(&ctl->step_tail))
+                    ticket = atomicAdd(&ctl->hot_head, 1u);
+                if (ticket != kNoItem &&
+                    ticket < cold_long + *reinterpret_cast<volatile unsigned int*>(&ctl->step_tail)) {
+                    q = ticket;
+                    ticket = kNoItem;
+                    got = 1;
+                }
+            }
+            got = __shfl_sync(kAll, got, 0);
+            if (got) {
+                q = __shfl_sync(kAll, q, 0);
+                // the entry may still be being written: wait for its row index
+                HotItem it;
+                it.idx = kNoItem;
+                if (lane == 0) {
+                    const volatile uint32_t* vi = &S.hot[q].idx;
+                    for (unsigned int w = 0; w < kIdleLimit; ++w) {
+                        if (*vi != kNoItem) break;
+                        __nanosleep(64);
+                    }
+                    __threadfence();
+                    it = S.hot[q];
+                }
+                it.idx = __shfl_sync(kAll, it.idx, 0);
+                if (it.idx == kNoItem) {
+                    timed_out = true;
+                    break;
+                }
+                it.s = __shfl_sync(kAll, it.s, 0);
+                it.t_rem.hi = __shfl_sync(kAll, it.t_rem.hi, 0);
+                it.t_rem.lo = __shfl_sync(kAll, it.t_rem.lo, 0);
+                warp_item<kSampler>(P, S, SP, ctl, sm, net, it, step, k0, k1, stats, stats.cand,
+                                    true);
+                if (lane == 0) ++done;
+                idle = 0;
+                continue;
+            }
+        }
+        // ---- 2. rows for the idle lanes: children first, then the medium plans.
+        // Lane 0 takes child indices with one atomic add into a pending range
+        // and hands a lane only an index whose row is reserved already (the
+        // rest stay pending; indices never reserved are void when the step
+        // ends); medium plans come the same way, an index past their count is
+        // dropped.
+        {
+            const unsigned int free_lanes = __ballot_sync(kAll, !active && !waiting);
+            if (free_lanes) {
+                const int want = __popc(free_lanes);
+                unsigned long long base_c = 0, base_i = 0;
+                int got_c = 0, got_i = 0;
+                if (lane == 0) {
+                    if (cascade) {
+                        const unsigned long long stored = stored_rows(P);
+                        if (pend_lo == pend_hi) {
+                            const unsigned long long ch =
+                                *reinterpret_cast<volatile unsigned long long*>(&ctl->child_head);
+                            if (ch < stored) {
+                                const unsigned long long k =
+                                    min((unsigned long long)want, stored - ch);
+                                pend_lo = atomicAdd(&ctl->child_head, k);
+                                pend_hi = pend_lo + k;
+                            }
+                        }
+                        if (pend_lo < pend_hi && pend_lo < stored) {
+                            got_c = (int)min((unsigned long long)want, min(pend_hi, stored) - pend_lo);
+                            base_c = pend_lo;
+                            pend_lo += (unsigned long long)got_c;
+                        }
+                    }
+                    if (got_c < want &&
+                        *reinterpret_cast<volatile unsigned int*>(&ctl->med_head) < cold_med) {
+                        const unsigned int k = (unsigned int)(want - got_c);
+                        const unsigned int b = atomicAdd(&ctl->med_head, k);
+                        base_i = b;
+                        got_i = b < cold_med ? (int)min(k, cold_med - b) : 0;
+                    }
+                }
+                got_c = __shfl_sync(kAll, got_c, 0);
+                got_i = __shfl_sync(kAll, got_i, 0);
+                if (got_c + got_i) {
+                    base_c = __shfl_sync(kAll, base_c, 0);
+                    base_i = __shfl_sync(kAll, base_i, 0);
+                    const int rank = __popc(free_lanes & ((1u << lane) - 1u));
+                    if (!active && !waiting && rank < got_c + got_i) {
+                        // a child's row index, or a medium plan's queue position
+                        child = rank < got_c;
+                        i = (long long)(child ? base_c + rank : base_i + (rank - got_c));
+                        waiting = true;
+                    }
+                }
+            }
+        }
+        // ---- 3. lanes holding a row: load and plan it once it is written
+        if (waiting) {
+            uint32_t s0 = 0;
+            if (!child) {   // a medium plan: its row, first sub-step and remaining time
+                const HotItem it = S.hot[S.hot_cap - 1 - i];
+                i = it.idx;
+                s0 = it.s;
+                t_rem = it.t_rem;
+            }
+            const uint8_t ty = *reinterpret_cast<volatile uint8_t*>(P.type + i);
+            if (!child || ty != kNotReady) {
+                if (child) {
+                    __threadfence();
+                    t_rem = S.t_rem[i];
+                }
+                waiting = false;
+                photon = ty == QED_PHOTON;
+                bool work = ty <= QED_PHOTON && process_enabled(SP, photon) && time_positive(t_rem);
+                if (work) {
+                    id = P.id[i];
+                    st = PState{P.px[i], P.py[i], P.pz[i]};
+                    fld[0][threadIdx.x] = P.Ex[i];
+                    fld[1][threadIdx.x] = P.Ey[i];
+                    fld[2][threadIdx.x] = P.Ez[i];
+                    fld[3][threadIdx.x] = P.Bx[i];
+                    fld[4][threadIdx.x] = P.By[i];
+                    fld[5][threadIdx.x] = P.Bz[i];
+                    s = s0;
+                    changed = removed = false;
+                    pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz,
+                                       fld[0][threadIdx.x], fld[1][threadIdx.x],
+                                       fld[2][threadIdx.x], fld[3][threadIdx.x],
+                                       fld[4][threadIdx.x], fld[5][threadIdx.x], t_rem, &chi, &eps);
+                    work = eps > 0.0f;
+                }
+                if (!work) {
+                    ++done;
+                } else {
+                    stats.max_N = max(stats.max_N, pl.N);
+                    if (pl.N >= SP.long_min || (!photon && sampler_bin_ok(SP, chi))) {
+                        push_long(S, ctl, cold_long, i, s, t_rem);   // the warp mode plans again
+                    } else {
+                        stats.plans++;
+                        stats.guard += pl.guard ? 1 : 0;
+                        if (pl.T == 0u) {   // no candidates: the plan passes without an event
+                            stats.substeps += pl.N;
+                            ++done;
+                        } else {
+                            active = true;
+                            k_done = 0;
+                        }
+                    }
+                }
+            }
+        }
+        // ---- 4. nothing to draw: wait for work, or finish
+        if (!__any_sync(kAll, active)) {
+            // lanes waiting for a row still being written hold the warp
+            const bool hold = __any_sync(kAll, waiting);
+            bool finish = false;
+            if (!hold) {
+                // add this warp's finished rows, then test for the end of the step
+                const unsigned long long sum = warp_sum(done);
+                done = 0;
+                if (lane == 0) {
+                    if (sum) atomicAdd(&ctl->finished, sum);
+                    // units to complete: the thread pass's queue, and every child
+                    // reserved so far when children are stepped within the step
+                    const unsigned long long c1 = units0 + (cascade ? stored_rows(P) - n0 : 0ull);
+                    const unsigned long long f =
+                        *reinterpret_cast<volatile unsigned long long*>(&ctl->finished);
+                    const unsigned long long c2 = units0 + (cascade ? stored_rows(P) - n0 : 0ull);
+                    finish = f == c1 && c1 == c2;
+                }
+                finish = __shfl_sync(kAll, finish ? 1 : 0, 0) != 0;
+            }
+            if (finish) break;
+            if (++idle > kIdleLimit) {
+                timed_out = true;
+                break;
+            }
+            __nanosleep(256);
+            continue;
+        }
+        idle = 0;
+        // ---- 5. one round of warp-shared draws for the active lanes
+        const uint32_t n_win = active ? min(kWindow, pl.N - k_done) : 0u;
+        const uint32_t s_end = s + n_win;
+        warp_draw_round(sm, facc, active, s, s_end, pl.T, pl.b, pl.c_h, id, photon, step, k0, k1,
+                        stats.cand);
+        if (active) {
+            const uint32_t s_ev = facc[lane];
+            bool fin = false;
+            if (s_ev == kNoEvent) {
+                stats.substeps += n_win;
+                s = s_end;
+                k_done += n_win;
+                fin = k_done == pl.N;   // the plan ran out without an event
+            } else {
+                const uint32_t k = k_done + (s_ev - s);
+                stats.substeps += s_ev - s + 1u;
+                const float x = draw_x(id, step, s_ev, k0, k1);
+                const ftime t_after = (k + 1u == pl.N) ? ftime{0.0f, 0.0f}
+                                                       : time_sub_mul(t_rem, k + 1u, pl.h);
+                removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
+                                      t_after, st, stats, true, false,
+                                      Fields{fld[0][threadIdx.x], fld[1][threadIdx.x],
+                                             fld[2][threadIdx.x], fld[3][threadIdx.x],
+                                             fld[4][threadIdx.x], fld[5][threadIdx.x]},
+                                      true);
+                changed = true;
+                s = s_ev + 1u;
+                t_rem = t_after;
+                fin = removed || !time_positive(t_rem);
+                if (!fin) {
+                    pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz,
+                                       fld[0][threadIdx.x], fld[1][threadIdx.x],
+                                       fld[2][threadIdx.x], fld[3][threadIdx.x],
+                                       fld[4][threadIdx.x], fld[5][threadIdx.x], t_rem, &chi,
+                                       &eps);
+                    k_done = 0;
+                    if (!(eps > 0.0f)) {
+                        fin = true;
+                    } else {
+                        stats.max_N = max(stats.max_N, pl.N);
+                        if (pl.N >= SP.long_min || (!photon && sampler_bin_ok(SP, chi))) {
+                            // continue in the warp mode; its state goes with the row
+                            P.px[i] = st.px;
+                            P.py[i] = st.py;
+                            P.pz[i] = st.pz;
+                            changed = false;
+                            push_long(S, ctl, cold_long, i, s, t_rem);
+                            active = false;
+                        } else {
+                            stats.plans++;
+                            stats.guard += pl.guard ? 1 : 0;
+                            if (pl.T == 0u) {
+                                stats.substeps += pl.N;
+                                s += pl.N;
+                                fin = true;
+                            }
+                        }
+                    }
+                }
+            }
+            if (fin) {
+                if (removed) {
+                    P.type[i] = QED_REMOVED;
+                } else if (changed) {
+                    P.px[i] = st.px;
+                    P.py[i] = st.py;
+                    P.pz[i] = st.pz;
+                }
+                active = false;
+                ++done;
+            }
+        }
+        __syncwarp();   // facc is reset by the next round
+    }
+    if (timed_out && lane == 0) atomicExch(&ctl->status, (int)QED_ERR_TIMEOUT);
+    const unsigned long long sum = warp_sum(done);
+    if (lane == 0 && sum) atomicAdd(&ctl->finished, sum);
+    flush_stats(stats, ctl);
+}
+
+// Before the persistent step (cascading): rows [n0, capacity) are free; mark
+// them not written, so that a lane taking a child row waits for its writer.
+
 // Start a step.  keep_sticky: inside a multi-step graph, a step that follows
 // a failed step does nothing (its range is empty and it keeps the status).
 __global__ void k_step_init(DevCtl* ctl, long long* count, long long capacity, int keep_sticky) {
@@ -975,8 +1366,11 @@ __global__ void k_step_init(DevCtl* ctl, long long* count, long long capacity, i
 
 // Close a cascade generation: the next generation is the rows appended during
 // this one.  In a graph, the WHILE node's condition is set here.
+// tail_rows > 0: a next generation of fewer rows goes to the tail pass
+// instead (ctl->tail set, the loop ends).
 __global__ void k_advance(DevCtl* ctl, long long* count, long long capacity, int more_allowed,
-                          int max_passes, cudaGraphConditionalHandle handle, int use_handle) {
+                          int max_passes, long long tail_rows, cudaGraphConditionalHandle handle,
+                          int use_handle) {
     long long n = *count;
     if (n > capacity) {
         n = capacity;
@@ -984,6 +1378,7 @@ __global__ void k_advance(DevCtl* ctl, long long* count, long long capacity, int
     }
     ctl->pass_begin = ctl->sticky ? 0 : ctl->pass_end;
     ctl->pass_end = ctl->sticky ? 0 : n;
+    ctl->hot_hw = max(ctl->hot_hw, ctl->hot_tail);
     ctl->hot_head = 0;
     ctl->hot_tail = 0;
     ctl->med_head = 0;
@@ -995,8 +1390,59 @@ __global__ void k_advance(DevCtl* ctl, long long* count, long long capacity, int
         more = 0;
         ctl->status = (int)QED_ERR_STATE;  // cascade deeper than the configured passes
     }
+    if (more && tail_rows > 0 && ctl->pass_end - ctl->pass_begin < tail_rows) {
+        more = 0;
+        ctl->tail = 1;
+    }
     ctl->more = more;
     if (use_handle) cudaGraphSetConditional(handle, (unsigned int)more);
+}
+
+// Start of the tail pass (or nothing, when the generations ran to the end):
+// rows from pass_end to the capacity are marked not written, so that a lane
+// taking a child row waits for its writer, and the long-plan queue entries
+// the generations wrote go back to "not written", so that a warp waiting for
+// an entry the persistent kernel pushes never reads an older one.  The thread
+// pass that follows runs over [pass_begin, pass_end) as one more generation.
+__global__ void k_tail_begin(DevParticles P, Scratch S, DevCtl* ctl) {
+    const bool on = ctl->tail != 0;
+    const long long n0 = ctl->pass_end;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0) {
+        ctl->skip = on ? 0 : 1;
+        ctl->n0 = n0;
+        ctl->child_head = (unsigned long long)n0;
+        ctl->finished = 0;
+        ctl->step_tail = 0;
+    }
+    if (!on) return;
+    for (long long r = n0 + t0; r < P.capacity; r += stride) P.type[r] = kNotReady;
+    const long long used = min((long long)ctl->hot_hw, S.hot_cap);
+    for (long long q = t0; q < used; q += stride) S.hot[q].idx = kNoItem;
+}
+
+// End of the step: after a tail pass the count is capped at the capacity
+// (children that did not fit were dropped and the status says so) and rows
+// past it go back to removed; in every step the long-plan queue entries used
+// go back to "not written".
+__global__ void k_tail_end(DevParticles P, Scratch S, DevCtl* ctl) {
+    const bool on = ctl->tail != 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long c = min(*P.count, P.capacity);
+    if (on) {
+        for (long long r = c + t0; r < P.capacity; r += stride) P.type[r] = QED_REMOVED;
+        if (t0 == 0) {
+            *P.count = c;
+            ctl->pass_begin = ctl->pass_end;
+            ctl->pass_end = ctl->sticky ? 0 : c;   // the count the step reports
+            ctl->passes += 1;
+        }
+    }
+    const long long used =
+        min(max((long long)ctl->hot_hw, (long long)ctl->hot_tail + ctl->step_tail), S.hot_cap);
+    for (long long q = t0; q < used; q += stride) S.hot[q].idx = kNoItem;
 }
 
 // Write the statistics of the step into `rec` (if not null); an error becomes
@@ -1212,6 +1658,8 @@ struct qed_ctx {
     int cold_blocks_max, hot_blocks_max;
     int net_blocks;           // grid of the hot pass in sampler mode
     uint32_t hot_min, long_min;
+    long long tail_rows;        // cascade generations below this size go to the tail pass
+    int step_blocks, step_net_blocks;   // resident blocks of the tail pass's kernel
     // compaction
     Mirror mirror;
     long long mirror_cap;
@@ -1238,7 +1686,7 @@ struct qed_ctx {
     // when its key (store, scratch, parameters, grids) changes
     cudaGraph_t step_graph;
     cudaGraphExec_t step_exec;
-    uint64_t step_key[48];
+    uint64_t step_key[64];
     int step_key_n;
     uint32_t* d_step_idx;
     qed_step_stats* d_records;
@@ -1329,7 +1777,13 @@ qed_status ensure_scratch(qed_ctx* ctx, long long cap) {
     ctx->d_hot = nullptr;
     ctx->scratch_cap = 0;
     QED_CUDA(ctx, cudaMalloc(&ctx->d_trem, sizeof(ftime) * cap));
-    QED_CUDA(ctx, cudaMalloc(&ctx->d_hot, sizeof(HotItem) * cap));
+    // queue: long plans from the front, medium plans from the back.  Every
+    // entry belongs to a row and a row has at most two entries per generation
+    // (in the tail pass a medium plan may come back as a long plan), so 2 cap
+    // entries never let the ends meet.  Long-plan entries start "not written"
+    // (row index all ones) and each step resets the ones it used.
+    QED_CUDA(ctx, cudaMalloc(&ctx->d_hot, sizeof(HotItem) * 2 * cap));
+    QED_CUDA(ctx, cudaMemset(ctx->d_hot, 0xFF, sizeof(HotItem) * 2 * cap));
     ctx->scratch_cap = cap;
     return QED_OK;
 }
@@ -1412,7 +1866,7 @@ Scratch make_scratch(const qed_ctx* ctx) {
     Scratch S;
     S.t_rem = ctx->d_trem;
     S.hot = ctx->d_hot;
-    S.hot_cap = ctx->scratch_cap;
+    S.hot_cap = 2 * ctx->scratch_cap;
     S.log = ctx->log;
     S.log_cap = ctx->log_cap;
     S.log_count = ctx->log_count;
@@ -1490,8 +1944,18 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<true>, kLaneThreads,
                                                       sizeof(SamplerSmem));
         ctx->net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
+        per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<false>, kLaneThreads, 0);
+        ctx->step_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
+        per_sm = 0;
+        cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SamplerSmem));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<true>, kLaneThreads,
+                                                      sizeof(SamplerSmem));
+        ctx->step_net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         ctx->hot_min = kHotMinDefault;
         ctx->long_min = kLongMinDefault;
+        ctx->tail_rows = kTailRowsDefault;
         st = cuda_check(ctx, cudaGetLastError(), "occupancy");
     }
     if (st != QED_OK) {
@@ -1641,7 +2105,7 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
         {
             LaunchScope ls(ctx, QED_KERNEL_CONTROL);
             k_advance<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, cascade ? 1 : 0,
-                                                ctx->cfg.max_passes, 0ull, 0);
+                                                ctx->cfg.max_passes, ctx->tail_rows, 0ull, 0);
         }
         QED_CUDA(ctx, cudaGetLastError());
         if (!cascade) break;
@@ -1650,6 +2114,28 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
         QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         if (!ctx->h_ctl->more) break;
     }
+    // the tail pass (its kernels do nothing when the generations ran to the end)
+    {
+        LaunchScope ls(ctx, QED_KERNEL_CONTROL);
+        k_tail_begin<<<ctx->sms * 8, 256, 0, ctx->stream>>>(D, S, ctx->d_ctl);
+    }
+    {
+        LaunchScope ls(ctx, QED_KERNEL_COLD);
+        k_cold<<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+    }
+    {
+        LaunchScope ls(ctx, QED_KERNEL_HOT);
+        if (SP.sampler)
+            k_step<true><<<ctx->step_net_blocks, kLaneThreads, sizeof(SamplerSmem), ctx->stream>>>(
+                D, SP, S, ctx->d_ctl);
+        else
+            k_step<false><<<ctx->step_blocks, kLaneThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+    }
+    {
+        LaunchScope ls(ctx, QED_KERNEL_CONTROL);
+        k_tail_end<<<ctx->sms * 8, 256, 0, ctx->stream>>>(D, S, ctx->d_ctl);
+    }
+    QED_CUDA(ctx, cudaGetLastError());
     if (out) return qed_read_stats(ctx, out);
     return QED_OK;
 }
@@ -1737,6 +2223,43 @@ qed_status add_kernel(qed_ctx* ctx, cudaGraph_t g, cudaGraphNode_t* node, const 
                       "cudaGraphAddKernelNode");
 }
 
+// The tail pass after a step's generation loop (node `dep`): tail begin,
+// thread pass, persistent kernel, tail end (`last`).  Its kernels do nothing
+// when the generations ran to the end.
+qed_status add_tail_nodes(qed_ctx* ctx, cudaGraph_t g, cudaGraphNode_t dep, const DevParticles& Din,
+                          const StepParams& SPin, const Scratch& Sin, DevCtl* ctl_in,
+                          cudaGraphNode_t* last) {
+    DevParticles D = Din;
+    StepParams SP = SPin;
+    Scratch S = Sin;
+    DevCtl* ctl = ctl_in;
+    cudaGraphNode_t tb, tc, ts, te;
+    qed_status st;
+    {
+        void* a[] = {&D, &S, &ctl};
+        st = add_kernel(ctx, g, &tb, (const void*)k_tail_begin, dim3(ctx->sms * 8), dim3(256), a,
+                        &dep, 1);
+    }
+    if (st == QED_OK) {
+        void* a[] = {&D, &SP, &S, &ctl};
+        st = add_kernel(ctx, g, &tc, (const void*)k_cold, dim3(ctx->cold_blocks),
+                        dim3(kColdThreads), a, &tb, 1);
+    }
+    if (st == QED_OK) {
+        void* a[] = {&D, &SP, &S, &ctl};
+        st = add_kernel(ctx, g, &ts, SP.sampler ? (const void*)k_step<true> : (const void*)k_step<false>,
+                        dim3(SP.sampler ? ctx->step_net_blocks : ctx->step_blocks),
+                        dim3(kLaneThreads), a, &tc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
+    }
+    if (st == QED_OK) {
+        void* a[] = {&D, &S, &ctl};
+        st = add_kernel(ctx, g, &te, (const void*)k_tail_end, dim3(ctx->sms * 8), dim3(256), a,
+                        &ts, 1);
+    }
+    *last = te;
+    return st;
+}
+
 }  // namespace
 
 qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t first_step,
@@ -1767,6 +2290,7 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
     long long capacity = D.capacity;
     int more_allowed = cascade_enabled(ctx->cfg) ? 1 : 0;
     int max_passes = ctx->cfg.max_passes;
+    long long tail_rows = ctx->tail_rows;
     int keep_sticky = 1;
     float drain = ctx->cfg.drain_chi;
     double* hist = ctx->d_hist;
@@ -1823,14 +2347,17 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
                             a, &bc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
         }
         if (st == QED_OK) {
-            void* a[] = {&ctl, &count, &capacity, &more_allowed, &max_passes, &h, &use_handle};
+            void* a[] = {&ctl,        &count, &capacity, &more_allowed, &max_passes,
+                         &tail_rows, &h,     &use_handle};
             st = add_kernel(ctx, body, &ba, (const void*)k_advance, dim3(1), dim3(1), a, &bh, 1);
         }
+        cudaGraphNode_t tend;
+        if (st == QED_OK) st = add_tail_nodes(ctx, g, wnode, D, SP, S, ctl, &tend);
         // compaction (and optional photon drain) after the cascade
         if (st == QED_OK) {
             void* a[] = {&D, &SP, &drain, &hist, &block_live};
             st = add_kernel(ctx, g, &n1, (const void*)k_compact_count, dim3(nb),
-                            dim3(kCompactThreads), a, &wnode, 1);
+                            dim3(kCompactThreads), a, &tend, 1);
         }
         if (st == QED_OK) {
             void* a[] = {&block_live, &nb, &ctl, &count};
@@ -1901,9 +2428,9 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
     if (!ctx->d_step_idx) QED_CUDA(ctx, cudaMalloc(&ctx->d_step_idx, sizeof(uint32_t)));
     SPin.step = 0;
     SPin.step_base = ctx->d_step_idx;
-    uint64_t key[48];
+    uint64_t key[64];
     int nk = 0;
-    auto put = [&](uint64_t v) { if (nk < 48) key[nk++] = v; };
+    auto put = [&](uint64_t v) { if (nk < 64) key[nk++] = v; };
     auto putf = [&](float v) { uint32_t b; memcpy(&b, &v, 4); put(b); };
     auto putp = [&](const void* v) { put((uint64_t)(uintptr_t)v); };
     for (const void* q : {(const void*)Din.px, (const void*)Din.py, (const void*)Din.pz,
@@ -1924,6 +2451,7 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
     put((uint64_t)SPin.recoil); put((uint64_t)SPin.cascade);
     put((uint64_t)ctx->cold_blocks); put((uint64_t)ctx->hot_blocks); put((uint64_t)ctx->net_blocks);
     put((uint64_t)ctx->cfg.max_passes);
+    put((uint64_t)ctx->tail_rows); put((uint64_t)ctx->step_blocks); put((uint64_t)ctx->step_net_blocks);
     const bool same = ctx->step_exec && nk == ctx->step_key_n &&
                       memcmp(key, ctx->step_key, sizeof(uint64_t) * nk) == 0;
     if (!same) {
@@ -1941,7 +2469,8 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
         long long* count = D.count;
         long long capacity = D.capacity;
         int keep_sticky = 0, more_allowed = 1, max_passes = ctx->cfg.max_passes, use_handle = 1;
-        cudaGraphNode_t init, wnode, bc, bh, ba;
+        long long tail_rows = ctx->tail_rows;
+        cudaGraphNode_t init, wnode, bc, bh, ba, tend;
         qed_status st;
         {
             void* a[] = {&ctl, &count, &capacity, &keep_sticky};
@@ -1972,10 +2501,12 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
                                 dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks),
                                 dim3(kLaneThreads), a, &bc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
             if (st == QED_OK) {
-                void* b[] = {&ctl, &count, &capacity, &more_allowed, &max_passes, &h, &use_handle};
+                void* b[] = {&ctl,        &count, &capacity, &more_allowed, &max_passes,
+                             &tail_rows, &h,     &use_handle};
                 st = add_kernel(ctx, body, &ba, (const void*)k_advance, dim3(1), dim3(1), b, &bh, 1);
             }
         }
+        if (st == QED_OK) st = add_tail_nodes(ctx, g, wnode, D, SP, S, ctl, &tend);
         if (st == QED_OK)
             st = cuda_check(ctx, cudaGraphInstantiate(&ctx->step_exec, g, 0), "cudaGraphInstantiate");
         if (st != QED_OK) {
@@ -2333,6 +2864,12 @@ qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, uint32_t long_min,
     return QED_OK;
 }
 
+qed_status qed_set_tail(qed_ctx* ctx, int64_t tail_rows) {
+    if (!ctx || tail_rows < 0) return QED_ERR_ARG;
+    ctx->tail_rows = tail_rows;
+    return QED_OK;
+}
+
 qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
                         const char* out_json) {
     if (!ctx) return QED_ERR_ARG;
@@ -2349,11 +2886,12 @@ qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_inde
     QED_CUDA(ctx, cudaEventCreate(&e0));
     QED_CUDA(ctx, cudaEventCreate(&e1));
     const int cold_max = ctx->cold_blocks_max / ctx->sms, hot_max = ctx->hot_blocks_max / ctx->sms;
-    struct Setting { uint32_t hot_min, long_min; int cold, hot; };
+    struct Setting { uint32_t hot_min, long_min; int cold, hot; long long tail; };
     struct Trial { Setting c; float ms; };
     std::vector<Trial> trials;
     auto run = [&](const Setting& c, float* ms) -> qed_status {
         qed_set_launch(ctx, c.hot_min, c.long_min, c.cold, c.hot);
+        qed_set_tail(ctx, c.tail);
         qed_status s2 = copy_store(ctx, p, n, false);
         if (s2 != QED_OK) return s2;
         cudaEventRecord(e0, ctx->stream);
@@ -2367,7 +2905,7 @@ qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_inde
         return QED_OK;
     };
     float ms = 0.0f, best = 0.0f;
-    Setting b{ctx->hot_min, ctx->long_min, cold_max, hot_max};
+    Setting b{ctx->hot_min, ctx->long_min, cold_max, hot_max, ctx->tail_rows};
     st = run(b, &best);   // warm-up and reference
     if (st == QED_OK) st = run(b, &best);
     // coordinate search: one setting at a time, keeping the best so far
@@ -2389,7 +2927,10 @@ qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_inde
     sweep([](Setting& c, uint32_t v) { c.long_min = v; }, long_mins);
     sweep([](Setting& c, int v) { c.cold = v; }, colds);
     sweep([](Setting& c, int v) { c.hot = v; }, hots);
+    const long long tails[] = {0, 1ll << 14, 1ll << 16, 1ll << 18, 1ll << 20, 1ll << 22};
+    sweep([](Setting& c, long long v) { c.tail = v; }, tails);
     qed_set_launch(ctx, b.hot_min, b.long_min, b.cold, b.hot);
+    qed_set_tail(ctx, b.tail);
     const qed_status st_restore = copy_store(ctx, p, n, false);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2399,13 +2940,13 @@ qed_status qed_autotune(qed_ctx* ctx, const qed_particles* p, uint64_t step_inde
         FILE* f = fopen(out_json, "w");
         if (!f) return set_err(ctx, QED_ERR_ARG, "qed_autotune: cannot write the JSON file");
         fprintf(f, "{\"hot_min\": %u, \"long_min\": %u, \"cold_blocks_per_sm\": %d, "
-                   "\"hot_blocks_per_sm\": %d, \"ms\": %.4f, \"trials\": [",
-                b.hot_min, b.long_min, b.cold, b.hot, best);
+                   "\"hot_blocks_per_sm\": %d, \"tail_rows\": %lld, \"ms\": %.4f, \"trials\": [",
+                b.hot_min, b.long_min, b.cold, b.hot, b.tail, best);
         for (size_t k = 0; k < trials.size(); ++k)
             fprintf(f, "%s{\"hot_min\": %u, \"long_min\": %u, \"cold\": %d, \"hot\": %d, "
-                       "\"ms\": %.4f}",
+                       "\"tail_rows\": %lld, \"ms\": %.4f}",
                     k ? ", " : "", trials[k].c.hot_min, trials[k].c.long_min, trials[k].c.cold,
-                    trials[k].c.hot, trials[k].ms);
+                    trials[k].c.hot, trials[k].c.tail, trials[k].ms);
         fprintf(f, "]}\n");
         fclose(f);
     }
@@ -2468,17 +3009,17 @@ constexpr size_t kNoAllocCtlBytes = 256;
 constexpr size_t kNoAllocTremOffset = kNoAllocCtlBytes;
 constexpr size_t kNoAllocHotOffset =
     kNoAllocTremOffset + sizeof(ftime) * (size_t)QED_NOALLOC_MAX_ROWS;
-constexpr size_t kNoAllocBytes = kNoAllocHotOffset + sizeof(HotItem) * (size_t)QED_NOALLOC_MAX_ROWS;
+constexpr size_t kNoAllocBytes =
+    kNoAllocHotOffset + sizeof(HotItem) * 2 * (size_t)QED_NOALLOC_MAX_ROWS;
 static_assert(sizeof(DevCtl) <= kNoAllocCtlBytes, "control block does not fit");
 static_assert(kNoAllocHotOffset % 16 == 0, "queue alignment");
-static_assert(sizeof(DevCtl) <= kNoAllocCtlBytes, "control block fits its slot");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 struct NoAllocDevice {
     int ready;
     unsigned char* base;   // device address of g_noalloc_scratch on this device
-    int cold_blocks, hot_blocks;
+    int sms, cold_blocks, hot_blocks, step_blocks;
 };
 constexpr int kNoAllocMaxDevices = 64;
 NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
@@ -2491,17 +3032,26 @@ qed_status noalloc_setup(int dev, NoAllocDevice* out) {
         void* ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
             return QED_ERR_CUDA;
-        int sms = 0, per_cold = 0, per_hot = 0;
+        int sms = 0, per_cold = 0, per_hot = 0, per_step = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return QED_ERR_CUDA;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_cold, k_cold, kColdThreads, 0) !=
                 cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot_lanes<false>, kLaneThreads, 0) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_step, k_step<false>, kLaneThreads, 0) !=
                 cudaSuccess)
             return QED_ERR_CUDA;
+        // long-plan queue entries start "not written"; each step resets the ones it used
+        if (cudaMemset(static_cast<unsigned char*>(ptr) + kNoAllocHotOffset, 0xFF,
+                       sizeof(HotItem) * 2 * (size_t)QED_NOALLOC_MAX_ROWS) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess)
+            return QED_ERR_CUDA;
         d.base = static_cast<unsigned char*>(ptr);
+        d.sms = sms;
         d.cold_blocks = sms * (per_cold > 0 ? per_cold : 1);
         d.hot_blocks = sms * (per_hot > 0 ? per_hot : 1);
+        d.step_blocks = sms * (per_step > 0 ? per_step : 1);
         d.ready = 1;
     }
     *out = d;
@@ -2532,7 +3082,7 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     Scratch S;
     S.t_rem = reinterpret_cast<ftime*>(nd.base + kNoAllocTremOffset);
     S.hot = reinterpret_cast<HotItem*>(nd.base + kNoAllocHotOffset);
-    S.hot_cap = QED_NOALLOC_MAX_ROWS;
+    S.hot_cap = 2 * (long long)QED_NOALLOC_MAX_ROWS;
     S.log = nullptr;
     S.log_cap = 0;
     S.log_count = nullptr;
@@ -2544,7 +3094,8 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     for (int pass = 0; pass < max_passes; ++pass) {
         k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
         k_hot_lanes<false><<<nd.hot_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
-        k_advance<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, cascade ? 1 : 0, max_passes, 0ull, 0);
+        k_advance<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, cascade ? 1 : 0, max_passes,
+                                  kTailRowsDefault, 0ull, 0);
         if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
         if (!cascade) break;
         if (cudaMemcpyAsync(&h, ctl, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -2552,6 +3103,12 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
             return QED_ERR_CUDA;
         if (!h.more) break;
     }
+    // the tail pass (its kernels do nothing when the generations ran to the end)
+    k_tail_begin<<<nd.sms * 8, 256, 0, s>>>(D, S, ctl);
+    k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
+    k_step<false><<<nd.step_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
+    k_tail_end<<<nd.sms * 8, 256, 0, s>>>(D, S, ctl);
+    if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
     if (!out) return QED_OK;
     if (cudaMemcpyAsync(&h, ctl, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

@@ -112,6 +112,8 @@ def lib():
         L.qed_sampler_save.restype = st
         L.qed_set_launch.argtypes = [vp, C.c_uint32, C.c_uint32, C.c_int, C.c_int]
         L.qed_set_launch.restype = st
+        L.qed_set_tail.argtypes = [vp, C.c_int64]
+        L.qed_set_tail.restype = st
         L.qed_autotune.argtypes = [vp, C.POINTER(Particles), u64, C.c_char_p]
         L.qed_autotune.restype = st
         L.qed_profile_enable.argtypes = [vp, C.c_int]
@@ -344,6 +346,10 @@ class Context:
     def set_launch(self, hot_min=0, long_min=0, cold_blocks_per_sm=0, hot_blocks_per_sm=0):
         self._check(lib().qed_set_launch(self._h, int(hot_min), int(long_min),
                                          int(cold_blocks_per_sm), int(hot_blocks_per_sm)))
+
+    def set_tail(self, tail_rows):
+        """Generations below tail_rows rows go to the tail pass (0: off)."""
+        self._check(lib().qed_set_tail(self._h, int(tail_rows)))
 
     def autotune(self, store, step, out_json=None):
         """Pick the fastest launch settings for `store` (left unchanged)."""

@@ -166,3 +166,56 @@ def test_host_loop_equals_graph_step():
             assert a[k] == b[k], (k, a[k], b[k])
     for k in ga:
         np.testing.assert_array_equal(ga[k], gb[k])
+
+
+@pytest.mark.parametrize("n,hot,profile", [(3000, 0.03, False), (30000, 0.01, True),
+                                           (200000, 0.01, False)])
+def test_tail_pass_equals_generations(n, hot, profile):
+    # generations below tail_rows are finished by one thread pass and one
+    # persistent kernel; every decision is the generation loop's
+    arr = I.clumped_mixed(n, 41, hot_fraction=hot)
+    cap = n * 40
+    out = []
+    for tail in (0, 1 << 30, 4096):
+        ctx = qed.Context(seed=23)
+        ctx.set_tail(tail)
+        ctx.profile(profile)
+        store = qed.ParticleStore.from_numpy(arr, capacity=cap)
+        sts = []
+        for k in range(2):
+            sts.append(ctx.event_step(store, 60 + k))
+            assert sts[-1]["status"] == 0
+            assert sts[-1]["count"] == store.n()
+        out.append((sts, _sorted(store.to_numpy())))
+    (s0, g0) = out[0]
+    assert s0[0]["children"] > 0 and s0[0]["passes"] > 2
+    for sts, g in out[1:]:
+        for a, b in zip(s0, sts):
+            # (candidates also count draws past an event, which depend on the
+            # launch shape: not compared)
+            for k in ("substeps", "emissions", "pairs", "children", "plans", "max_N", "count"):
+                assert a[k] == b[k], (k, a[k], b[k])
+        for k in g0:
+            np.testing.assert_array_equal(g0[k], g[k])
+    # with the tail from the second generation on, a step has at most three passes
+    assert all(s["passes"] <= 3 for s in out[1][0])
+
+
+def test_tail_pass_in_multi_step_graph():
+    arr = I.clumped_mixed(20000, 43, hot_fraction=0.02)
+    cap = 20000 * 40
+    res = []
+    for tail in (0, 1 << 30):
+        ctx = qed.Context(seed=5)
+        ctx.set_tail(tail)
+        store = qed.ParticleStore.from_numpy(arr, capacity=cap)
+        ctx.graph_capture(store, 70, 3)
+        ctx.graph_launch()
+        res.append((ctx.graph_read_stats(), _sorted(store.to_numpy())))
+    (sa, ga), (sb, gb) = res
+    for a, b in zip(sa, sb):
+        assert a["status"] == 0 and b["status"] == 0
+        for k in ("substeps", "emissions", "pairs", "children", "plans", "count"):
+            assert a[k] == b[k], (k, a[k], b[k])
+    for k in ga:
+        np.testing.assert_array_equal(ga[k], gb[k])
