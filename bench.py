@@ -38,13 +38,14 @@ SEED_CASCADE = 20081046 + 4
 CASCADE_CELLS = 4096
 CASCADE_CAPACITY = 1 << 26
 CASCADE_DRAIN_CHI = 0.05
-# DRAM bytes (read + write) per launch of the hot pass on the 2^24 clumped
-# population, from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum over every launch of three profiled steps; see
-# profiles/k_hot_lanes_traffic_clumped_2p24.md), valid for the kernel sources
-# whose SHA-256 is given; any other source reports traffic as unknown.
-HOT_TRAFFIC = {"bytes_per_launch": 37.72e6,
-               "sources_sha256": "63f473d16c03a12fe0143fe1920caa851c3202874de542501973bb8ac4480d16"}
+# DRAM bytes (read + write) per launch of the hot pass (k_hot_lanes and the
+# tail pass's k_step) on the 2^24 clumped population, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum over every launch of three
+# profiled steps; see profiles/hot_pass_traffic_clumped_2p24.md), valid for the
+# kernel sources whose SHA-256 is given; any other source reports traffic as
+# unknown.
+HOT_TRAFFIC = {"bytes_per_launch": 64.39e6,
+               "sources_sha256": "761795185ba3fdc2aebe786f09e96eb954594332ca9c2409c670c506ef45b2ee"}
 
 METRIC = "particle-steps/sec (sub-stepped)"
 UNIT = "substeps/s"
@@ -228,6 +229,8 @@ def run_gb300(args):
     store = qed.ParticleStore(cap, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > L2
     ctx = qed.Context(seed=SEED_CLUMPED + rank, process_mask=3, cascade=True)
+    if getattr(args, "tail_rows", None) is not None:
+        ctx.set_tail(args.tail_rows)
     stream = torch.cuda.current_stream()
 
     def restore():
@@ -265,8 +268,10 @@ def run_gb300(args):
         barrier(pg)
         total_ms += e0.elapsed_time(e1)
         sub_total += st["substeps"]
-        # our kernels per graph step: step index, step init, three per generation
-        launches_timed += 2 + 3 * st["passes"]
+        # our kernels per graph step: step index, step init, three per loop
+        # generation, and the tail pass's four (launched whether or not it ran;
+        # when it ran it counts as one of the passes)
+        launches_timed += 2 + 3 * (st["passes"] - st["tail"]) + 4
         for key in agg:
             agg[key] = max(agg[key], st[key]) if key == "max_N" else agg[key] + st[key]
         if st["status"] != 0:
@@ -328,7 +333,7 @@ def run_gb300(args):
         achieved = per_launch / t_launch / 1e12
         traffic = (HOT_TRAFFIC["bytes_per_launch"]
                    if HOT_TRAFFIC["sources_sha256"] == kernel_sources_sha256() else None)
-        roof = {"kernel": "k_hot_lanes", "bound": "alu", "achieved": achieved, "peak": mul_peak,
+        roof = {"kernel": "k_hot_lanes + k_step (hot pass)", "bound": "alu", "achieved": achieved, "peak": mul_peak,
                 "unit": "T int32-mul/s", "frac": achieved / mul_peak, "traffic": traffic,
                 "peak_kind": "derived: 152 SMs x 64 IMAD/clk x 2070 MHz"}
 
@@ -616,6 +621,9 @@ def main():
     ap.add_argument("--no-sampler", action="store_true")
     ap.add_argument("--no-cascade", action="store_true")
     ap.add_argument("--cascade-steps", type=int, default=100)
+    ap.add_argument("--tail-rows", type=int, default=None,
+                    help="generations below this many rows go to the tail pass (0: off; "
+                         "default: the library's)")
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="population size (smaller values only for profiling runs)")
     ap.add_argument("--sweep-n", type=int, default=SWEEP_N,

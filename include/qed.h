@@ -99,8 +99,8 @@ typedef struct {
     int64_t required_capacity; /* rows needed when status == QED_ERR_CAPACITY   */
     int64_t count;             /* rows in use after the step                    */
     int32_t passes;            /* cascade generations processed                 */
-    int32_t reserved;
-    uint64_t substeps_warp;    /* of `substeps`, those run on the warp-per-particle path */
+    int32_t tail;              /* 1: the step's last generations ran as the tail pass */
+    uint64_t substeps_warp;    /* of `substeps`, those run by the hot pass and the tail pass's persistent kernel */
     uint64_t sampler_events;   /* emissions whose energy came from the learned sampler */
 } qed_step_stats;
 
@@ -294,7 +294,7 @@ qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, uint32_t long_min,
  * the generations stop: one thread pass over that generation, then one
  * persistent kernel takes its queue and every child appended after it as
  * they come, so that the step is not bound by the longest chain of each
- * small generation in turn.  0 turns it off; default 262144 rows.  No
+ * small generation in turn.  0 turns it off; default 131072 rows.  No
  * setting changes a result (the passes count counts the tail as one).
  * Errors: QED_ERR_ARG (ctx null, tail_rows < 0). */
 qed_status qed_set_tail(qed_ctx* ctx, int64_t tail_rows);

@@ -52,7 +52,7 @@ constexpr double kPiD = 3.14159265358979323846;
 // hot_min 32..128 and long_min 128..2048)
 constexpr uint32_t kHotMinDefault = 32;    // plans with N >= hot_min go to the hot pass
 constexpr uint32_t kLongMinDefault = 256;  // ... and with N >= long_min to its warp mode
-constexpr long long kTailRowsDefault = 1ll << 18;   // generations below this go to the tail pass
+constexpr long long kTailRowsDefault = 1ll << 17;   // generations below this go to the tail pass
 
 // Minimum resident blocks per SM requested from the register allocator:
 // 3 x 256 threads hold the thread and hot passes at 80 registers (24 warps
@@ -724,7 +724,6 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
     uint32_t s = it.s;
     ftime t_rem = it.t_rem;
     bool removed = false, changed = false;
-    const unsigned int sub0 = stats.substeps;
     while (time_positive(t_rem)) {
         float eps, chi;
         const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
@@ -813,7 +812,6 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
         if (!event) t_rem = ftime{0.0f, 0.0f};
     }
     if (lane == 0) {
-        stats.warp_substeps += stats.substeps - sub0;
         if (removed) P.type[i] = QED_REMOVED;
         else if (changed) {
             P.px[i] = st.px;
@@ -1340,6 +1338,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
     if (timed_out && lane == 0) atomicExch(&ctl->status, (int)QED_ERR_TIMEOUT);
     const unsigned long long sum = warp_sum(done);
     if (lane == 0 && sum) atomicAdd(&ctl->finished, sum);
+    stats.warp_substeps = stats.substeps;   // every sub-step of this kernel is a hot-pass one
     flush_stats(stats, ctl);
 }
 
@@ -1465,7 +1464,7 @@ __global__ void k_step_close(DevCtl* ctl, const long long* count, qed_step_stats
         r.required_capacity = c.required;
         r.count = *count;
         r.passes = c.passes;
-        r.reserved = 0;
+        r.tail = c.tail;
         r.substeps_warp = c.substeps_warp;
         r.sampler_events = c.sampler_events;
         *rec = r;
@@ -1886,7 +1885,7 @@ void fill_stats(const DevCtl& c, qed_step_stats* out, long long count) {
     out->required_capacity = c.required;
     out->count = count;
     out->passes = c.passes;
-    out->reserved = 0;
+    out->tail = c.tail;
     out->substeps_warp = c.substeps_warp;
     out->sampler_events = c.sampler_events;
 }

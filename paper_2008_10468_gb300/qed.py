@@ -48,7 +48,7 @@ class StepStats(C.Structure):
                 ("children", C.c_uint64), ("guard_hits", C.c_uint64), ("plans", C.c_uint64),
                 ("candidates", C.c_uint64), ("max_N", C.c_uint32), ("status", C.c_int32),
                 ("required_capacity", C.c_int64), ("count", C.c_int64), ("passes", C.c_int32),
-                ("reserved", C.c_int32), ("substeps_warp", C.c_uint64),
+                ("tail", C.c_int32), ("substeps_warp", C.c_uint64),
                 ("sampler_events", C.c_uint64)]
 
 
@@ -135,7 +135,7 @@ def _ptr(t):
 
 
 def stats_dict(s):
-    return {k: int(getattr(s, k)) for k, _ in StepStats._fields_ if k != "reserved"}
+    return {k: int(getattr(s, k)) for k, _ in StepStats._fields_}
 
 
 class ParticleStore:

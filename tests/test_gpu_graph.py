@@ -189,6 +189,7 @@ def test_tail_pass_equals_generations(n, hot, profile):
         out.append((sts, _sorted(store.to_numpy())))
     (s0, g0) = out[0]
     assert s0[0]["children"] > 0 and s0[0]["passes"] > 2
+    assert all(s["tail"] == 0 for s in s0) and all(s["tail"] == 1 for s in out[1][0])
     for sts, g in out[1:]:
         for a, b in zip(s0, sts):
             # (candidates also count draws past an event, which depend on the
