@@ -1010,10 +1010,13 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
 // unit known so far (the children: the store count, capped at the capacity,
 // less n0) is complete.  Warps add their completed units to the control block
 // when they run out of work, so the count is exact whenever the test can
-// succeed.  Every wait is bounded: past kIdleLimit polls the kernel records
-// QED_ERR_TIMEOUT and returns.
+// succeed.  Idle warps back off (256 ns doubling to 4 us), so that their
+// polls of the control words do not slow the atomics of the busy ones.  Every
+// wait is bounded: past 1 s idle (kIdleNs), or kIdleLimit polls for a queue
+// entry, the kernel records QED_ERR_TIMEOUT and returns.
 // ---------------------------------------------------------------------------
 constexpr unsigned int kIdleLimit = 1u << 22;    // polls of ~0.25 us: about 1 s
+constexpr unsigned long long kIdleNs = 1000000000ull;   // idle time before giving up: 1 s
 
 __device__ __forceinline__ unsigned long long stored_rows(const DevParticles& P) {
     const long long c = *reinterpret_cast<volatile long long*>(P.count);
@@ -1070,6 +1073,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
     pl.b = pl.c_h = 0.0f;
     float chi = 0.0f, eps = 0.0f;
     unsigned int idle = 0;
+    unsigned long long idle_ns = 0;
     unsigned int ticket = kNoItem;   // lane 0: long-queue entry taken, not yet pushed
     unsigned long long pend_lo = 0, pend_hi = 0;   // lane 0: child indices taken, not handed out
     bool timed_out = false;
@@ -1119,6 +1123,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
                                     true);
                 if (lane == 0) ++done;
                 idle = 0;
+                idle_ns = 0;
                 continue;
             }
         }
@@ -1253,14 +1258,20 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
                 finish = __shfl_sync(kAll, finish ? 1 : 0, 0) != 0;
             }
             if (finish) break;
-            if (++idle > kIdleLimit) {
+            // idle: back off from 256 ns to 4 us (64 ns while a row is being
+            // written); the wait is bounded by the time spent idle
+            const unsigned int nap = hold ? 64u : 256u << min(idle, 4u);
+            ++idle;
+            idle_ns += nap;
+            if (idle_ns > kIdleNs) {
                 timed_out = true;
                 break;
             }
-            __nanosleep(256);
+            __nanosleep(nap);
             continue;
         }
         idle = 0;
+        idle_ns = 0;
         // ---- 5. one round of warp-shared draws for the active lanes
         const uint32_t n_win = active ? min(kWindow, pl.N - k_done) : 0u;
         const uint32_t s_end = s + n_win;

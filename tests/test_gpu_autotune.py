@@ -42,6 +42,8 @@ def test_autotune_restores_store_and_writes_record(tmp_path):
     assert rec["hot_min"] in (16, 32, 64, 128, 256)
     assert rec["long_min"] in (128, 256, 512, 1024, 2048, 1 << 30)
     assert rec["cold_blocks_per_sm"] >= 1 and rec["hot_blocks_per_sm"] >= 1
+    assert rec["tail_rows"] in (0, 1 << 14, 1 << 16, 1 << 17, 1 << 18, 1 << 20, 1 << 22)
+    assert any(t["tail_rows"] == 0 for t in rec["trials"])
     assert len(rec["trials"]) >= 6 and all(t["ms"] > 0 for t in rec["trials"])
 
 

@@ -8,6 +8,7 @@ import pytest
 
 import oracle as O
 from oracle import mlp
+from paper_2008_10468_gb300 import inputs as I
 from tests import refs
 
 pytestmark = pytest.mark.gpu
@@ -159,3 +160,29 @@ def test_sampler_events_follow_the_spectrum(trained):
     assert abs(st["emissions"] - pst["emissions"]) < 5 * math.sqrt(2 * W_dt * M)
     px_ = np.cbrt(pev["delta"].astype(np.float64))
     assert stats.ks_2samp(xs, px_).pvalue > 0.01
+
+
+def test_sampler_cascade_tail_pass_equals_generations(trained):
+    # with the network on, the tail pass (persistent kernel) takes the same
+    # decisions as the generation loop: the sampler's particles go to a warp in
+    # both, and the network sees the same uniforms
+    ctx, _ = trained
+    arr = I.clumped_mixed(40000, 91, hot_fraction=0.02)
+    out = []
+    for tail in (0, 1 << 30):
+        sctx = qed.Context(seed=19, sampler=True, sampler_max_err=1e-3)
+        sctx.sampler_load(ctx.sampler_save())
+        sctx.sampler_evaluate()
+        sctx.set_tail(tail)
+        store = qed.ParticleStore.from_numpy(arr, capacity=40000 * 40)
+        st = sctx.event_step(store, 5)
+        assert st["status"] == 0 and st["tail"] == (1 if tail else 0)
+        g = store.to_numpy()
+        o = np.argsort(g["id"], kind="stable")
+        out.append((st, {k: v[o] for k, v in g.items()}))
+    (a, ga), (b, gb) = out
+    assert a["sampler_events"] > 0
+    for k in ("substeps", "emissions", "pairs", "children", "sampler_events", "count"):
+        assert a[k] == b[k], (k, a[k], b[k])
+    for k in ga:
+        np.testing.assert_array_equal(ga[k], gb[k])
