@@ -44,8 +44,8 @@ CASCADE_DRAIN_CHI = 0.05
 # profiled steps; see profiles/hot_pass_traffic_clumped_2p24.md), valid for the
 # kernel sources whose SHA-256 is given; any other source reports traffic as
 # unknown.
-HOT_TRAFFIC = {"bytes_per_launch": 64.39e6,
-               "sources_sha256": "761795185ba3fdc2aebe786f09e96eb954594332ca9c2409c670c506ef45b2ee"}
+HOT_TRAFFIC = {"bytes_per_launch": 64.32e6,
+               "sources_sha256": "c8af8ac65a26537e8962e09a1edb2a2ad231fe0c9c1eb1fa15970e888816577b"}
 
 METRIC = "particle-steps/sec (sub-stepped)"
 UNIT = "substeps/s"
