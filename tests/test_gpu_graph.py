@@ -220,3 +220,30 @@ def test_tail_pass_in_multi_step_graph():
             assert a[k] == b[k], (k, a[k], b[k])
     for k in ga:
         np.testing.assert_array_equal(ga[k], gb[k])
+
+
+@pytest.mark.parametrize("tail", [0, 1 << 30])
+def test_capacity_overflow_in_the_cascade(tail):
+    # children that do not fit end the step with QED_ERR_CAPACITY and the rows
+    # needed.  With room for 80% of the children the overflow comes after the
+    # first generation, i.e. inside the tail pass when it is on: there the rows
+    # published as removed by a failed reservation are completed like any
+    # other, so the step ends (no timeout)
+    n = 4000
+    arr = I.clumped_mixed(n, 51, hot_fraction=0.05)
+    ctx = qed.Context(seed=3)
+    ctx.set_tail(tail)
+    full = qed.ParticleStore.from_numpy(arr, capacity=n * 60)
+    st_full = ctx.event_step(full, 9)
+    assert st_full["status"] == 0
+    total = st_full["count"]
+    cap = n + int(0.8 * (total - n))
+    ctx = qed.Context(seed=3)
+    ctx.set_tail(tail)
+    store = qed.ParticleStore.from_numpy(arr, capacity=cap)
+    st = ctx.event_step(store, 9)
+    assert st["status"] == qed.QED_ERR_CAPACITY
+    assert st["required_capacity"] > cap
+    assert store.n() == cap and st["count"] == cap
+    if tail:
+        assert st["tail"] == 1
