@@ -316,7 +316,7 @@ enum {
     QED_KERNEL_GENERATE = 1,   /* synchrotron functions, in-kernel arguments   */
     QED_KERNEL_PLAN = 2,       /* planner                                      */
     QED_KERNEL_COLD = 3,       /* event step: thread-per-particle pass         */
-    QED_KERNEL_HOT = 4,        /* event step: warp-per-particle queue pass     */
+    QED_KERNEL_HOT = 4,        /* event step: queue pass and tail pass         */
     QED_KERNEL_CONTROL = 5,    /* event step: per-step and per-pass bookkeeping */
     QED_KERNEL_KINDS = 8
 };
