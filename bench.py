@@ -511,13 +511,45 @@ def run_sampler(arr, pristine, store, cap, n, dev, args, restore, plain_value):
         sampled += st["sampler_events"]
         emis += st["emissions"]
     value = subs / (total_ms / 1e3)
+
+    # the same network, event-driven: the sub-steps to the next event are drawn
+    # at once (geometric), so the sampler's particles take no per-sub-step
+    # draws; its sub-steps are the same plans', decided by those draws
+    ectx = qed.Context(seed=SEED_CLUMPED, process_mask=3, cascade=True, sampler="event",
+                       sampler_max_err=1e-3)
+    ectx.sampler_load(ctx.sampler_save())
+    ectx.sampler_evaluate()
+    for w in range(2):
+        restore()
+        ectx.event_step(store, 4000 + w)
+    e_ms, e_subs, e_sampled, e_emis = 0.0, 0, 0, 0
+    for k in range(args.steps):
+        restore()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ectx.event_step(store, 2000 + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms += e0.elapsed_time(e1)
+        e_subs += st["substeps"]
+        e_sampled += st["sampler_events"]
+        e_emis += st["emissions"]
+    e_value = e_subs / (e_ms / 1e3)
     return {"train_samples": 1 << 26, "train_s": train_s, "final_mse": loss,
             "bins_usable": int(usable.sum()), "bins": int(len(err)),
             "max_cdf_err_usable": float(err[usable].max()) if usable.any() else None,
             "max_cdf_err_all": float(err.max()), "median_cdf_err": float(np.median(err)),
             "substeps_per_s": value, "ms_per_step": total_ms / args.steps,
             "emissions_from_sampler": sampled / max(emis, 1),
-            "speedup_vs_rejection": value / plain_value}
+            "speedup_vs_rejection": value / plain_value,
+            "event_driven": {"substeps_per_s": e_value, "ms_per_step": e_ms / args.steps,
+                             "emissions_from_sampler": e_sampled / max(e_emis, 1),
+                             "emissions_per_step": e_emis / args.steps,
+                             "emissions_per_step_sub_stepped": emis / args.steps,
+                             "speedup_vs_rejection": e_value / plain_value,
+                             "note": "sub-steps decided by geometric waiting-time draws"}}
 
 
 def run_e2e(ctx, arr, cap, dev, args):

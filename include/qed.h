@@ -62,7 +62,11 @@ typedef struct {
     float drain_chi;           /* compaction drains photons with chi below this
                                   into the photon spectrum (0: never)           */
     int32_t sampler_mode;      /* 1: learned inverse-CDF sampler for e+- emission
-                                  where usable (see qed_sampler_train)          */
+                                  where usable (see qed_sampler_train): each
+                                  sub-step is an event with the tabulated
+                                  probability; 2: the same, event-driven: the
+                                  sub-steps to the next event are drawn at once
+                                  (geometric), with no per-sub-step draws        */
     float sampler_max_err;     /* a chi bin is usable if its max CDF error <= this
                                   (1e-3)                                        */
 } qed_config;

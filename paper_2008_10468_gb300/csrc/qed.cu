@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
 // kSampler: an e+- in a usable bin of the sampler's chi range decides events
 // from the tabulated total probability c_h W(b) and takes the energy fraction
 // from the network at the event's uniform, evaluated by the warp (FP32).
-template <bool kSampler>
+template <int kSampler>
 __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& S,
                                           const StepParams& SP, DevCtl* ctl,
                                           const SharedTables& sm, SamplerSmem& net,
@@ -734,14 +734,50 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
             stats.guard += pl.guard ? 1 : 0;
             stats.max_N = max(stats.max_N, pl.N);
         }
-        const bool use_net = kSampler && !photon && sampler_bin_ok(SP, chi);
-        const float thr = use_net ? pl.c_h * sampler_wtot(net, chi) : 0.0f;
+        const bool use_net = kSampler != 0 && !photon && sampler_bin_ok(SP, chi);
+        const float thr = use_net ? fminf(pl.c_h * sampler_wtot(net, chi), 1.0f) : 0.0f;
         uint32_t kdone = 0;
         bool event = false;
         if (!use_net && pl.T == 0u) {   // no candidates: count without drawing
             if (lane == 0) stats.substeps += pl.N;
             s += pl.N;
             kdone = pl.N;
+        }
+        if (kSampler == 2 && use_net) {
+            // Event-driven: with chi and the plan fixed until the next event,
+            // each sub-step is an event with probability thr on its own, so
+            // the sub-steps before the next event are geometric, drawn by
+            // inversion: floor(ln u / ln(1 - thr)).  One Philox block per
+            // segment (counter: the segment's first sub-step, own key); its
+            // second word gives the network's uniform.
+            const uint32_t left = pl.N - kdone;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, s),
+                                          k0 ^ kWaitKeyLo, k1 ^ kWaitKeyHi);
+            const float wait = floorf(logf(u01(r.y)) / log1pf(-thr));
+            if (!(wait < (float)left)) {   // no event in the rest of the plan
+                if (lane == 0) stats.substeps += left;
+                s += left;
+                kdone = pl.N;
+            } else {
+                const uint32_t k = (uint32_t)wait;
+                const uint32_t s_ev = s + k;
+                const uint32_t k_ev = kdone + k;
+                const float x = mlp_infer_warp(net, log10f(chi) * 0.5f, mlp_input_u(u01(r.x)));
+                if (lane == 0) {
+                    stats.substeps += k + 1;
+                    stats.sampled++;
+                }
+                const ftime t_after = (k_ev + 1 == pl.N) ? ftime{0.0f, 0.0f}
+                                                         : time_sub_mul(t_rem, k_ev + 1, pl.h);
+                removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
+                                      t_after, st, stats, lane == 0, true,
+                                      Fields{Ex, Ey, Ez, Bx, By, Bz}, publish);
+                changed = true;
+                s = s_ev + 1;
+                t_rem = t_after;
+                event = true;
+                kdone = pl.N;   // skips the sub-step loop below
+            }
         }
         while (kdone < pl.N) {
             const uint32_t sb = s;
@@ -753,7 +789,7 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
             const bool v0 = s0 >= sb && s0 < lim;
             const bool v1 = s0 + 1 >= sb && s0 + 1 < lim;
             bool c0, c1, a0 = false, a1 = false;
-            if (use_net) {
+            if (kSampler == 1 && use_net) {
                 c0 = c1 = false;
                 a0 = v0 && u01(r.y) < thr;
                 a1 = v1 && u01(r.w) < thr;
@@ -790,7 +826,7 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
             const uint32_t s_ev = sa + (uint32_t)pos;
             const float xo = (pos & 1) ? u01(r.z) : u01(r.x);
             float x = __shfl_sync(0xffffffffu, xo, pos >> 1);
-            if (kSampler && use_net) {
+            if (kSampler == 1 && use_net) {
                 // inverse sampling: the event's uniform through the network
                 x = mlp_infer_warp(net, log10f(chi) * 0.5f, mlp_input_u(x));
                 if (lane == 0) stats.sampled++;
@@ -836,7 +872,7 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
 // are queued for the warp mode, which evaluates the network (warp_item).
 constexpr uint32_t kWindow = 64;
 
-template <bool kSampler>
+template <int kSampler>
 __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lanes(DevParticles P, StepParams SP,
                                                                  Scratch S, DevCtl* ctl) {
     const uint32_t step = step_index(SP);
@@ -1034,7 +1070,7 @@ __device__ __forceinline__ void push_long(const Scratch& S, DevCtl* ctl, unsigne
     *reinterpret_cast<volatile uint32_t*>(&e->idx) = (uint32_t)i;
 }
 
-template <bool kSampler>
+template <int kSampler>
 __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(DevParticles P, StepParams SP,
                                                             Scratch S, DevCtl* ctl) {
     const uint32_t step = step_index(SP);
@@ -1376,6 +1412,18 @@ __global__ void k_step_init(DevCtl* ctl, long long* count, long long capacity, i
 
 // Close a cascade generation: the next generation is the rows appended during
 // this one.  In a graph, the WHILE node's condition is set here.
+// The hot-pass and tail-pass kernels for a sampler mode (0: off, 1: per
+// sub-step, 2: event-driven), each its own instantiation so that a mode's
+// code carries no other mode's path.
+const void* hot_kernel(int mode) {
+    return mode == 2 ? (const void*)k_hot_lanes<2>
+                     : mode ? (const void*)k_hot_lanes<1> : (const void*)k_hot_lanes<0>;
+}
+const void* step_kernel(int mode) {
+    return mode == 2 ? (const void*)k_step<2>
+                     : mode ? (const void*)k_step<1> : (const void*)k_step<0>;
+}
+
 // tail_rows > 0: a next generation of fewer rows goes to the tail pass
 // instead (ctl->tail set, the loop ends).
 __global__ void k_advance(DevCtl* ctl, long long* count, long long capacity, int more_allowed,
@@ -1925,7 +1973,8 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
     if (!out || !cfg) return QED_ERR_ARG;
     *out = nullptr;
     if (!(cfg->p_max > 0.0f && cfg->p_max <= 1.0f) || !(cfg->dt_periods > 0.0) ||
-        !(cfg->lambda_m > 0.0) || !(cfg->pair_bound_coeff > 0.0f) || !(cfg->drain_chi >= 0.0f))
+        !(cfg->lambda_m > 0.0) || !(cfg->pair_bound_coeff > 0.0f) || !(cfg->drain_chi >= 0.0f) ||
+        cfg->sampler_mode < 0 || cfg->sampler_mode > 2)
         return QED_ERR_ARG;
     qed_ctx* ctx = new (std::nothrow) qed_ctx();
     if (!ctx) return QED_ERR_ARG;
@@ -1946,21 +1995,23 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cold, kColdThreads, 0);
         ctx->cold_blocks = ctx->cold_blocks_max = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<false>, kLaneThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<0>, kLaneThreads, 0);
         ctx->hot_blocks = ctx->hot_blocks_max = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
-        cudaFuncSetAttribute(k_hot_lanes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(SamplerSmem));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<true>, kLaneThreads,
+        for (int m = 1; m <= 2; ++m) {
+            cudaFuncSetAttribute(hot_kernel(m), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(SamplerSmem));
+            cudaFuncSetAttribute(step_kernel(m), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(SamplerSmem));
+        }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<1>, kLaneThreads,
                                                       sizeof(SamplerSmem));
         ctx->net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<false>, kLaneThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<0>, kLaneThreads, 0);
         ctx->step_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
-        cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(SamplerSmem));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<true>, kLaneThreads,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<1>, kLaneThreads,
                                                       sizeof(SamplerSmem));
         ctx->step_net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         ctx->hot_min = kHotMinDefault;
@@ -2105,12 +2156,15 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
         }
         {
             LaunchScope ls(ctx, QED_KERNEL_HOT);
-            if (SP.sampler)
-                k_hot_lanes<true><<<ctx->net_blocks, kLaneThreads, sizeof(SamplerSmem),
-                                    ctx->stream>>>(D, SP, S, ctx->d_ctl);
-            else
-                k_hot_lanes<false><<<ctx->hot_blocks, kLaneThreads, 0, ctx->stream>>>(D, SP, S,
-                                                                                     ctx->d_ctl);
+            DevParticles d = D;
+            StepParams sp = SP;
+            Scratch sc = S;
+            DevCtl* c = ctx->d_ctl;
+            void* a[] = {&d, &sp, &sc, &c};
+            QED_CUDA(ctx, cudaLaunchKernel(hot_kernel(SP.sampler),
+                                           dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks),
+                                           dim3(kLaneThreads), a,
+                                           SP.sampler ? sizeof(SamplerSmem) : 0, ctx->stream));
         }
         {
             LaunchScope ls(ctx, QED_KERNEL_CONTROL);
@@ -2135,11 +2189,15 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
     }
     {
         LaunchScope ls(ctx, QED_KERNEL_HOT);
-        if (SP.sampler)
-            k_step<true><<<ctx->step_net_blocks, kLaneThreads, sizeof(SamplerSmem), ctx->stream>>>(
-                D, SP, S, ctx->d_ctl);
-        else
-            k_step<false><<<ctx->step_blocks, kLaneThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+        DevParticles d = D;
+        StepParams sp = SP;
+        Scratch sc = S;
+        DevCtl* c = ctx->d_ctl;
+        void* a[] = {&d, &sp, &sc, &c};
+        QED_CUDA(ctx, cudaLaunchKernel(step_kernel(SP.sampler),
+                                       dim3(SP.sampler ? ctx->step_net_blocks : ctx->step_blocks),
+                                       dim3(kLaneThreads), a,
+                                       SP.sampler ? sizeof(SamplerSmem) : 0, ctx->stream));
     }
     {
         LaunchScope ls(ctx, QED_KERNEL_CONTROL);
@@ -2257,7 +2315,7 @@ qed_status add_tail_nodes(qed_ctx* ctx, cudaGraph_t g, cudaGraphNode_t dep, cons
     }
     if (st == QED_OK) {
         void* a[] = {&D, &SP, &S, &ctl};
-        st = add_kernel(ctx, g, &ts, SP.sampler ? (const void*)k_step<true> : (const void*)k_step<false>,
+        st = add_kernel(ctx, g, &ts, step_kernel(SP.sampler),
                         dim3(SP.sampler ? ctx->step_net_blocks : ctx->step_blocks),
                         dim3(kLaneThreads), a, &tc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
     }
@@ -2352,7 +2410,7 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         if (st == QED_OK) {
             void* a[] = {&D, &SP, &S, &ctl};
             st = add_kernel(ctx, body, &bh,
-                            SP.sampler ? (const void*)k_hot_lanes<true> : (const void*)k_hot_lanes<false>,
+                            hot_kernel(SP.sampler),
                             dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks), dim3(kLaneThreads),
                             a, &bc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
         }
@@ -2506,8 +2564,7 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
                             dim3(kColdThreads), a, nullptr, 0);
             if (st == QED_OK)
                 st = add_kernel(ctx, body, &bh,
-                                SP.sampler ? (const void*)k_hot_lanes<true>
-                                           : (const void*)k_hot_lanes<false>,
+                                hot_kernel(SP.sampler),
                                 dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks),
                                 dim3(kLaneThreads), a, &bc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
             if (st == QED_OK) {
@@ -2577,7 +2634,7 @@ qed_status sampler_params(qed_ctx* ctx, StepParams* SP) {
     if (!ctx->cfg.sampler_mode) return QED_OK;
     if (!ctx->net_ready || !ctx->d_wtot)
         return set_err(ctx, QED_ERR_STATE, "sampler_mode set but no sampler trained or loaded");
-    SP->sampler = 1;
+    SP->sampler = ctx->cfg.sampler_mode;   // 1: per sub-step, 2: event-driven
     SP->net_rows = kCdfRows;
     SP->net_bins = ctx->net_bins;
     SP->net_w = ctx->d_wbf;
@@ -3047,9 +3104,9 @@ qed_status noalloc_setup(int dev, NoAllocDevice* out) {
             return QED_ERR_CUDA;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_cold, k_cold, kColdThreads, 0) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot_lanes<false>, kLaneThreads, 0) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot_lanes<0>, kLaneThreads, 0) !=
                 cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_step, k_step<false>, kLaneThreads, 0) !=
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_step, k_step<0>, kLaneThreads, 0) !=
                 cudaSuccess)
             return QED_ERR_CUDA;
         // long-plan queue entries start "not written"; each step resets the ones it used
@@ -3103,7 +3160,7 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     DevCtl h;
     for (int pass = 0; pass < max_passes; ++pass) {
         k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
-        k_hot_lanes<false><<<nd.hot_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
+        k_hot_lanes<0><<<nd.hot_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
         k_advance<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, cascade ? 1 : 0, max_passes,
                                   kTailRowsDefault, 0ull, 0);
         if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
@@ -3116,7 +3173,7 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     // the tail pass (its kernels do nothing when the generations ran to the end)
     k_tail_begin<<<nd.sms * 8, 256, 0, s>>>(D, S, ctl);
     k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
-    k_step<false><<<nd.step_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
+    k_step<0><<<nd.step_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
     k_tail_end<<<nd.sms * 8, 256, 0, s>>>(D, S, ctl);
     if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
     if (!out) return QED_OK;

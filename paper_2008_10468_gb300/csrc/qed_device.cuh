@@ -43,6 +43,9 @@ __device__ __forceinline__ float u01(uint32_t r) {
 // the seed itself as key).
 constexpr uint32_t kChildKeyLo = 0xA511E9B3u;
 constexpr uint32_t kChildKeyHi = 0x63C1D2F5u;
+// ... and of the event-driven sampler's waiting-time stream.
+constexpr uint32_t kWaitKeyLo = 0x3C6EF372u;
+constexpr uint32_t kWaitKeyHi = 0xDAA66D2Bu;
 
 // ---------------------------------------------------------------------------
 // Float-float arithmetic (error-free transformations with FMA).  Explicit

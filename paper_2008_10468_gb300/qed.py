@@ -210,7 +210,8 @@ class Context:
         cfg.recoil = int(bool(recoil))
         cfg.max_passes = int(max_passes)
         cfg.drain_chi = float(drain_chi)
-        cfg.sampler_mode = int(bool(sampler))
+        # sampler: False, True (per sub-step) or "event" (event-driven)
+        cfg.sampler_mode = 2 if sampler == "event" else int(bool(sampler))
         cfg.sampler_max_err = float(sampler_max_err)
         if stream is None:
             stream = torch.cuda.current_stream()

@@ -186,3 +186,76 @@ def test_sampler_cascade_tail_pass_equals_generations(trained):
         assert a[k] == b[k], (k, a[k], b[k])
     for k in ga:
         np.testing.assert_array_equal(ga[k], gb[k])
+
+
+def _identical_electrons(M, gamma, chi_t):
+    pm = math.sqrt(gamma * gamma - 1.0)
+    E0 = np.float32(chi_t * O.schwinger_field() / (gamma + pm))
+    f32 = np.float32
+    arr = {"px": np.full(M, -pm, f32), "py": np.zeros(M, f32), "pz": np.zeros(M, f32),
+           "Ex": np.zeros(M, f32), "Ey": np.full(M, E0, f32), "Ez": np.zeros(M, f32),
+           "Bx": np.zeros(M, f32), "By": np.zeros(M, f32), "Bz": np.full(M, E0, f32),
+           "w": np.ones(M, f32), "id": np.arange(M, dtype=np.uint64),
+           "type": np.zeros(M, np.uint8)}
+    chi, g = O.chi((-pm, 0.0, 0.0), (0.0, float(E0), 0.0), (0.0, 0.0, float(E0)))
+    return arr, chi, g
+
+
+def test_event_driven_sampler_follows_rate_and_spectrum(trained):
+    # the event-driven form draws the sub-steps to the next event at once
+    # (geometric, the per-sub-step probability of the sub-stepped form): the
+    # same event rate W dt and the same spectrum, with no per-sub-step draws
+    ctx, err = trained
+    M = 4000
+    arr, chi, g = _identical_electrons(M, 3000.0, 3.0)
+    assert err[int((math.log10(chi) + 2) * 16)] <= 1e-3
+    ectx = qed.Context(seed=78, process_mask=1, cascade=False, recoil=False, sampler="event",
+                       sampler_max_err=1e-3)
+    ectx.sampler_load(ctx.sampler_save())
+    ectx.sampler_evaluate()
+    ectx.set_event_log(1 << 16)
+    store = qed.ParticleStore.from_numpy(arr, capacity=M * 20)
+    st = ectx.event_step(store, 4)
+    ev, _ = ectx.read_event_log()
+    assert st["status"] == 0
+    assert st["sampler_events"] == st["emissions"] and st["candidates"] == 0
+    b = 1.5 * chi
+    W_dt = SQRT3 / math.pi * O.rate_unit() * 0.1 / g * O.total_per_c(0, b)
+    assert abs(st["emissions"] / M - W_dt) < 4 * math.sqrt(W_dt / M)
+    # every sub-step of every particle is accounted for
+    sctx = qed.Context(seed=78, process_mask=1, cascade=False, recoil=False)
+    pst = sctx.event_step(qed.ParticleStore.from_numpy(arr, capacity=M * 20), 4)
+    assert st["substeps"] == pst["substeps"]
+    xs = np.cbrt(ev["delta"].astype(np.float64))
+    grid = np.linspace(0, 1, 161)
+    cdf = np.array([_oracle_cdf(b, g_) if g_ > 0 else 0.0 for g_ in grid])
+    from scipy import stats
+    assert stats.kstest(xs, lambda v: np.interp(v, grid, cdf)).pvalue > 0.01
+
+
+def test_event_driven_sampler_matches_sub_stepped_in_a_cascade(trained):
+    # with recoil and the in-step cascade the two forms take different draws,
+    # so the comparison is statistical: event counts within a few standard
+    # deviations and the emitted spectra from one distribution
+    ctx, _ = trained
+    arr = I.clumped_mixed(60000, 93, hot_fraction=0.02)
+    res = []
+    for mode in (True, "event"):
+        sctx = qed.Context(seed=29, sampler=mode, sampler_max_err=1e-3)
+        sctx.sampler_load(ctx.sampler_save())
+        sctx.sampler_evaluate()
+        sctx.set_event_log(1 << 20)
+        store = qed.ParticleStore.from_numpy(arr, capacity=60000 * 60)
+        st = sctx.event_step(store, 6)
+        ev, _ = sctx.read_event_log()
+        assert st["status"] == 0
+        res.append((st, ev))
+    (a, ea), (b, eb) = res
+    assert b["candidates"] <= a["candidates"] and b["sampler_events"] > 1000
+    for k in ("emissions", "pairs", "children"):
+        assert abs(a[k] - b[k]) < 6 * math.sqrt(a[k] + b[k]) + 10, (k, a[k], b[k])
+    assert abs(a["substeps"] / b["substeps"] - 1) < 0.03
+    from scipy import stats
+    da = ea["delta"][ea["kind"] == 1].astype(np.float64)
+    db = eb["delta"][eb["kind"] == 1].astype(np.float64)
+    assert stats.ks_2samp(np.cbrt(da), np.cbrt(db)).pvalue > 1e-3
