@@ -2667,13 +2667,13 @@ __device__ float mlp_infer_thread(const SamplerSmem& S, float v0, float v1) {
     float h1[kMlpW], h2[kMlpW];
     for (int n = 0; n < kMlpW; ++n)
         h1[n] = siluf_(fmaf(S.W1[2 * n], v0, fmaf(S.W1[2 * n + 1], v1, S.b1[n])));
-    for (int n = 0; n < kMlpW; ++n) h2[n] = siluf_(neuron_dot(S.W2 + n * kBfPad, h1, S.b2[n]));
+    for (int n = 0; n < kMlpW; ++n) h2[n] = siluf_(neuron_dot(S.W2 + n * kWPad, h1, S.b2[n]));
     float part[32];
     for (int l = 0; l < 32; ++l) {
         float o = 0.0f;
         for (int q = 0; q < 2; ++q) {
             const int n = l + 32 * q;
-            o = fmaf(S.w4[n], siluf_(neuron_dot(S.W3 + n * kBfPad, h2, S.b3[n])), o);
+            o = fmaf(S.w4[n], siluf_(neuron_dot(S.W3 + n * kWPad, h2, S.b3[n])), o);
         }
         part[l] = o;
     }

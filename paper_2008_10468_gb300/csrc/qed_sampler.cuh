@@ -429,12 +429,16 @@ __global__ void k_mlp_adam(const float* __restrict__ partial, int nparts, float*
 // ---------------------------------------------------------------------------
 // Inference with BF16 weights and FP32 accumulation.  Each output neuron is a
 // dot product taken in the order j = 0..63, the same in the warp-cooperative
-// and the per-thread forms, so both give the same result.
+// and the per-thread forms, so both give the same result.  The hidden-layer
+// weights are staged once as FP32 (the BF16 values, converted exactly), so
+// that the dot products take no conversion per weight.
 // ---------------------------------------------------------------------------
-constexpr int kBfPad = kMlpW + 2;   // BF16 row stride: 66 (33 words, odd)
+constexpr int kWPad = kMlpW + 4;   // FP32 row stride: 68 (16-byte rows; the
+                                   // 128-bit loads of 8 lanes hit distinct banks)
 
 struct SamplerSmem {
-    __nv_bfloat16 W2[kMlpW * kBfPad], W3[kMlpW * kBfPad];
+    __align__(16) float W2[kMlpW * kWPad];
+    __align__(16) float W3[kMlpW * kWPad];
     float W1[kMlpW * 2], b1[kMlpW], b2[kMlpW], b3[kMlpW], w4[kMlpW];
     float b4;
     float wtot[1024];                 // total probability per c along log10 chi
@@ -448,8 +452,8 @@ __device__ __forceinline__ void stage_sampler(SamplerSmem& S, const __nv_bfloat1
                                               unsigned long long bin_ok) {
     for (int i = threadIdx.x; i < kMlpW * kMlpW; i += blockDim.x) {
         const int n = i / kMlpW, j = i % kMlpW;
-        S.W2[n * kBfPad + j] = w[kMlpOffW2 + i];
-        S.W3[n * kBfPad + j] = w[kMlpOffW3 + i];
+        S.W2[n * kWPad + j] = __bfloat162float(w[kMlpOffW2 + i]);
+        S.W3[n * kWPad + j] = __bfloat162float(w[kMlpOffW3 + i]);
     }
     for (int i = threadIdx.x; i < 128; i += blockDim.x) S.W1[i] = __bfloat162float(w[kMlpOffW1 + i]);
     for (int i = threadIdx.x; i < kMlpW; i += blockDim.x) {
@@ -466,29 +470,34 @@ __device__ __forceinline__ void stage_sampler(SamplerSmem& S, const __nv_bfloat1
     }
 }
 
-__device__ __forceinline__ float neuron_dot(const __nv_bfloat16* __restrict__ row,
+__device__ __forceinline__ float neuron_dot(const float* __restrict__ row,
                                             const float* __restrict__ h, float acc) {
 #pragma unroll 8
-    for (int j = 0; j < kMlpW; ++j) acc = fmaf(__bfloat162float(row[j]), h[j], acc);
+    for (int j = 0; j < kMlpW; ++j) acc = fmaf(row[j], h[j], acc);
     return acc;
 }
 
-// Two neurons of one lane, sharing the activation loads: weights read as
-// BF16 pairs, products accumulated in FP32 in the order j = 0..63 (the order
-// of neuron_dot, so both forms give identical results).
-__device__ __forceinline__ void neuron_dot2(const __nv_bfloat16* __restrict__ row0,
-                                            const __nv_bfloat16* __restrict__ row1,
+// Two neurons of one lane, sharing the activation loads: weights and
+// activations read four at a time (128-bit loads), products accumulated in
+// FP32 in the order j = 0..63 (the order of neuron_dot, so both forms give
+// identical results).
+__device__ __forceinline__ void neuron_dot2(const float* __restrict__ row0,
+                                            const float* __restrict__ row1,
                                             const float* __restrict__ h, float& acc0,
                                             float& acc1) {
-#pragma unroll 8
-    for (int j = 0; j < kMlpW; j += 2) {
-        const float2 hv = *reinterpret_cast<const float2*>(h + j);
-        const __nv_bfloat162 w0 = *reinterpret_cast<const __nv_bfloat162*>(row0 + j);
-        const __nv_bfloat162 w1 = *reinterpret_cast<const __nv_bfloat162*>(row1 + j);
-        acc0 = fmaf(__low2float(w0), hv.x, acc0);
-        acc0 = fmaf(__high2float(w0), hv.y, acc0);
-        acc1 = fmaf(__low2float(w1), hv.x, acc1);
-        acc1 = fmaf(__high2float(w1), hv.y, acc1);
+#pragma unroll 4
+    for (int j = 0; j < kMlpW; j += 4) {
+        const float4 hv = *reinterpret_cast<const float4*>(h + j);
+        const float4 w0 = *reinterpret_cast<const float4*>(row0 + j);
+        const float4 w1 = *reinterpret_cast<const float4*>(row1 + j);
+        acc0 = fmaf(w0.x, hv.x, acc0);
+        acc0 = fmaf(w0.y, hv.y, acc0);
+        acc0 = fmaf(w0.z, hv.z, acc0);
+        acc0 = fmaf(w0.w, hv.w, acc0);
+        acc1 = fmaf(w1.x, hv.x, acc1);
+        acc1 = fmaf(w1.y, hv.y, acc1);
+        acc1 = fmaf(w1.z, hv.z, acc1);
+        acc1 = fmaf(w1.w, hv.w, acc1);
     }
 }
 
@@ -506,7 +515,7 @@ __device__ __forceinline__ float mlp_infer_warp(SamplerSmem& S, float v0, float 
     __syncwarp();
     a0 = S.b2[lane];
     a1 = S.b2[lane + 32];
-    neuron_dot2(S.W2 + lane * kBfPad, S.W2 + (lane + 32) * kBfPad, h, a0, a1);
+    neuron_dot2(S.W2 + lane * kWPad, S.W2 + (lane + 32) * kWPad, h, a0, a1);
     a0 = siluf_(a0);
     a1 = siluf_(a1);
     __syncwarp();
@@ -515,7 +524,7 @@ __device__ __forceinline__ float mlp_infer_warp(SamplerSmem& S, float v0, float 
     __syncwarp();
     a0 = S.b3[lane];
     a1 = S.b3[lane + 32];
-    neuron_dot2(S.W3 + lane * kBfPad, S.W3 + (lane + 32) * kBfPad, h, a0, a1);
+    neuron_dot2(S.W3 + lane * kWPad, S.W3 + (lane + 32) * kWPad, h, a0, a1);
     float o = fmaf(S.w4[lane], siluf_(a0), 0.0f);
     o = fmaf(S.w4[lane + 32], siluf_(a1), o);
 #pragma unroll
