@@ -44,8 +44,8 @@ CASCADE_DRAIN_CHI = 0.05
 # profiled steps; see profiles/hot_pass_traffic_clumped_2p24.md), valid for the
 # kernel sources whose SHA-256 is given; any other source reports traffic as
 # unknown.
-HOT_TRAFFIC = {"bytes_per_launch": 64.32e6,
-               "sources_sha256": "c8af8ac65a26537e8962e09a1edb2a2ad231fe0c9c1eb1fa15970e888816577b"}
+HOT_TRAFFIC = {"bytes_per_launch": 64.33e6,
+               "sources_sha256": "89491df6a620885aaff09a6b87b5b0b501b30452c967c6de891e550015acc2e9"}
 
 METRIC = "particle-steps/sec (sub-stepped)"
 UNIT = "substeps/s"
