@@ -385,6 +385,7 @@ def run_gb300(args):
 def run_sweep(ctx, dev, args, hbm_peak, peak_kind):
     import torch
     from paper_2008_10468_gb300 import inputs as I
+    from paper_2008_10468_gb300 import qed
     SWEEP_N = args.sweep_n
     y = torch.from_numpy(I.sweep_points(SWEEP_N, SEED_SWEEP)).to(dev)
     F1 = torch.empty_like(y)
@@ -416,10 +417,35 @@ def run_sweep(ctx, dev, args, hbm_peak, peak_kind):
     torch.cuda.synchronize()
     ms_gen = e0.elapsed_time(e1) / reps
     del y, F1, F2
+
+    # binary64 functions (the double-precision level of Table 1), same points:
+    # 8 B in + 16 B out per evaluation; the arithmetic is two degree-13
+    # polynomials (26 multiply-adds, 52 FP64 flops) plus exp for x >= 1/2, on
+    # the FP64 pipe (nominal 1.25 TFLOP/s dense on GB300; not in the measured
+    # peaks file)
+    y64 = torch.from_numpy(I.sweep_points(SWEEP_N, SEED_SWEEP).astype(np.float64)).to(dev)
+    G1 = torch.empty_like(y64)
+    G2 = torch.empty_like(y64)
+    for _ in range(2):
+        qed.synchrotron_F1F2_f64(y64, G1, G2, stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        qed.synchrotron_F1F2_f64(y64, G1, G2, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / reps
+    del y64, G1, G2
+    tf64 = 52.0 * SWEEP_N / (ms64 / 1e3) / 1e12
+    f64 = {"evals_per_s": SWEEP_N / (ms64 / 1e3), "ms": ms64,
+           "hbm_gbs": 24.0 * SWEEP_N / (ms64 / 1e3) / 1e9,
+           "fp64": {"achieved": tf64, "peak": 1.25, "unit": "TFLOP/s", "frac": tf64 / 1.25,
+                    "peak_kind": "nominal (GB300 dense FP64)", "flops_per_eval": 52}}
     return {"n": SWEEP_N, "evals_per_s": evals, "ms": ms,
             "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                     "peak_kind": peak_kind, "bytes_per_eval": 12},
-            "generate_evals_per_s": SWEEP_N / (ms_gen / 1e3), "generate_ms": ms_gen}
+            "generate_evals_per_s": SWEEP_N / (ms_gen / 1e3), "generate_ms": ms_gen,
+            "binary64": f64}
 
 
 def run_cascade(dev, args):

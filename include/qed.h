@@ -146,6 +146,17 @@ const char* qed_last_error(const qed_ctx* ctx);
  * QED_ERR_ARG (null ctx, null y with n > 0, n < 0). */
 qed_status qed_synchrotron_F1F2(qed_ctx* ctx, const float* y, float* F1, float* F2, int64_t n);
 
+/* The same functions in binary64, at the double-precision accuracy level of
+ * Sec. 3.2.1 (Table 1: 1e-14): relative error below 1e-15 for y in
+ * (0, 512), from per-half-octave polynomials of degree 13 (no difference of
+ * large terms is formed); 0 for y <= 0, y >= 512 (where F, G < 1e-220) and
+ * NaN.  y, F1, F2 are device arrays of n doubles; F1 or F2 may be NULL (not
+ * both when n > 0); n == 0 is a no-op.  No context: runs on `stream` (a
+ * cudaStream_t, NULL for the default stream), asynchronously.  Errors:
+ * QED_ERR_ARG (n < 0, null y or both outputs null with n > 0), QED_ERR_CUDA. */
+qed_status qed_synchrotron_F1F2_f64(const double* y, double* F1, double* F2, int64_t n,
+                                    void* stream);
+
 /* The same functions on arguments generated in the kernel:
  *   y_i = lo * (hi/lo)^u_i,  u_i the open-interval uniform of word (i mod 4)
  *   of Philox4x32-10 at counter (i/4 low, i/4 high, 0, 0), key `seed`.

@@ -8,7 +8,8 @@ What it computes (each function cites the passage it follows):
 
 * ``F1``/``F2``: the synchrotron functions F(x) = x int_x^inf K_{5/3} and
   G(x) = x K_{2/3}(x) of Sec. 3.2.1, by trapezoidal quadrature of the integral
-  representation of K_nu (C code in ``qed_oracle.c``).
+  representation of K_nu (C code in ``qed_oracle.c``); ``F1F2_double_reference``
+  adds G from mpmath's K_nu for the binary64 routine's 1e-14 level.
 * ``philox``/``draw``/``child_ids``: Philox4x32-10 (Salmon et al., SC'11) and
   the per-sub-step draw x, y of Algorithms 1 and 2.
 * ``chi``/``plan``: the quantum parameter of Sec. 2.2 and the sub-step count
@@ -137,6 +138,21 @@ def F1F2(x, threads=None):
     if threads is None:
         threads = min(os.cpu_count() or 1, max(1, x.size // 256))
     lib().orc_F1F2(x.size, _dp(x), _dp(f1), _dp(f2), int(threads))
+    return f1, f2
+
+
+def F1F2_double_reference(x):
+    """Reference values for the binary64 routine: F from the quadrature above
+    (FP64 rounding level, ~2e-15), G = x K_{2/3}(x) from mpmath's K_nu at 30
+    digits (the definition of Sec. 3.2.1).  Slow: for up to ~10^4 points."""
+    import mpmath as mp
+    x = np.asarray(x, dtype=np.float64).ravel()
+    f1, _ = F1F2(x)
+    f2 = np.empty_like(x)
+    with mp.workdps(30):
+        nu = mp.mpf(2) / 3
+        for i, v in enumerate(x):
+            f2[i] = float(mp.mpf(v) * mp.besselk(nu, mp.mpf(v))) if v > 0 else 0.0
     return f1, f2
 
 

@@ -77,6 +77,8 @@ def lib():
         L.qed_last_error.restype = C.c_char_p
         L.qed_synchrotron_F1F2.argtypes = [vp, vp, vp, vp, i64]
         L.qed_synchrotron_F1F2.restype = st
+        L.qed_synchrotron_F1F2_f64.argtypes = [vp, vp, vp, i64, vp]
+        L.qed_synchrotron_F1F2_f64.restype = st
         L.qed_synchrotron_generate.argtypes = [vp, u64, i64, C.c_float, C.c_float, vp, vp, vp, vp]
         L.qed_synchrotron_generate.restype = st
         L.qed_plan.argtypes = [vp, C.POINTER(Particles), i64, vp, vp]
@@ -136,6 +138,22 @@ def _ptr(t):
 
 def stats_dict(s):
     return {k: int(getattr(s, k)) for k, _ in StepStats._fields_}
+
+
+def synchrotron_F1F2_f64(y, F1=None, F2=None, stream=None):
+    """F and G in binary64 (float64 CUDA tensors) on `stream` (default: the
+    current torch stream); no context needed."""
+    import torch
+    if y.dtype != torch.float64 or any(t is not None and t.dtype != torch.float64
+                                       for t in (F1, F2)):
+        raise QEDError(QED_ERR_ARG, "float64 tensors expected")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = lib().qed_synchrotron_F1F2_f64(_ptr(y), _ptr(F1), _ptr(F2), int(y.numel()),
+                                        C.c_void_p(stream.cuda_stream))
+    if st != QED_OK:
+        raise QEDError(st, "qed_synchrotron_F1F2_f64 failed")
+    return F1, F2
 
 
 class ParticleStore:
