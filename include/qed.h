@@ -148,7 +148,7 @@ qed_status qed_synchrotron_F1F2(qed_ctx* ctx, const float* y, float* F1, float* 
 
 /* The same functions in binary64, at the double-precision accuracy level of
  * Sec. 3.2.1 (Table 1: 1e-14): relative error below 1e-15 for y in
- * (0, 512), from per-half-octave polynomials of degree 13 (no difference of
+ * (0, 512), from three polynomials of degree 11 per octave (no difference of
  * large terms is formed); 0 for y <= 0, y >= 512 (where F, G < 1e-220) and
  * NaN.  y, F1, F2 are device arrays of n doubles; F1 or F2 may be NULL (not
  * both when n > 0); n == 0 is a no-op.  No context: runs on `stream` (a

@@ -3,9 +3,11 @@
 //
 // F(x) = x int_x^inf K_{5/3}(t) dt and G(x) = x K_{2/3}(x) (Sec. 3.2.1) to
 // ~1e-15 relative error, the double-precision accuracy level of Table 1, from
-// the tables of fit_synchrotron64.py: per half-octave of x = m 2^k,
-//   F = 2^{k/3} exp(-lam_k x) sum_j c_j u^j,  u = 4 (m - centre) in [-1, 1)
-// (u exact), and below 2^KMIN the small-x series F = x^{1/3} sum_j a_j x^{2j/3}.
+// the tables of fit_synchrotron64.py: per piece [1, 1.25), [1.25, 1.5), [1.5, 2)
+// of m in x = m 2^k,
+//   F = 2^{k/3} exp(-lam_k x) sum_j c_j u^j,  u = (m - centre) / halfwidth in [-1, 1)
+// (u exact: dyadic centres and half-widths), and below 2^KMIN the small-x
+// series F = x^{1/3} sum_j a_j x^{2j/3}.
 // No difference of two large terms is formed, so the binary64 evaluation
 // keeps the fit's accuracy; arguments from 2^(KMAX+1) on give 0 (F, G < 1e-220).
 #include <cstdint>
@@ -16,7 +18,7 @@
 namespace {
 
 constexpr int kCoef64 = 2 * (QED_SYN64_DEG + 1);
-constexpr int kPieceStride64 = 48;   // pieces padded (NPIECE <= 48)
+constexpr int kPieceStride64 = 72;   // pieces padded (NPIECE <= 72)
 static_assert(QED_SYN64_NPIECE <= kPieceStride64, "piece stride");
 constexpr int kThreads64 = 256;
 
@@ -33,7 +35,7 @@ __device__ void stage_syn64(Syn64Table& T) {
         T.c[j][p] = p < QED_SYN64_NPIECE ? qed_syn64_table[p][j] : 0.0;
     }
     for (int p = threadIdx.x; p < kPieceStride64; p += blockDim.x) {
-        const int k = QED_SYN64_KMIN + p / 2;
+        const int k = QED_SYN64_KMIN + p / 3;
         T.scale[p] = exp2((double)k / 3.0);
     }
     for (int i = threadIdx.x; i < 2 * (QED_SYN64_SMALL_DEG + 1); i += blockDim.x)
@@ -64,9 +66,11 @@ __device__ __forceinline__ void syn64(const Syn64Table& T, double x, double& F, 
         return;
     }
     const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
-    const int h = m >= 1.5 ? 1 : 0;
-    const double u = 4.0 * (m - (1.25 + 0.5 * h));
-    const int p = 2 * (k - QED_SYN64_KMIN) + h;
+    const int part = m < 1.25 ? 0 : (m < 1.5 ? 1 : 2);
+    const double centre = part == 0 ? 1.125 : (part == 1 ? 1.375 : 1.75);
+    const double inv_half = part == 2 ? 4.0 : 8.0;
+    const double u = (m - centre) * inv_half;
+    const int p = 3 * (k - QED_SYN64_KMIN) + part;
     double pf = T.c[QED_SYN64_DEG][p], pg = T.c[2 * QED_SYN64_DEG + 1][p];
 #pragma unroll
     for (int j = QED_SYN64_DEG - 1; j >= 0; --j) {

@@ -8,19 +8,20 @@ paper fits its F and G forms to 1e-8 and to 1e-14 relative error, Table 1).
 Its medium-range form x^{1/3} M - x^{5/3} P still cancels by ~10^3 near x = 4
 in binary64, so this scheme, like the binary32 one, avoids the difference:
 
-    x = m 2^k, m in [1, 2);  each half [1, 1.5), [1.5, 2) of an octave is a piece
-    F(x) = 2^{k/3} * exp(-lam_k x) * sum_j c_j u^j,   u = 4 (m - centre) in [-1, 1)
+    x = m 2^k, m in [1, 2);  [1, 1.25), [1.25, 1.5), [1.5, 2) of an octave are pieces
+    F(x) = 2^{k/3} * exp(-lam_k x) * sum_j c_j u^j,   u = (m - centre) / halfwidth in [-1, 1)
 
 with lam_k = 0 below x = 1/2 and 1 from there (the large-x e^{-x} envelope).
 The factor x^{1/3} of the small- and medium-x behaviour is split into the
 per-octave constant 2^{k/3} and a part m^{1/3} that the polynomial absorbs, so
 the evaluation needs neither a logarithm nor a cube root; u is exact in
-binary64.  Below x = 2^KMIN one more piece is the small-x series
+binary64 (dyadic centres and half-widths).  The pieces are narrower near m = 1,
+where the branch point of m^{1/3} at m = 0 is closest.  Below x = 2^KMIN one more piece is the small-x series
 F = x^{1/3} * sum_j a_j v^j in v = x^{2/3} (the paper's S(x)).  Above 2^(KMAX+1)
 the functions are below 1e-220 and the kernel returns 0.
 
 Coefficients interpolate the target at Chebyshev nodes of u (solved at 60
-digits), then are rounded to binary64; with degree 13 the evaluation error in
+digits), then are rounded to binary64; with degree 11 the evaluation error in
 binary64 is a few units in the last place.  The targets are the binary32
 generator's extended-precision series (this module does not use the oracle).
 """
@@ -37,11 +38,12 @@ try:
 except ImportError:  # pragma: no cover
     mp = None
 
-KMIN, KMAX = -14, 8        # octaves [2^k, 2^(k+1)), k = KMIN..KMAX, two halves each
+KMIN, KMAX = -14, 8        # octaves [2^k, 2^(k+1)), k = KMIN..KMAX
+PARTS = ((1.125, 0.125), (1.375, 0.125), (1.75, 0.25))   # (centre, half-width) in m
 LAMBDA_FROM = -1           # lam_k = 1 for k >= LAMBDA_FROM (x >= 1/2)
-DEG = 13
+DEG = 11
 SMALL_DEG = 6
-NPIECE = 1 + 2 * (KMAX - KMIN + 1)
+NPIECE = 1 + len(PARTS) * (KMAX - KMIN + 1)
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(HERE, "csrc", "synchro_coeffs64.h")
@@ -63,20 +65,20 @@ def _interp(us, vals, deg):
         return [float(c[j]) for j in range(deg + 1)]
 
 
-def piece_target(fun, k, h, u):
-    """fun(x) * exp(lam x) / 2^(k/3) at x = (centre + u / 4) 2^k."""
-    centre = mp.mpf(1.25) + mp.mpf(0.5) * h
+def piece_target(fun, k, part, u):
+    """fun(x) * exp(lam x) / 2^(k/3) at x = (centre + halfwidth u) 2^k."""
+    centre, half = (mp.mpf(v) for v in PARTS[part])
     lam = 1 if k >= LAMBDA_FROM else 0
     with mp.workdps(60):
-        x = (centre + mp.mpf(u) / 4) * mp.power(2, k)
+        x = (centre + half * mp.mpf(u)) * mp.power(2, k)
     xf = float(x)
     with mp.workdps(fs._dps_for(xf)):
         return fun(x) * mp.exp(lam * x) / mp.power(2, mp.mpf(k) / 3)
 
 
-def fit_piece(k, h):
+def fit_piece(k, part):
     us = _nodes(DEG + 1)
-    return [_interp(us, [piece_target(fun, k, h, u) for u in us], DEG)
+    return [_interp(us, [piece_target(fun, k, part, u) for u in us], DEG)
             for fun in (fs.F_mp, fs.G_mp)]
 
 
@@ -125,9 +127,10 @@ def eval64(table, x):
                 p = p * v + a
             res.append(r * p)
         return tuple(res)
-    h = 1 if m >= 1.5 else 0
-    u = 4.0 * (m - (1.25 + 0.5 * h))
-    cf = pieces[(k - KMIN) * 2 + h]
+    part = 0 if m < 1.25 else (1 if m < 1.5 else 2)
+    centre, half = PARTS[part]
+    u = (m - centre) / half
+    cf = pieces[(k - KMIN) * len(PARTS) + part]
     s = 2.0 ** (k / 3.0) * (math.exp(-x) if k >= LAMBDA_FROM else 1.0)
     res = []
     for f in range(2):
@@ -142,8 +145,9 @@ def write_header(table, path=OUT):
     small, pieces = table
     lines = ["// Generated by paper_2008_10468_gb300/fit_synchrotron64.py -- do not edit.",
              "// Binary64 synchrotron functions F(x) = x int_x^inf K_{5/3}, G(x) = x K_{2/3}(x)",
-             "// (Sec. 3.2.1): per half-octave of x = m 2^k, F = 2^{k/3} exp(-lam x) sum_j c_j u^j",
-             "// with u = 4 (m - centre); below 2^KMIN, F = x^{1/3} sum_j a_j (x^{2/3})^j.",
+             "// (Sec. 3.2.1): per piece [1, 1.25), [1.25, 1.5), [1.5, 2) of m in x = m 2^k,",
+             "// F = 2^{k/3} exp(-lam x) sum_j c_j u^j with u = (m - centre) / halfwidth;",
+             "// below 2^KMIN, F = x^{1/3} sum_j a_j (x^{2/3})^j.",
              "#pragma once",
              "#define QED_SYN64_KMIN (%d)" % KMIN,
              "#define QED_SYN64_KMAX %d" % KMAX,
@@ -151,7 +155,7 @@ def write_header(table, path=OUT):
              "#define QED_SYN64_DEG %d" % DEG,
              "#define QED_SYN64_SMALL_DEG %d" % SMALL_DEG,
              "#define QED_SYN64_NPIECE %d" % (len(pieces)),
-             "// [piece][F coefficients 0..DEG, G coefficients 0..DEG], piece = 2 (k - KMIN) + half",
+             "// [piece][F coefficients 0..DEG, G coefficients 0..DEG], piece = 3 (k - KMIN) + part",
              "static __device__ const double qed_syn64_table[QED_SYN64_NPIECE][2 * (QED_SYN64_DEG + 1)] = {"]
     for cf in pieces:
         vals = cf[0] + cf[1]
@@ -172,9 +176,9 @@ def main():
     fs._self_check()
     pieces = []
     for k in range(KMIN, KMAX + 1):
-        for h in (0, 1):
-            pieces.append(fit_piece(k, h))
-            print("piece k=%d h=%d" % (k, h), flush=True)
+        for part in range(len(PARTS)):
+            pieces.append(fit_piece(k, part))
+            print("piece k=%d part=%d" % (k, part), flush=True)
     table = (fit_small(), pieces)
     # check: random points per piece against the targets
     rng = np.random.default_rng(20081046)

@@ -7,7 +7,7 @@ against the same reference, at piece boundaries, ragged sizes and special
 arguments.  The reference's F (the oracle's quadrature) is within ~5e-15 of
 40-digit values up to x = 100 but drifts to 2e-14 to 7e-14 toward x = 512,
 so the 1e-14 bound is tested on [1e-7, 100) and the oracle's 1e-13 on
-[100, 512) (the table itself is within 4.4e-16 of 40-digit values there, as
+[100, 512) (the table itself is within 6.7e-16 of 40-digit values there, as
 its generator checks)."""
 import math
 import os
@@ -28,7 +28,7 @@ def _sample(n, seed, lo=1e-7, hi=100.0):
     x = np.exp(rng.uniform(math.log(lo), math.log(hi), n))
     edges = []
     for k in range(fit.KMIN - 1, 7):
-        for m in (1.0, 1.5):
+        for m in (1.0, 1.25, 1.5):
             v = m * 2.0 ** k
             edges += [v, np.nextafter(v, 0.0), np.nextafter(v, np.inf)]
     return np.concatenate([x, np.array(edges)])
