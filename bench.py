@@ -350,6 +350,9 @@ def run_gb300(args):
     sampler = None if args.no_sampler else run_sampler(arr, pristine, store, cap, n, dev, args,
                                                         restore, value)
 
+    # the same step with the Boris push before every e+- draw
+    push = None if args.no_push else run_push(store, dev, args, restore, value)
+
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -369,6 +372,7 @@ def run_gb300(args):
         "roofline": roof,
         "sweep": sweep,
         "sampler": sampler,
+        "push": push,
         "cascade": cascade,
         "e2e": e2e,
         "gpu_launches": launches_timed,
@@ -501,6 +505,52 @@ def run_cascade(dev, args):
         "substeps_per_step": [s["substeps"] for s in done],
         "drained_photon_weight": float(spec.sum()), "drain_chi": CASCADE_DRAIN_CHI,
     }
+
+
+def run_push(store, dev, args, restore, plain_value):
+    """The clumped step with the Boris push of Algorithm 1 before every e+-
+    draw (qed_event_step_push): one lane per particle through its sub-steps
+    in order, the generations launched one by one."""
+    import torch
+    from paper_2008_10468_gb300 import qed
+    ctx = qed.Context(seed=SEED_CLUMPED, process_mask=3, cascade=True)
+    stream = torch.cuda.current_stream()
+    for w in range(2):
+        restore()
+        ctx.event_step(store, 4000 + w, push=True)
+    steps = max(3, min(args.steps, 5))
+    total_ms, subs, agg = 0.0, 0, {"emissions": 0, "pairs": 0, "children": 0, "passes": 0}
+    ctx.profile_read()
+    ctx.profile(True)
+    kern = {}
+    for k in range(steps):
+        restore()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ctx.event_step(store, 2000 + k, push=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        subs += st["substeps"]
+        for key in agg:
+            agg[key] += st[key]
+        if st["status"] != 0:
+            raise SystemExit("push step failed with status %d" % st["status"])
+        for name, (ms, nl) in ctx.profile_read().items():
+            a = kern.setdefault(name, [0.0, 0])
+            a[0] += ms
+            a[1] += nl
+    ctx.profile(False)
+    value = subs / (total_ms / 1e3)
+    return {"substeps_per_s": value, "ms_per_step": total_ms / steps, "steps": steps,
+            "per_step": {k: v / steps for k, v in agg.items()},
+            "substeps_per_step": subs / steps,
+            "k_push_ms_per_step": kern.get("hot", [0.0])[0] / steps,
+            "relative_to_step_without_push": value / plain_value,
+            "note": "generations launched one by one with CUDA events around each "
+                    "launch; no tail pass, no graph"}
 
 
 def run_sampler(arr, pristine, store, cap, n, dev, args, restore, plain_value):
@@ -678,6 +728,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sampler", action="store_true")
     ap.add_argument("--no-cascade", action="store_true")
+    ap.add_argument("--no-push", action="store_true")
     ap.add_argument("--cascade-steps", type=int, default=100)
     ap.add_argument("--tail-rows", type=int, default=None,
                     help="generations below this many rows go to the tail pass (0: off; "

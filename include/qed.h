@@ -191,6 +191,23 @@ qed_status qed_plan(qed_ctx* ctx, const qed_particles* p, int64_t n, float* chi,
 qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
                           qed_step_stats* out);
 
+/* The same step with the Boris push of Algorithm 1 (Sec. 2.2: the particle is
+ * propagated by the sub-step with the Boris pusher, then chi is computed and
+ * the draw tested): before every draw an electron or positron moves its
+ * momentum by one sub-step h under the Lorentz force of its own constant
+ * fields, dp/dt = 2 pi q (E + p x B / gamma) in code units (q = -1 for e-,
+ * +1 for e+), and the draw is tested at the chi of the pushed momentum.  A
+ * photon flies straight (Algorithm 2): momentum and chi stay.  The sub-step
+ * count is planned from the state at the start of the step and after each
+ * event, as in qed_event_step.  The push is the IEEE binary32 evaluation of
+ * the Boris formulas (the store's precision).  Positions are not stored, so
+ * only momenta move.  On return every processed e+- row holds its momentum
+ * after the step.  Same arguments, statistics, capacity rule and errors as
+ * qed_event_step; the learned sampler is not used, and the generations run
+ * one launch each (no tail pass, no graph). */
+qed_status qed_event_step_push(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                               qed_step_stats* out);
+
 /* Synchronise and read the statistics of the last step.  Errors: ARG, CUDA. */
 qed_status qed_read_stats(qed_ctx* ctx, qed_step_stats* out);
 

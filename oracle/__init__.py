@@ -18,7 +18,10 @@ What it computes (each function cites the passage it follows):
   P_p (Eq. 2 with the bracket sign corrected, Algorithm 2).
 * ``total_per_c``: the per-sub-step event probability divided by c
   (the integral bounded by f(b) in Sec. 3.1.1).
-* ``event_step``: Algorithms 1 and 2 for a particle store over one global step.
+* ``event_step``: Algorithms 1 and 2 for a particle store over one global step,
+  optionally with the Boris push of Algorithm 1 before every e+- draw.
+* ``boris64``/``boris32``: that push (the Lorentz force in code units), in
+  binary64 and on the binary32 particle state.
 
 Parity is pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py``.
 """
@@ -66,6 +69,10 @@ def lib():
         L.orc_event_step_mt.argtypes = [P(Config), P(Particles), u32, P(Stats)]
         L.orc_log_free.restype = None; L.orc_log_free.argtypes = [P(Log)]
         L.orc_plan.restype = u32
+        L.orc_boris64.restype = None
+        L.orc_boris64.argtypes = [i32, d, P(d), P(d), P(d)]
+        L.orc_boris32.restype = None
+        L.orc_boris32.argtypes = [i32, C.c_float, P(C.c_float), P(C.c_float), P(C.c_float)]
         L.orc_plan.argtypes = [P(Config), i32] + [d] * 10 + [P(d), P(d), P(d)]
         _lib = L
     return _lib
@@ -76,7 +83,7 @@ class Config(C.Structure):
                 ("E_s", C.c_double), ("p_max", C.c_double), ("pair_coeff", C.c_double),
                 ("tie_draw", C.c_double), ("tie_plan", C.c_double),
                 ("process_mask", C.c_uint32), ("cascade", C.c_int32),
-                ("recoil", C.c_int32), ("threads", C.c_int32)]
+                ("recoil", C.c_int32), ("threads", C.c_int32), ("push", C.c_int32)]
 
 
 class Particles(C.Structure):
@@ -227,7 +234,7 @@ def total_per_c(kind, b, panels=64, order=16):
 
 def make_config(seed, dt=0.1, lambda_m=1e-6, p_max=0.01, pair_coeff=0.1,
                 process_mask=3, cascade=1, recoil=1, threads=1,
-                tie_draw=TIE_DRAW, tie_plan=TIE_PLAN):
+                tie_draw=TIE_DRAW, tie_plan=TIE_PLAN, push=0):
     cf = Config()
     cf.seed = int(seed)
     cf.dt = float(dt)
@@ -241,7 +248,29 @@ def make_config(seed, dt=0.1, lambda_m=1e-6, p_max=0.01, pair_coeff=0.1,
     cf.cascade = int(cascade)
     cf.recoil = int(recoil)
     cf.threads = int(threads)
+    cf.push = int(push)
     return cf
+
+
+def boris64(charge, h, p, E, B, steps=1):
+    """`steps` Boris pushes of length h (periods) in binary64; returns p."""
+    pa = (C.c_double * 3)(*[float(v) for v in p])
+    Ea = (C.c_double * 3)(*[float(v) for v in E])
+    Ba = (C.c_double * 3)(*[float(v) for v in B])
+    for _ in range(int(steps)):
+        lib().orc_boris64(int(charge), float(h), pa, Ea, Ba)
+    return np.array(list(pa), dtype=np.float64)
+
+
+def boris32(charge, h, p, E, B, steps=1):
+    """`steps` Boris pushes on the binary32 state; returns p (float32)."""
+    f = C.c_float
+    pa = (f * 3)(*[float(np.float32(v)) for v in p])
+    Ea = (f * 3)(*[float(np.float32(v)) for v in E])
+    Ba = (f * 3)(*[float(np.float32(v)) for v in B])
+    for _ in range(int(steps)):
+        lib().orc_boris32(int(charge), float(np.float32(h)), pa, Ea, Ba)
+    return np.array(list(pa), dtype=np.float32)
 
 
 def plan(cf, p, E, B, t_rem, photon=False):

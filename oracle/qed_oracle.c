@@ -17,7 +17,10 @@
  *     bracket corrected, see below);
  *   - the sub-step planner from the rate bounds f(b) of Sec. 3.1.1;
  *   - Algorithms 1 and 2 with local sub-stepping, recoil and children;
- *   - Philox4x32-10 (Salmon et al., SC'11) for the per-sub-step draws.
+ *   - Philox4x32-10 (Salmon et al., SC'11) for the per-sub-step draws;
+ *   - optionally, the Boris push of Algorithm 1 (line 3 of its loop): every
+ *     sub-step of an electron or positron first moves its momentum by the
+ *     Lorentz force, then chi is recomputed for the draw.
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *   * Eq. 2 as printed, F(z) - (3/2) chi z G(z), is negative for every
@@ -203,6 +206,65 @@ double orc_chi(int is_photon, double px, double py, double pz,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Boris push (Algorithm 1, the momentum update of every sub-step).          */
+/* In code units (p in m c, E and B in m c omega / e, t in laser periods)    */
+/* the Lorentz force reads dp/dt = 2 pi q (E + p x B / gamma), q = -1 for    */
+/* an electron and +1 for a positron.  One step of length h with a = pi q h: */
+/*   p- = p + a E;   gamma- = sqrt(1 + |p-|^2);   t = (a / gamma-) B;         */
+/*   s = 2 t / (1 + |t|^2);   p' = p- + p- x t;   p+ = p- + p' x s;           */
+/*   p(h) = p+ + a E                                                          */
+/* (half an electric kick, a rotation about B by 2 atan|t|, half a kick).    */
+/* ------------------------------------------------------------------------ */
+void orc_boris64(int charge, double h, double p[3], const double E[3], const double B[3]) {
+    const double a = ORC_PI * (double)charge * h;
+    double m[3], t[3], s[3], q[3], r[3];
+    for (int k = 0; k < 3; ++k) m[k] = p[k] + a * E[k];
+    const double g = sqrt(1.0 + m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    for (int k = 0; k < 3; ++k) t[k] = a / g * B[k];
+    const double t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
+    for (int k = 0; k < 3; ++k) s[k] = 2.0 * t[k] / (1.0 + t2);
+    q[0] = m[0] + (m[1] * t[2] - m[2] * t[1]);
+    q[1] = m[1] + (m[2] * t[0] - m[0] * t[2]);
+    q[2] = m[2] + (m[0] * t[1] - m[1] * t[0]);
+    r[0] = m[0] + (q[1] * s[2] - q[2] * s[1]);
+    r[1] = m[1] + (q[2] * s[0] - q[0] * s[2]);
+    r[2] = m[2] + (q[0] * s[1] - q[1] * s[0]);
+    for (int k = 0; k < 3; ++k) p[k] = r[k] + a * E[k];
+}
+
+/* The same step on the binary32 particle state: every operation above in  */
+/* IEEE binary32 with round-to-nearest, in this order (the store holds the */
+/* momentum in binary32, and the state after each sub-step is a binary32   */
+/* value).  Built with -ffp-contract=off, so no two operations fuse.       */
+void orc_boris32(int charge, float h, float p[3], const float E[3], const float B[3]) {
+    const float pi = (float)ORC_PI;
+    const float ah = pi * h;
+    const float a = charge < 0 ? -ah : ah;
+    float m[3], t[3], s[3], q[3], r[3];
+    for (int k = 0; k < 3; ++k) {
+        const float kick = a * E[k];
+        m[k] = p[k] + kick;
+    }
+    const float m2 = (m[0] * m[0] + m[1] * m[1]) + m[2] * m[2];
+    const float g = sqrtf(1.0f + m2);
+    const float ag = a / g;
+    for (int k = 0; k < 3; ++k) t[k] = ag * B[k];
+    const float t2 = (t[0] * t[0] + t[1] * t[1]) + t[2] * t[2];
+    const float f = 2.0f / (1.0f + t2);
+    for (int k = 0; k < 3; ++k) s[k] = f * t[k];
+    q[0] = m[0] + (m[1] * t[2] - m[2] * t[1]);
+    q[1] = m[1] + (m[2] * t[0] - m[0] * t[2]);
+    q[2] = m[2] + (m[0] * t[1] - m[1] * t[0]);
+    r[0] = m[0] + (q[1] * s[2] - q[2] * s[1]);
+    r[1] = m[1] + (q[2] * s[0] - q[0] * s[2]);
+    r[2] = m[2] + (q[0] * s[1] - q[1] * s[0]);
+    for (int k = 0; k < 3; ++k) {
+        const float kick = a * E[k];
+        p[k] = r[k] + kick;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Rate bounds, Sec. 3.1.1.  c = sqrt(3) R t / (pi gamma), b = 3 chi / 2.    */
 /* ------------------------------------------------------------------------ */
 double orc_bound_emission(double b, double c) {
@@ -306,6 +368,7 @@ typedef struct {
     int32_t cascade;      /* process children within the step            */
     int32_t recoil;       /* 0: events leave the parent unchanged (test) */
     int32_t threads;
+    int32_t push;         /* 1: Boris push of e+- before every sub-step's draw */
 } orc_config;
 
 typedef struct {
@@ -415,6 +478,13 @@ static void process_particle(const orc_config* cf, orc_particles* P, int64_t i, 
     const double Ex = P->Ex[i], Ey = P->Ey[i], Ez = P->Ez[i];
     const double Bx = P->Bx[i], By = P->By[i], Bz = P->Bz[i];
     const double k_sqrt3_pi = ORC_SQRT3 / ORC_PI;
+    /* Algorithm 1 with the push: an electron (charge -1) or positron (+1) is
+     * pushed before every draw.  A photon flies straight (Algorithm 2): its
+     * momentum, and so chi, stays as it is. */
+    const int push = cf->push && !is_photon;
+    const int charge = type == 0 ? -1 : 1;
+    const float fE[3] = {P->Ex[i], P->Ey[i], P->Ez[i]};
+    const float fB[3] = {P->Bx[i], P->By[i], P->Bz[i]};
 
     while (t_rem > 0.0) {
         /* Algorithms 1/2, planning: sub-step for the remaining time. */
@@ -440,19 +510,30 @@ static void process_particle(const orc_config* cf, orc_particles* P, int64_t i, 
         double c_h = k_sqrt3_pi * cf->R * h / gamma;
         int event = 0;
         for (uint32_t k = 0; k < N; ++k) {
+            /* with the push: move the momentum over this sub-step, then chi */
+            double chi_k = chi, b_k = b, c_k = c_h;
+            if (push) {
+                float pf[3] = {(float)px, (float)py, (float)pz};
+                orc_boris32(charge, (float)h, pf, fE, fB);
+                px = pf[0]; py = pf[1]; pz = pf[2];
+                double g;
+                chi_k = orc_chi(0, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, cf->E_s, &g);
+                b_k = 1.5 * chi_k;
+                c_k = k_sqrt3_pi * cf->R * h / g;
+            }
             /* draw x, y for this sub-step */
             double x, y;
             orc_draw(cf->seed, id, step, s, &x, &y);
             st->substeps++;
             /* acceptance test */
-            double P_acc = is_photon ? orc_Pp(b, c_h, x) : orc_Pm(b, c_h, x);
+            double P_acc = is_photon ? orc_Pp(b_k, c_k, x) : orc_Pm(b_k, c_k, x);
             if (!tied && fabs(y - P_acc) <= cf->tie_draw) { tied = 1; log_tie(L, id, s, 1); }
             if (y < P_acc) {
                 /* the event closes sub-step k */
                 double t_after = (k + 1 == N) ? 0.0 : t_rem - (double)(k + 1) * h;
                 orc_event e;
                 memset(&e, 0, sizeof e);
-                e.parent_id = id; e.s = s; e.chi = chi;
+                e.parent_id = id; e.s = s; e.chi = chi_k;
                 orc_child_ids(cf->seed, id, step, s, e.child_id);
                 if (!is_photon) {
                     double delta = x * x * x;

@@ -91,6 +91,7 @@ struct DevCtl {
     unsigned int step_tail;         // long plans queued by the persistent kernel, stored
                                     // after the thread pass's hot_tail entries
     int skip;                       // the tail pass does nothing
+    unsigned long long push_head;   // push mode: next row of the generation to take
 };
 
 // Type byte of a child row that has been reserved but not yet written: in the
@@ -699,6 +700,158 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
     flush_stats(stats, ctl);
 }
 
+// ---------------------------------------------------------------------------
+// Push mode: Algorithm 1 with the Boris push before every e+- draw
+// ---------------------------------------------------------------------------
+// One generation of a push-mode step.  The push makes every sub-step depend
+// on the one before, so a lane steps one particle through its sub-steps in
+// order; a lane whose particle is done takes the next row of the generation
+// (the idle lanes of a warp share one atomic on ctl->push_head, which the
+// host clears before the launch).  Per sub-step of an e+-: the push over h,
+// chi and eps of the new momentum, the squeeze bound for that chi, the draw
+// of sub-step s and the test.  A photon flies straight: its momentum, chi and
+// plan stay, as in the other kernels.  After an event the particle is
+// re-planned over the time that remains, from its state after the push and
+// the recoil.
+__global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParams SP, Scratch S,
+                                                       DevCtl* ctl) {
+    const uint32_t step = step_index(SP);
+    __shared__ SharedTables sm;
+    stage_tables(sm);
+    __syncthreads();
+    if (ctl->status == (int)QED_ERR_TIMEOUT) return;
+    const bool first_pass = ctl->first_pass != 0;
+    const long long begin = first_pass ? 0 : ctl->pass_begin;
+    const long long n = ctl->pass_end - begin;
+    constexpr unsigned int kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
+    const PlanConst PC = plan_const(SP);
+    Stats stats;
+    bool busy = false, drained = n <= 0, photon = false, electron = false, need_plan = false;
+    bool removed = false;
+    long long i = 0;
+    uint64_t id = 0;
+    PState st{0.0f, 0.0f, 0.0f};
+    Fields F{0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    ftime t_rem{0.0f, 0.0f};
+    Plan pl;
+    pl.N = 0;
+    pl.T = 0;
+    pl.b = pl.c_h = 0.0f;
+    pl.h = ftime{0.0f, 0.0f};
+    float chi = 0.0f, eps = 0.0f, a = 0.0f;
+    uint32_t k = 0, s = 0, blk = kNoEvent;
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    while (true) {
+        const unsigned int idle = __ballot_sync(kAll, !busy);
+        if (idle && !drained) {
+            const int leader = __ffs(idle) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&ctl->push_head, (unsigned long long)__popc(idle));
+            base = __shfl_sync(kAll, base, leader);
+            if ((long long)base + __popc(idle) >= n) drained = true;
+            if (!busy) {
+                const long long row = (long long)base + __popc(idle & ((1u << lane) - 1u));
+                if (row < n) {
+                    i = begin + row;
+                    const uint8_t type = P.type[i];
+                    photon = type == QED_PHOTON;
+                    if (type <= QED_PHOTON && process_enabled(SP, photon)) {
+                        t_rem = first_pass ? SP.t_step : S.t_rem[i];
+                        if (time_positive(t_rem)) {
+                            busy = true;
+                            need_plan = true;
+                            removed = false;
+                            electron = type == QED_ELECTRON;
+                            id = P.id[i];
+                            st = PState{P.px[i], P.py[i], P.pz[i]};
+                            F = Fields{P.Ex[i], P.Ey[i], P.Ez[i], P.Bx[i], P.By[i], P.Bz[i]};
+                            s = 0;
+                            blk = kNoEvent;
+                        }
+                    }
+                }
+            }
+        }
+        if (!__any_sync(kAll, busy)) {
+            if (drained) break;
+            continue;
+        }
+        if (!busy) continue;
+        bool done = false;
+        if (need_plan) {
+            need_plan = false;
+            pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, F.Ex, F.Ey,
+                               F.Ez, F.Bx, F.By, F.Bz, t_rem, &chi, &eps);
+            if (!(eps > 0.0f)) {
+                done = true;
+            } else {
+                stats.plans++;
+                stats.guard += pl.guard ? 1 : 0;
+                stats.max_N = max(stats.max_N, pl.N);
+                k = 0;
+                const float ah = __fmul_rn(kPi, pl.h.hi);
+                a = electron ? -ah : ah;
+                if (photon && pl.T == 0u) {
+                    // a zero squeeze threshold admits no candidate
+                    stats.substeps += pl.N;
+                    s += pl.N;
+                    done = true;
+                }
+            }
+        } else {
+            float b = pl.b, c_h = pl.c_h, chi_k = chi, eps_k = eps;
+            uint32_t T = pl.T;
+            if (!photon) {
+                boris_push(st.px, st.py, st.pz, a, F.Ex, F.Ey, F.Ez, F.Bx, F.By, F.Bz);
+                chi_k = chi_any(false, st.px, st.py, st.pz, F.Ex, F.Ey, F.Ez, F.Bx, F.By, F.Bz,
+                                PC.inv_Es, &eps_k);
+                b = 1.5f * chi_k;
+                c_h = PC.K * pl.h.hi * __fdividef(1.0f, eps_k);
+                const float b23 = b > 0.0f ? exp2f(__log2f(b) * (2.0f / 3.0f)) : 0.0f;
+                T = squeeze_threshold(squeeze_bound(sm.sqz_e, sm.sqz_p, false, b, c_h, b23));
+            }
+            if ((s >> 1) != blk) {
+                blk = s >> 1;
+                r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, blk), k0, k1);
+            }
+            const uint32_t yw = (s & 1u) ? r.w : r.y;
+            const float x = u01((s & 1u) ? r.z : r.x);
+            stats.substeps++;
+            bool acc = false;
+            if ((yw >> 9) < T) {
+                stats.cand++;
+                float dtmp;
+                acc = u01(yw) < acceptance(sm.syn, photon, b, c_h, x, &dtmp);
+            }
+            if (acc) {
+                const ftime t_after = (k + 1u == pl.N) ? ftime{0.0f, 0.0f}
+                                                       : time_sub_mul(t_rem, k + 1u, pl.h);
+                removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps_k, chi_k, step, s,
+                                      t_after, st, stats, true, false, F, false);
+                ++s;
+                t_rem = t_after;
+                if (removed || !time_positive(t_rem)) done = true;
+                else need_plan = true;
+            } else {
+                ++s;
+                if (++k == pl.N) done = true;
+            }
+        }
+        if (done) {
+            busy = false;
+            if (removed) {
+                P.type[i] = QED_REMOVED;
+            } else if (!photon) {
+                P.px[i] = st.px;
+                P.py[i] = st.py;
+                P.pz[i] = st.pz;
+            }
+        }
+    }
+    flush_stats(stats, ctl);
+}
 
 // One queued particle stepped by the whole warp (all 32 lanes, identical
 // arguments): 64 sub-steps per iteration (lane l draws the Philox block of
@@ -1718,6 +1871,7 @@ struct qed_ctx {
     uint32_t hot_min, long_min;
     long long tail_rows;        // cascade generations below this size go to the tail pass
     int step_blocks, step_net_blocks;   // resident blocks of the tail pass's kernel
+    int push_blocks;            // resident blocks of the push-mode kernel
     // compaction
     Mirror mirror;
     long long mirror_cap;
@@ -2014,6 +2168,9 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<1>, kLaneThreads,
                                                       sizeof(SamplerSmem));
         ctx->step_net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
+        per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push, kLaneThreads, 0);
+        ctx->push_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         ctx->hot_min = kHotMinDefault;
         ctx->long_min = kLongMinDefault;
         ctx->tail_rows = kTailRowsDefault;
@@ -2204,6 +2361,45 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
         k_tail_end<<<ctx->sms * 8, 256, 0, ctx->stream>>>(D, S, ctx->d_ctl);
     }
     QED_CUDA(ctx, cudaGetLastError());
+    if (out) return qed_read_stats(ctx, out);
+    return QED_OK;
+}
+
+qed_status qed_event_step_push(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                               qed_step_stats* out) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!particles_ok(p) || step_index > 0xffffffffull)
+        return set_err(ctx, QED_ERR_ARG, "qed_event_step_push: bad argument");
+    qed_status st = ensure_scratch(ctx, p->capacity);
+    if (st != QED_OK) return st;
+    const StepParams SP = make_params(ctx->cfg, step_index);   // the sampler is not used
+    const DevParticles D = to_dev(p);
+    const Scratch S = make_scratch(ctx);
+    const bool cascade = cascade_enabled(ctx->cfg);
+    {
+        LaunchScope ls(ctx, QED_KERNEL_CONTROL);
+        k_step_init<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, 0);
+    }
+    for (int pass = 0; pass < ctx->cfg.max_passes; ++pass) {
+        QED_CUDA(ctx, cudaMemsetAsync(&ctx->d_ctl->push_head, 0, sizeof(unsigned long long),
+                                      ctx->stream));
+        {
+            LaunchScope ls(ctx, QED_KERNEL_HOT);
+            k_push<<<ctx->push_blocks, kLaneThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+        }
+        {
+            LaunchScope ls(ctx, QED_KERNEL_CONTROL);
+            // no tail pass: every generation runs k_push
+            k_advance<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, cascade ? 1 : 0,
+                                                ctx->cfg.max_passes, 0ll, 0ull, 0);
+        }
+        QED_CUDA(ctx, cudaGetLastError());
+        if (!cascade) break;
+        QED_CUDA(ctx, cudaMemcpyAsync(ctx->h_ctl, ctx->d_ctl, sizeof(DevCtl),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+        QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (!ctx->h_ctl->more) break;
+    }
     if (out) return qed_read_stats(ctx, out);
     return QED_OK;
 }

@@ -5,7 +5,8 @@
 //   - the synchrotron functions F and G (Sec. 3.2.1) from the octave tables of
 //     synchro_coeffs.h, staged in shared memory;
 //   - the rate bounds f(b) of Sec. 3.1.1 and the sub-step planner;
-//   - the acceptance functions of Algorithms 1 and 2.
+//   - the acceptance functions of Algorithms 1 and 2;
+//   - the Boris push of Algorithm 1 on the binary32 momentum.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -136,6 +137,47 @@ __device__ __forceinline__ float chi_f32(bool photon, float px, float py, float 
     *eps_out = eps;
     *well_conditioned = q > 0.125f * M2;
     return q > 0.0f ? sqrtf(q) * inv_Es : 0.0f;
+}
+
+// chi and eps of a momentum: binary32 when well conditioned, else float-float.
+__device__ __forceinline__ float chi_any(bool photon, float px, float py, float pz, float Ex,
+                                         float Ey, float Ez, float Bx, float By, float Bz,
+                                         float inv_Es, float* eps_out) {
+    bool wc;
+    const float chi = chi_f32(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, inv_Es, eps_out, &wc);
+    if (wc) return chi;
+    return chi_ff(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, inv_Es, eps_out);
+}
+
+// Boris push (Algorithm 1: the particle moves by one sub-step before the
+// draw).  In code units (p in m c, fields in m c omega / e, time in laser
+// periods) the Lorentz force is dp/dt = 2 pi q (E + p x B / gamma); with
+// a = pi q h for a sub-step h:
+//   p- = p + a E,  t = (a / gamma(p-)) B,  s = 2 t / (1 + t^2),
+//   p+ = p- + (p- + p- x t) x s,  p(h) = p+ + a E.
+// Each operation is an explicit round-to-nearest binary32 intrinsic, in this
+// order: the result is the IEEE binary32 evaluation of these formulas, not
+// subject to contraction into FMAs.
+__device__ __forceinline__ void boris_push(float& px, float& py, float& pz, float a, float Ex,
+                                           float Ey, float Ez, float Bx, float By, float Bz) {
+    const float mx = __fadd_rn(px, __fmul_rn(a, Ex));
+    const float my = __fadd_rn(py, __fmul_rn(a, Ey));
+    const float mz = __fadd_rn(pz, __fmul_rn(a, Ez));
+    const float m2 = __fadd_rn(__fadd_rn(__fmul_rn(mx, mx), __fmul_rn(my, my)), __fmul_rn(mz, mz));
+    const float ag = __fdiv_rn(a, __fsqrt_rn(__fadd_rn(1.0f, m2)));
+    const float tx = __fmul_rn(ag, Bx), ty = __fmul_rn(ag, By), tz = __fmul_rn(ag, Bz);
+    const float t2 = __fadd_rn(__fadd_rn(__fmul_rn(tx, tx), __fmul_rn(ty, ty)), __fmul_rn(tz, tz));
+    const float f = __fdiv_rn(2.0f, __fadd_rn(1.0f, t2));
+    const float sx = __fmul_rn(f, tx), sy = __fmul_rn(f, ty), sz = __fmul_rn(f, tz);
+    const float qx = __fadd_rn(mx, __fsub_rn(__fmul_rn(my, tz), __fmul_rn(mz, ty)));
+    const float qy = __fadd_rn(my, __fsub_rn(__fmul_rn(mz, tx), __fmul_rn(mx, tz)));
+    const float qz = __fadd_rn(mz, __fsub_rn(__fmul_rn(mx, ty), __fmul_rn(my, tx)));
+    const float rx = __fadd_rn(mx, __fsub_rn(__fmul_rn(qy, sz), __fmul_rn(qz, sy)));
+    const float ry = __fadd_rn(my, __fsub_rn(__fmul_rn(qz, sx), __fmul_rn(qx, sz)));
+    const float rz = __fadd_rn(mz, __fsub_rn(__fmul_rn(qx, sy), __fmul_rn(qy, sx)));
+    px = __fadd_rn(rx, __fmul_rn(a, Ex));
+    py = __fadd_rn(ry, __fmul_rn(a, Ey));
+    pz = __fadd_rn(rz, __fmul_rn(a, Ez));
 }
 
 // ---------------------------------------------------------------------------

@@ -85,6 +85,8 @@ def lib():
         L.qed_plan.restype = st
         L.qed_event_step.argtypes = [vp, C.POINTER(Particles), u64, C.POINTER(StepStats)]
         L.qed_event_step.restype = st
+        L.qed_event_step_push.argtypes = [vp, C.POINTER(Particles), u64, C.POINTER(StepStats)]
+        L.qed_event_step_push.restype = st
         L.qed_read_stats.argtypes = [vp, C.POINTER(StepStats)]
         L.qed_read_stats.restype = st
         L.qed_set_event_log.argtypes = [vp, vp, i64, vp]
@@ -288,16 +290,18 @@ class Context:
         raw = buf[:n * EVENT_DTYPE.itemsize].cpu().numpy()
         return raw.view(EVENT_DTYPE).copy(), int(cnt.item())
 
-    def event_step(self, store, step, sync=True):
-        """One global step; returns the statistics dict (sync=True) or None."""
+    def event_step(self, store, step, sync=True, push=False):
+        """One global step; returns the statistics dict (sync=True) or None.
+        push=True: the step with the Boris push before every e+- draw."""
+        fn = lib().qed_event_step_push if push else lib().qed_event_step
         p = store.struct()
         if sync:
             s = StepStats()
-            st = lib().qed_event_step(self._h, C.byref(p), int(step), C.byref(s))
+            st = fn(self._h, C.byref(p), int(step), C.byref(s))
             if st not in (QED_OK, QED_ERR_CAPACITY):
                 self._check(st)
             return stats_dict(s)
-        self._check(lib().qed_event_step(self._h, C.byref(p), int(step), None))
+        self._check(fn(self._h, C.byref(p), int(step), None))
         return None
 
     def compact(self, store):
