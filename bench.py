@@ -44,8 +44,8 @@ CASCADE_DRAIN_CHI = 0.05
 # profiled steps; see profiles/hot_pass_traffic_clumped_2p24.md), valid for the
 # kernel sources whose SHA-256 is given; any other source reports traffic as
 # unknown.
-HOT_TRAFFIC = {"bytes_per_launch": 64.33e6,
-               "sources_sha256": "89491df6a620885aaff09a6b87b5b0b501b30452c967c6de891e550015acc2e9"}
+HOT_TRAFFIC = {"bytes_per_launch": 64.32e6,
+               "sources_sha256": "478bd92d31f797a9457e99aa5b29c110190cfe3e822bfe99b3e4d19fa3445059"}
 
 METRIC = "particle-steps/sec (sub-stepped)"
 UNIT = "substeps/s"
