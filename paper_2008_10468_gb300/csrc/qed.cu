@@ -703,6 +703,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
 // ---------------------------------------------------------------------------
 // Push mode: Algorithm 1 with the Boris push before every e+- draw
 // ---------------------------------------------------------------------------
+constexpr int kPushGroupMax = 16;   // busy lanes of a drained warp that switch to group mode
 // One generation of a push-mode step.  The push makes every sub-step depend
 // on the one before, so a lane steps one particle through its sub-steps in
 // order; a lane whose particle is done takes the next row of the generation
@@ -774,33 +775,137 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
                 }
             }
         }
-        if (!__any_sync(kAll, busy)) {
+        const unsigned int bm = __ballot_sync(kAll, busy);
+        if (!bm) {
             if (drained) break;
             continue;
         }
-        if (!busy) continue;
-        bool done = false;
-        if (need_plan) {
+        // plan the lane's particle (Algorithms 1/2, planning); true if it is done
+        auto plan_now = [&]() -> bool {
             need_plan = false;
             pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, F.Ex, F.Ey,
                                F.Ez, F.Bx, F.By, F.Bz, t_rem, &chi, &eps);
-            if (!(eps > 0.0f)) {
-                done = true;
-            } else {
-                stats.plans++;
-                stats.guard += pl.guard ? 1 : 0;
-                stats.max_N = max(stats.max_N, pl.N);
-                k = 0;
-                const float ah = __fmul_rn(kPi, pl.h.hi);
-                a = electron ? -ah : ah;
-                if (photon && pl.T == 0u) {
-                    // a zero squeeze threshold admits no candidate
-                    stats.substeps += pl.N;
-                    s += pl.N;
-                    done = true;
+            if (!(eps > 0.0f)) return true;
+            stats.plans++;
+            stats.guard += pl.guard ? 1 : 0;
+            stats.max_N = max(stats.max_N, pl.N);
+            k = 0;
+            const float ah = __fmul_rn(kPi, pl.h.hi);
+            a = electron ? -ah : ah;
+            if (photon && pl.T == 0u) {
+                // a zero squeeze threshold admits no candidate
+                stats.substeps += pl.N;
+                s += pl.N;
+                return true;
+            }
+            return false;
+        };
+        const int m = __popc(bm);
+        bool done = false;
+        if (drained && m <= kPushGroupMax) {
+            // Group mode: no rows are left and at most kPushGroupMax lanes are
+            // busy.  The g-th busy lane's particle gets lanes [g G, (g+1) G):
+            // every lane of the group runs the same push chain from the
+            // owner's state and keeps the state after push j + 1 (j its place
+            // in the group), then tests sub-step s + j; the first accepted
+            // sub-step of the group decides, as in the sequential loop.  Only
+            // the pushes stay serial.
+            const int groups = m == 1 ? 1 : (m == 2 ? 2 : (m <= 4 ? 4 : (m <= 8 ? 8 : 16)));
+            const int G = 32 / groups;
+            const int g = lane / G, j = lane - g * G;
+            int owner = lane;
+            if (g < m) {
+                unsigned int mm = bm;
+                for (int t = 0; t < g; ++t) mm &= mm - 1u;
+                owner = __ffs(mm) - 1;
+            }
+            const bool ready = busy && !need_plan;
+            if (busy && need_plan) done = plan_now();   // its group waits this round
+            const bool g_ready = (__shfl_sync(kAll, ready ? 1 : 0, owner) != 0) && g < m;
+            const float ox = __shfl_sync(kAll, st.px, owner), oy = __shfl_sync(kAll, st.py, owner),
+                        oz = __shfl_sync(kAll, st.pz, owner);
+            const float oa = __shfl_sync(kAll, a, owner);
+            const float oEx = __shfl_sync(kAll, F.Ex, owner), oEy = __shfl_sync(kAll, F.Ey, owner),
+                        oEz = __shfl_sync(kAll, F.Ez, owner), oBx = __shfl_sync(kAll, F.Bx, owner),
+                        oBy = __shfl_sync(kAll, F.By, owner), oBz = __shfl_sync(kAll, F.Bz, owner);
+            const float ohh = __shfl_sync(kAll, pl.h.hi, owner), ob = __shfl_sync(kAll, pl.b, owner),
+                        och = __shfl_sync(kAll, pl.c_h, owner), ochi = __shfl_sync(kAll, chi, owner),
+                        oeps = __shfl_sync(kAll, eps, owner);
+            const uint32_t oT = __shfl_sync(kAll, pl.T, owner), oN = __shfl_sync(kAll, pl.N, owner),
+                           ok = __shfl_sync(kAll, k, owner), os = __shfl_sync(kAll, s, owner);
+            const uint32_t oid0 = __shfl_sync(kAll, (uint32_t)id, owner),
+                           oid1 = __shfl_sync(kAll, (uint32_t)(id >> 32), owner);
+            const bool oph = __shfl_sync(kAll, photon ? 1 : 0, owner) != 0;
+            const uint32_t valid = g_ready ? min((uint32_t)G, oN - ok) : 0u;
+            PState q{ox, oy, oz}, mine = q;
+            const bool do_push = g_ready && !oph;
+            for (int t = 0; t < G; ++t) {
+                if (do_push && (uint32_t)t < valid)
+                    boris_push(q.px, q.py, q.pz, oa, oEx, oEy, oEz, oBx, oBy, oBz);
+                if (t == j) mine = q;
+            }
+            bool acc = false, cnd = false;
+            float cj = ochi, ej = oeps, xj = 0.0f;
+            if ((uint32_t)j < valid) {
+                float b = ob, c_h = och;
+                uint32_t T = oT;
+                if (!oph) {
+                    cj = chi_any(false, mine.px, mine.py, mine.pz, oEx, oEy, oEz, oBx, oBy, oBz,
+                                 PC.inv_Es, &ej);
+                    b = 1.5f * cj;
+                    c_h = PC.K * ohh * __fdividef(1.0f, ej);
+                    const float b23 = b > 0.0f ? exp2f(__log2f(b) * (2.0f / 3.0f)) : 0.0f;
+                    T = squeeze_threshold(squeeze_bound(sm.sqz_e, sm.sqz_p, false, b, c_h, b23));
+                }
+                const uint32_t sj = os + (uint32_t)j;
+                const uint4 r = philox4x32_10(make_uint4(oid0, oid1, step, sj >> 1), k0, k1);
+                const uint32_t yw = (sj & 1u) ? r.w : r.y;
+                xj = u01((sj & 1u) ? r.z : r.x);
+                if ((yw >> 9) < T) {
+                    cnd = true;
+                    float dtmp;
+                    acc = u01(yw) < acceptance(sm.syn, oph, b, c_h, xj, &dtmp);
                 }
             }
-        } else {
+            const unsigned int am = __ballot_sync(kAll, acc);
+            const unsigned int gmask = G == 32 ? kAll : (((1u << G) - 1u) << (g * G));
+            const unsigned int ga = am & gmask;
+            const int jstar = ga ? __ffs(ga) - 1 - g * G : -1;
+            const uint32_t used = jstar >= 0 ? (uint32_t)jstar + 1u : valid;
+            if (cnd && (uint32_t)j < used) stats.cand++;
+            // each busy lane takes the outcome of the group it owns
+            const int my_g = __popc(bm & ((1u << lane) - 1u));
+            const int gl = (busy ? my_g : 0) * G;
+            const uint32_t used_o = __shfl_sync(kAll, used, gl);
+            const int jstar_o = __shfl_sync(kAll, jstar, gl);
+            const int src = gl + (used_o > 0u ? (int)used_o - 1 : 0);
+            const float nx = __shfl_sync(kAll, mine.px, src), ny = __shfl_sync(kAll, mine.py, src),
+                        nz = __shfl_sync(kAll, mine.pz, src);
+            const float nchi = __shfl_sync(kAll, cj, src), neps = __shfl_sync(kAll, ej, src),
+                        nxd = __shfl_sync(kAll, xj, src);
+            if (ready) {
+                stats.substeps += used_o;
+                st = PState{nx, ny, nz};
+                if (jstar_o >= 0) {
+                    const uint32_t kk = k + used_o;
+                    const ftime t_after = (kk == pl.N) ? ftime{0.0f, 0.0f}
+                                                       : time_sub_mul(t_rem, kk, pl.h);
+                    removed = apply_event(P, S, SP, ctl, i, id, photon, nxd, neps, nchi, step,
+                                          s + (uint32_t)jstar_o, t_after, st, stats, true, false, F,
+                                          false);
+                    s += used_o;
+                    t_rem = t_after;
+                    if (removed || !time_positive(t_rem)) done = true;
+                    else need_plan = true;
+                } else {
+                    s += used_o;
+                    k += used_o;
+                    if (k == pl.N) done = true;
+                }
+            }
+        } else if (busy && need_plan) {
+            done = plan_now();
+        } else if (busy) {
             float b = pl.b, c_h = pl.c_h, chi_k = chi, eps_k = eps;
             uint32_t T = pl.T;
             if (!photon) {
