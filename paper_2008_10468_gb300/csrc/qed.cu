@@ -803,15 +803,15 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
         const int m = __popc(bm);
         bool done = false;
         if (drained && m <= kPushGroupMax) {
-            // Group mode: no rows are left and at most kPushGroupMax lanes are
-            // busy.  The g-th busy lane's particle gets lanes [g G, (g+1) G):
+            // Group mode: no rows are left and m <= kPushGroupMax lanes are
+            // busy.  The g-th busy lane's particle gets the G = 32 / m lanes
+            // [g G, (g+1) G):
             // every lane of the group runs the same push chain from the
             // owner's state and keeps the state after push j + 1 (j its place
             // in the group), then tests sub-step s + j; the first accepted
             // sub-step of the group decides, as in the sequential loop.  Only
             // the pushes stay serial.
-            const int groups = m == 1 ? 1 : (m == 2 ? 2 : (m <= 4 ? 4 : (m <= 8 ? 8 : 16)));
-            const int G = 32 / groups;
+            const int G = 32 / m;
             const int g = lane / G, j = lane - g * G;
             int owner = lane;
             if (g < m) {
