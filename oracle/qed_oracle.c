@@ -232,26 +232,36 @@ void orc_boris64(int charge, double h, double p[3], const double E[3], const dou
     for (int k = 0; k < 3; ++k) p[k] = r[k] + a * E[k];
 }
 
-/* The same step on the binary32 particle state: every operation above in  */
-/* IEEE binary32 with round-to-nearest, in this order (the store holds the */
-/* momentum in binary32, and the state after each sub-step is a binary32   */
-/* value).  Built with -ffp-contract=off, so no two operations fuse.       */
+/* The same step on the binary32 particle state, with t and s written over
+ * one common denominator so that one division serves both:
+ *   u = a B,  g^2 = 1 + |p-|^2,  w = g^2 + |u|^2,  D = g w,
+ *   t = u (w / D) = u / g,        s = u (2 g^2 / D) = 2 t / (1 + |t|^2).
+ * Every operation is IEEE binary32 with round-to-nearest, in this order
+ * (the store holds the momentum in binary32, and the state after each
+ * sub-step is a binary32 value); built with -ffp-contract=off, so no two
+ * operations fuse.  Pinned to the binary64 form above. */
 void orc_boris32(int charge, float h, float p[3], const float E[3], const float B[3]) {
     const float pi = (float)ORC_PI;
     const float ah = pi * h;
     const float a = charge < 0 ? -ah : ah;
-    float m[3], t[3], s[3], q[3], r[3];
+    float m[3], u[3], t[3], s[3], q[3], r[3];
     for (int k = 0; k < 3; ++k) {
         const float kick = a * E[k];
         m[k] = p[k] + kick;
+        u[k] = a * B[k];
     }
     const float m2 = (m[0] * m[0] + m[1] * m[1]) + m[2] * m[2];
-    const float g = sqrtf(1.0f + m2);
-    const float ag = a / g;
-    for (int k = 0; k < 3; ++k) t[k] = ag * B[k];
-    const float t2 = (t[0] * t[0] + t[1] * t[1]) + t[2] * t[2];
-    const float f = 2.0f / (1.0f + t2);
-    for (int k = 0; k < 3; ++k) s[k] = f * t[k];
+    const float u2 = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
+    const float g2 = 1.0f + m2;
+    const float g = sqrtf(g2);
+    const float w = g2 + u2;
+    const float R = 1.0f / (g * w);
+    const float ct = w * R;
+    const float cs = (2.0f * g2) * R;
+    for (int k = 0; k < 3; ++k) {
+        t[k] = ct * u[k];
+        s[k] = cs * u[k];
+    }
     q[0] = m[0] + (m[1] * t[2] - m[2] * t[1]);
     q[1] = m[1] + (m[2] * t[0] - m[0] * t[2]);
     q[2] = m[2] + (m[0] * t[1] - m[1] * t[0]);

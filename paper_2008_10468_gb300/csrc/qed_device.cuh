@@ -155,6 +155,9 @@ __device__ __forceinline__ float chi_any(bool photon, float px, float py, float 
 // a = pi q h for a sub-step h:
 //   p- = p + a E,  t = (a / gamma(p-)) B,  s = 2 t / (1 + t^2),
 //   p+ = p- + (p- + p- x t) x s,  p(h) = p+ + a E.
+// t and s share one denominator: with u = a B, g^2 = 1 + |p-|^2,
+// w = g^2 + |u|^2 and D = g w, t = u (w / D) and s = u (2 g^2 / D), so one
+// division serves both (the push is the serial part of the push-mode step).
 // Each operation is an explicit round-to-nearest binary32 intrinsic, in this
 // order: the result is the IEEE binary32 evaluation of these formulas, not
 // subject to contraction into FMAs.
@@ -163,12 +166,17 @@ __device__ __forceinline__ void boris_push(float& px, float& py, float& pz, floa
     const float mx = __fadd_rn(px, __fmul_rn(a, Ex));
     const float my = __fadd_rn(py, __fmul_rn(a, Ey));
     const float mz = __fadd_rn(pz, __fmul_rn(a, Ez));
+    const float ux = __fmul_rn(a, Bx), uy = __fmul_rn(a, By), uz = __fmul_rn(a, Bz);
     const float m2 = __fadd_rn(__fadd_rn(__fmul_rn(mx, mx), __fmul_rn(my, my)), __fmul_rn(mz, mz));
-    const float ag = __fdiv_rn(a, __fsqrt_rn(__fadd_rn(1.0f, m2)));
-    const float tx = __fmul_rn(ag, Bx), ty = __fmul_rn(ag, By), tz = __fmul_rn(ag, Bz);
-    const float t2 = __fadd_rn(__fadd_rn(__fmul_rn(tx, tx), __fmul_rn(ty, ty)), __fmul_rn(tz, tz));
-    const float f = __fdiv_rn(2.0f, __fadd_rn(1.0f, t2));
-    const float sx = __fmul_rn(f, tx), sy = __fmul_rn(f, ty), sz = __fmul_rn(f, tz);
+    const float u2 = __fadd_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)), __fmul_rn(uz, uz));
+    const float g2 = __fadd_rn(1.0f, m2);
+    const float g = __fsqrt_rn(g2);
+    const float w = __fadd_rn(g2, u2);
+    const float R = __fdiv_rn(1.0f, __fmul_rn(g, w));
+    const float ct = __fmul_rn(w, R);
+    const float cs = __fmul_rn(__fmul_rn(2.0f, g2), R);
+    const float tx = __fmul_rn(ct, ux), ty = __fmul_rn(ct, uy), tz = __fmul_rn(ct, uz);
+    const float sx = __fmul_rn(cs, ux), sy = __fmul_rn(cs, uy), sz = __fmul_rn(cs, uz);
     const float qx = __fadd_rn(mx, __fsub_rn(__fmul_rn(my, tz), __fmul_rn(mz, ty)));
     const float qy = __fadd_rn(my, __fsub_rn(__fmul_rn(mz, tx), __fmul_rn(mx, tz)));
     const float qz = __fadd_rn(mz, __fsub_rn(__fmul_rn(mx, ty), __fmul_rn(my, tx)));

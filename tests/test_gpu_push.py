@@ -142,6 +142,24 @@ def test_push_full_size_sampled():
     assert rep["events"] > 100
 
 
+def test_push_capacity_overflow_reports_required_rows():
+    arr = I.uniform_field_electrons(2000, 20081047)
+    ctx = qed.Context(process_mask=1, cascade=False)
+    store = qed.ParticleStore.from_numpy(arr, capacity=2100)
+    st = ctx.event_step(store, 0, push=True)
+    assert st["status"] == qed.QED_ERR_CAPACITY
+    assert st["required_capacity"] > 2100
+    assert store.n() == 2100
+    # with the cascade on, the generations stop at the overflow
+    store = qed.ParticleStore.from_numpy(arr, capacity=2100)
+    ctx2 = qed.Context(process_mask=3, cascade=True)
+    st = ctx2.event_step(store, 0, push=True)
+    assert st["status"] == qed.QED_ERR_CAPACITY and st["passes"] == 1
+    # the context stays usable after the error
+    store2 = qed.ParticleStore.from_numpy(I.uniform_field_electrons(100, 1), capacity=100000)
+    assert ctx.event_step(store2, 1, push=True)["status"] == 0
+
+
 def test_push_empty_store_and_bad_arguments():
     ctx = qed.Context()
     store = qed.ParticleStore(1024)
