@@ -44,8 +44,8 @@ CASCADE_DRAIN_CHI = 0.05
 # profiled steps; see profiles/hot_pass_traffic_clumped_2p24.md), valid for the
 # kernel sources whose SHA-256 is given; any other source reports traffic as
 # unknown.
-HOT_TRAFFIC = {"bytes_per_launch": 64.38e6,
-               "sources_sha256": "5562e958e45385ad676d0767b3e08ad4d00d3eedcb2072844ffe12e7eda85788"}
+HOT_TRAFFIC = {"bytes_per_launch": 64.37e6,
+               "sources_sha256": "9233e2be1ac5342d0bb3efe96ac74c7ebfe1350ae1232f11ddd52e47d53adc54"}
 
 METRIC = "particle-steps/sec (sub-stepped)"
 UNIT = "substeps/s"

@@ -174,6 +174,18 @@ qed_status qed_synchrotron_generate(qed_ctx* ctx, uint64_t seed, int64_t n, floa
  * whose process is disabled, get N = 0.  Errors: QED_ERR_ARG. */
 qed_status qed_plan(qed_ctx* ctx, const qed_particles* p, int64_t n, float* chi, uint32_t* N);
 
+/* Per-cell planning, the sub-step "for the current cell" of Algorithms 1/2
+ * (Sec. 2.2, first line of each): N_cell[c] = the largest sub-step count N of
+ * qed_plan over the rows i < n with cell[i] == c (0 for a cell without an
+ * active row), so that sub_t = dt / N_cell[c] keeps every particle of the
+ * cell within P_max per sub-step.  cell: device array of n cell indices;
+ * rows with cell[i] >= ncells are left out.  N_cell: device array of ncells
+ * entries, overwritten.  qed_event_step itself plans per particle, a finer
+ * form of the same bound; these counts are for callers that take one
+ * sub-step per cell.  Errors: QED_ERR_ARG, QED_ERR_CUDA. */
+qed_status qed_plan_cells(qed_ctx* ctx, const qed_particles* p, int64_t n, const uint32_t* cell,
+                          int64_t ncells, uint32_t* N_cell);
+
 /* One global step of the event generator (Algorithms 1 and 2) for every row
  * in use.  Each particle is planned, stepped through its sub-steps with
  * Philox4x32-10 draws keyed by (id, step_index, sub-step), emits photons /

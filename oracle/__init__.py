@@ -18,6 +18,8 @@ What it computes (each function cites the passage it follows):
   P_p (Eq. 2 with the bracket sign corrected, Algorithm 2).
 * ``total_per_c``: the per-sub-step event probability divided by c
   (the integral bounded by f(b) in Sec. 3.1.1).
+* ``plan_cells``: the sub-step count per cell of the first line of Algorithms
+  1 and 2 (the largest count of the cell's particles).
 * ``event_step``: Algorithms 1 and 2 for a particle store over one global step,
   optionally with the Boris push of Algorithm 1 before every e+- draw.
 * ``boris64``/``boris32``: that push (the Lorentz force in code units), in
@@ -279,6 +281,29 @@ def plan(cf, p, E, B, t_rem, photon=False):
     N = lib().orc_plan(C.byref(cf), int(photon), *[float(a) for a in (*p, *E, *B)],
                        float(t_rem), C.byref(ch), C.byref(g), C.byref(f))
     return int(N), ch.value, g.value, f.value
+
+
+def plan_cells(cf, arrs, cell, ncells):
+    """Per-cell sub-step counts, the sub-step "for the current cell" of the
+    first line of Algorithms 1 and 2: for each cell the largest planned N
+    (``plan`` over a full global step) of its rows whose process is enabled
+    (0 for a cell without one).  Rows with a cell index >= ncells are left out."""
+    out = np.zeros(int(ncells), dtype=np.int64)
+    for i in range(len(arrs["px"])):
+        t = int(arrs["type"][i])
+        c = int(cell[i])
+        if t > 2 or c >= ncells:
+            continue
+        photon = t == 2
+        if not (cf.process_mask & (2 if photon else 1)):
+            continue
+        p = (arrs["px"][i], arrs["py"][i], arrs["pz"][i])
+        if photon and not any(float(v) != 0.0 for v in p):
+            continue   # a photon without momentum has no plan
+        N, _, _, _ = plan(cf, p, (arrs["Ex"][i], arrs["Ey"][i], arrs["Ez"][i]),
+                          (arrs["Bx"][i], arrs["By"][i], arrs["Bz"][i]), cf.dt, photon=photon)
+        out[c] = max(out[c], N)
+    return out
 
 
 def _store(arrs, capacity):

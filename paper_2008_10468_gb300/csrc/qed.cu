@@ -251,8 +251,14 @@ __global__ void __launch_bounds__(kSweepThreads) k_generate(uint32_t k0, uint32_
 // ---------------------------------------------------------------------------
 // Planner
 // ---------------------------------------------------------------------------
+// cell / N_cell (optional): per-cell planning, Algorithm 1's sub-step "for
+// the current cell": N_cell[c] becomes the largest N of the rows of cell c
+// (N_cell zeroed by the caller; rows whose cell index is >= ncells are left
+// out of it).
 __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParams SP, long long n,
-                                                       float* chi_out, uint32_t* N_out) {
+                                                       float* chi_out, uint32_t* N_out,
+                                                       const uint32_t* __restrict__ cell,
+                                                       long long ncells, unsigned int* N_cell) {
     __shared__ SharedTables sm;
     stage_tables(sm);
     __syncthreads();
@@ -273,6 +279,10 @@ __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParam
         if (active && eps > 0.0f) N = pl.N;
         if (chi_out) chi_out[i] = chi;
         if (N_out) N_out[i] = N;
+        if (N_cell && N > 0u) {
+            const uint32_t c = cell[i];
+            if ((long long)c < ncells) atomicMax(N_cell + c, N);
+        }
     }
 }
 
@@ -2364,8 +2374,28 @@ qed_status qed_plan(qed_ctx* ctx, const qed_particles* p, int64_t n, float* chi,
     long long blocks = (n + kColdThreads - 1) / kColdThreads;
     if (blocks > ctx->cold_blocks) blocks = ctx->cold_blocks;
     LaunchScope ls(ctx, QED_KERNEL_PLAN);
-    k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(to_dev(p), SP, n, chi, N);
+    k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(to_dev(p), SP, n, chi, N, nullptr, 0ll,
+                                                          nullptr);
     return cuda_check(ctx, cudaGetLastError(), "k_plan");
+}
+
+qed_status qed_plan_cells(qed_ctx* ctx, const qed_particles* p, int64_t n, const uint32_t* cell,
+                          int64_t ncells, uint32_t* N_cell) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!particles_ok(p) || n < 0 || n > p->capacity || ncells < 0 || (n > 0 && !cell) ||
+        (ncells > 0 && !N_cell))
+        return set_err(ctx, QED_ERR_ARG, "qed_plan_cells: bad argument");
+    if (ncells == 0) return QED_OK;
+    QED_CUDA(ctx, cudaMemsetAsync(N_cell, 0, sizeof(uint32_t) * (size_t)ncells, ctx->stream));
+    if (n == 0) return QED_OK;
+    const StepParams SP = make_params(ctx->cfg, 0);
+    long long blocks = (n + kColdThreads - 1) / kColdThreads;
+    if (blocks > ctx->cold_blocks) blocks = ctx->cold_blocks;
+    LaunchScope ls(ctx, QED_KERNEL_PLAN);
+    k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(to_dev(p), SP, n, nullptr, nullptr, cell,
+                                                          (long long)ncells,
+                                                          reinterpret_cast<unsigned int*>(N_cell));
+    return cuda_check(ctx, cudaGetLastError(), "k_plan (cells)");
 }
 
 qed_status qed_set_event_log(qed_ctx* ctx, qed_event_record* records, int64_t capacity,

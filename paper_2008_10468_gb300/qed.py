@@ -87,6 +87,8 @@ def lib():
         L.qed_event_step.restype = st
         L.qed_event_step_push.argtypes = [vp, C.POINTER(Particles), u64, C.POINTER(StepStats)]
         L.qed_event_step_push.restype = st
+        L.qed_plan_cells.argtypes = [vp, C.POINTER(Particles), i64, vp, i64, vp]
+        L.qed_plan_cells.restype = st
         L.qed_read_stats.argtypes = [vp, C.POINTER(StepStats)]
         L.qed_read_stats.restype = st
         L.qed_set_event_log.argtypes = [vp, vp, i64, vp]
@@ -271,6 +273,15 @@ class Context:
     def plan(self, store, n, chi=None, N=None):
         p = store.struct()
         self._check(lib().qed_plan(self._h, C.byref(p), int(n), _ptr(chi), _ptr(N)))
+
+    def plan_cells(self, store, n, cell, ncells, N_cell=None):
+        """Per-cell sub-step counts (max of the rows' N per cell); returns N_cell."""
+        if N_cell is None:
+            N_cell = torch.empty(int(ncells), dtype=torch.int32, device=store.device)
+        p = store.struct()
+        self._check(lib().qed_plan_cells(self._h, C.byref(p), int(n), _ptr(cell), int(ncells),
+                                         _ptr(N_cell)))
+        return N_cell
 
     def set_event_log(self, capacity):
         """Record events of later steps into a device log of `capacity` records."""

@@ -167,6 +167,38 @@ def test_plan_parity(workload):
     assert not bad.any(), list(zip(rows[bad][:5], gN[bad][:5], oN[bad][:5]))
 
 
+def test_plan_cells_parity():
+    """Per-cell counts (the sub-step "for the current cell") against the
+    oracle; cells holding a row whose own count is a near-tie are exempt."""
+    n = 40_000
+    arr = I.clumped_mixed(n, 20081049, hot_fraction=0.02)
+    rng = np.random.default_rng(4)
+    ncells = 5000
+    cell = rng.integers(0, ncells + 50, n).astype(np.uint32)   # ~1% out of range
+    ctx = _ctx()
+    store = qed.ParticleStore.from_numpy(arr)
+    cd = torch.from_numpy(cell.view(np.int32)).cuda()
+    g = ctx.plan_cells(store, n, cd, ncells).cpu().numpy().view(np.uint32).astype(np.int64)
+    cf = O.make_config(1, process_mask=3)
+    o = O.plan_cells(cf, arr, cell, ncells)
+    _, _, tie = _oracle_plans(cf, arr, np.arange(n))
+    tied_cells = set(cell[tie].tolist())
+    ok = np.array([c not in tied_cells for c in range(ncells)])
+    print("plan_cells: %d cells, %d exempt, max count %d" % (ncells, (~ok).sum(), o.max()))
+    assert (~ok).sum() < 0.01 * ncells
+    assert np.array_equal(g[ok], o[ok]), np.nonzero((g != o) & ok)[0][:5]
+    # the count of every cell is a multiple-row maximum: check one against qed_plan
+    N = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.plan(store, n, None, N)
+    Nh = N.cpu().numpy().astype(np.int64)
+    c0 = int(cell[0])
+    if c0 < ncells:
+        assert g[c0] == Nh[cell == c0].max()
+    # no rows, no cells
+    assert ctx.plan_cells(store, 0, cd, ncells).sum().item() == 0
+    ctx.plan_cells(store, n, cd, 0)
+
+
 # --------------------------------------------------------------------------
 # Event step (Algorithms 1 and 2)
 # --------------------------------------------------------------------------
