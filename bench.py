@@ -353,6 +353,9 @@ def run_gb300(args):
     # the same step with the Boris push before every e+- draw
     push = None if args.no_push else run_push(store, dev, args, restore, value)
 
+    # per-cell planning over the same store (64 rows per cell)
+    cells = run_plan_cells(ctx, pristine, n, dev, hbm_peak, peak_kind)
+
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -373,6 +376,7 @@ def run_gb300(args):
         "sweep": sweep,
         "sampler": sampler,
         "push": push,
+        "plan_cells": cells,
         "cascade": cascade,
         "e2e": e2e,
         "gpu_launches": launches_timed,
@@ -551,6 +555,38 @@ def run_push(store, dev, args, restore, plain_value):
             "relative_to_step_without_push": value / plain_value,
             "note": "generations launched one by one with CUDA events around each "
                     "launch; no tail pass, no graph"}
+
+
+def run_plan_cells(ctx, store, n, dev, hbm_peak, peak_kind):
+    """qed_plan_cells over the 2^24 store, 64 consecutive rows per cell: rows/s
+    and the pass's algorithmic bytes (the row's 45 B and its 4 B cell index
+    read; the counts are atomics on 256K words) against HBM."""
+    import torch
+    ncells = (n + 63) // 64
+    cell = (torch.arange(n, device=dev, dtype=torch.int64) // 64).to(torch.int32)
+    N_cell = torch.empty(ncells, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        ctx.plan_cells(store, n, cell, ncells, N_cell)
+    reps = 20
+    total = 0.0
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(reps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.plan_cells(store, n, cell, ncells, N_cell)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+    ms = total / reps
+    gbs = 49.0 * n / (ms / 1e3) / 1e9
+    return {"rows": n, "cells": ncells, "ms": ms, "rows_per_s": n / (ms / 1e3),
+            "max_cell_N": int(N_cell.max().item()),
+            "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "peak_kind": peak_kind, "bytes_per_row": 49}}
 
 
 def run_sampler(arr, pristine, store, cap, n, dev, args, restore, plain_value):
