@@ -174,8 +174,8 @@ qed_status qed_synchrotron_generate(qed_ctx* ctx, uint64_t seed, int64_t n, floa
  * whose process is disabled, get N = 0.  Errors: QED_ERR_ARG. */
 qed_status qed_plan(qed_ctx* ctx, const qed_particles* p, int64_t n, float* chi, uint32_t* N);
 
-/* Per-cell planning, the sub-step "for the current cell" of Algorithms 1/2
- * (Sec. 2.2, first line of each): N_cell[c] = the largest sub-step count N of
+/* Per-cell planning (Sec. 2.2: the first line of Algorithms 1 and 2 plans
+ * one sub-step per cell): N_cell[c] = the largest sub-step count N of
  * qed_plan over the rows i < n with cell[i] == c (0 for a cell without an
  * active row), so that sub_t = dt / N_cell[c] keeps every particle of the
  * cell within P_max per sub-step.  cell: device array of n cell indices;
@@ -204,7 +204,7 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
                           qed_step_stats* out);
 
 /* The same step with the Boris push of Algorithm 1 (Sec. 2.2: the particle is
- * propagated by the sub-step with the Boris pusher, then chi is computed and
+ * moved by a Boris step of one sub-step, then chi is recomputed and
  * the draw tested): before every draw an electron or positron moves its
  * momentum by one sub-step h under the Lorentz force of its own constant
  * fields, dp/dt = 2 pi q (E + p x B / gamma) in code units (q = -1 for e-,

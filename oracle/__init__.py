@@ -284,8 +284,8 @@ def plan(cf, p, E, B, t_rem, photon=False):
 
 
 def plan_cells(cf, arrs, cell, ncells):
-    """Per-cell sub-step counts, the sub-step "for the current cell" of the
-    first line of Algorithms 1 and 2: for each cell the largest planned N
+    """Per-cell sub-step counts (the first line of Algorithms 1 and 2 plans one
+    sub-step per cell): for each cell the largest planned N
     (``plan`` over a full global step) of its rows whose process is enabled
     (0 for a cell without one).  Rows with a cell index >= ncells are left out."""
     out = np.zeros(int(ncells), dtype=np.int64)

@@ -168,7 +168,7 @@ def test_plan_parity(workload):
 
 
 def test_plan_cells_parity():
-    """Per-cell counts (the sub-step "for the current cell") against the
+    """Per-cell counts (one sub-step per cell, Algorithms 1 and 2) against the
     oracle; cells holding a row whose own count is a near-tie are exempt."""
     n = 40_000
     arr = I.clumped_mixed(n, 20081049, hot_fraction=0.02)

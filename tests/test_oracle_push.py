@@ -1,6 +1,6 @@
-"""Pins of the oracle's Boris push (Algorithm 1: the particle is propagated by
-each sub-step with the Boris pusher before the draw) and of the push mode of
-its event step.  CPU only.
+"""Pins of the oracle's Boris push (Algorithm 1 moves the momentum by a Boris
+step at the start of every sub-step, before the draw) and of the push mode
+of its event step.  CPU only.
 
 The binary64 push is pinned to the Lorentz force itself: the exact solution
 in a pure electric field, the exact rotation angle and sense in a pure
