@@ -44,8 +44,8 @@ CASCADE_DRAIN_CHI = 0.05
 # profiled steps; see profiles/hot_pass_traffic_clumped_2p24.md), valid for the
 # kernel sources whose SHA-256 is given; any other source reports traffic as
 # unknown.
-HOT_TRAFFIC = {"bytes_per_launch": 64.37e6,
-               "sources_sha256": "9233e2be1ac5342d0bb3efe96ac74c7ebfe1350ae1232f11ddd52e47d53adc54"}
+HOT_TRAFFIC = {"bytes_per_launch": 64.35e6,
+               "sources_sha256": "ca43c6a9f967d2b3695d15613bd9781b29c58accb6da2f06b5913c9a7562696d"}
 
 METRIC = "particle-steps/sec (sub-stepped)"
 UNIT = "substeps/s"
@@ -548,7 +548,29 @@ def run_push(store, dev, args, restore, plain_value):
             a[1] += nl
     ctx.profile(False)
     value = subs / (total_ms / 1e3)
+    # one sub-step per cell (64 consecutive rows per cell), Algorithm 1 as printed
+    restore()
+    n = int(store.count.item())
+    cell = (torch.arange(n, device=store.device, dtype=torch.int64) // 64).to(torch.int32)
+    ncells = (n + 63) // 64
+    c_ms, c_subs = 0.0, 0
+    for k in range(steps):
+        restore()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ctx.event_step_push_cells(store, 2000 + k, cell, ncells)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        c_ms += e0.elapsed_time(e1)
+        c_subs += st["substeps"]
+        if st["status"] != 0:
+            raise SystemExit("push step with cells failed with status %d" % st["status"])
+    cells = {"rows_per_cell": 64, "ms_per_step": c_ms / steps, "substeps_per_step": c_subs / steps,
+             "substeps_per_s": c_subs / (c_ms / 1e3)}
     return {"substeps_per_s": value, "ms_per_step": total_ms / steps, "steps": steps,
+            "with_cells": cells,
             "per_step": {k: v / steps for k, v in agg.items()},
             "substeps_per_step": subs / steps,
             "k_push_ms_per_step": kern.get("hot", [0.0])[0] / steps,

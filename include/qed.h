@@ -220,6 +220,19 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
 qed_status qed_event_step_push(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
                                qed_step_stats* out);
 
+/* The push-mode step with one sub-step per cell, Algorithm 1 as the paper
+ * states it: the counts of qed_plan_cells are taken over the rows in use at
+ * the start of the step (cell: device array with a cell index for each of
+ * them; rows with cell[i] >= ncells keep their own count), and each of those
+ * rows makes its first plan with its cell's count when that is larger than
+ * its own, i.e. with the cell's sub-step dt / N_cell.  Re-plans after events,
+ * and children, plan per particle as in qed_event_step_push.  The context
+ * owns the ncells counts (allocated on first use).  Errors: as
+ * qed_event_step_push; QED_ERR_ARG for a NULL cell or ncells outside
+ * [1, 2^32). */
+qed_status qed_event_step_push_cells(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                                     const uint32_t* cell, int64_t ncells, qed_step_stats* out);
+
 /* Synchronise and read the statistics of the last step.  Errors: ARG, CUDA. */
 qed_status qed_read_stats(qed_ctx* ctx, qed_step_stats* out);
 

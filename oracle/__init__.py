@@ -85,7 +85,8 @@ class Config(C.Structure):
                 ("E_s", C.c_double), ("p_max", C.c_double), ("pair_coeff", C.c_double),
                 ("tie_draw", C.c_double), ("tie_plan", C.c_double),
                 ("process_mask", C.c_uint32), ("cascade", C.c_int32),
-                ("recoil", C.c_int32), ("threads", C.c_int32), ("push", C.c_int32)]
+                ("recoil", C.c_int32), ("threads", C.c_int32), ("push", C.c_int32),
+                ("first_N", C.POINTER(C.c_uint32)), ("first_N_rows", C.c_int64)]
 
 
 class Particles(C.Structure):
@@ -332,8 +333,12 @@ def _stats_dict(st):
     return {k: int(getattr(st, k)) for k, _ in Stats._fields_}
 
 
-def event_step(cf, arrs, step, capacity=None, log=True):
+def event_step(cf, arrs, step, capacity=None, log=True, first_N=None):
     """One global step of Algorithms 1 and 2 on a copy of `arrs`.
+
+    first_N (optional, one count per row of `arrs`): the first plan of each
+    of these rows takes at least this many sub-steps (one sub-step per cell:
+    pass each row its cell's ``plan_cells`` count).
 
     Returns (arrays, stats, events, ties): arrays truncated to the final count,
     stats as a dict, events as a structured array (parent_id, child0, child1,
@@ -345,6 +350,14 @@ def event_step(cf, arrs, step, capacity=None, log=True):
     out, P = _store(arrs, capacity)
     st = Stats()
     L = Log()
+    fN = None
+    if first_N is not None:
+        fN = np.ascontiguousarray(first_N, dtype=np.uint32)
+        cf.first_N = fN.ctypes.data_as(C.POINTER(C.c_uint32))
+        cf.first_N_rows = len(fN)
+    else:
+        cf.first_N = None
+        cf.first_N_rows = 0
     if log:
         lib().orc_event_step(C.byref(cf), C.byref(P), int(step), C.byref(st), C.byref(L))
     else:

@@ -379,6 +379,8 @@ typedef struct {
     int32_t recoil;       /* 0: events leave the parent unchanged (test) */
     int32_t threads;
     int32_t push;         /* 1: Boris push of e+- before every sub-step's draw */
+    const uint32_t* first_N;  /* optional: at least this count for the first plan */
+    int64_t first_N_rows;     /* ... of rows [0, first_N_rows) (one sub-step per cell) */
 } orc_config;
 
 typedef struct {
@@ -505,10 +507,8 @@ static void process_particle(const orc_config* cf, orc_particles* P, int64_t i, 
         double c_rem = k_sqrt3_pi * cf->R * t_rem / gamma;
         int guard = 0;
         uint32_t N = plan_count(cf, is_photon, b, c_rem, 1.0, 1.0, &guard);
-        st->plans++;
-        if (guard) st->guard_hits++;
-        if (N > st->max_N) st->max_N = N;
         if (!tied) {
+            /* a near-tie of the particle's own count */
             double eps = cf->tie_plan;
             uint32_t lo = plan_count(cf, is_photon, b, c_rem, 1.0 - eps, 1.0 - eps, NULL);
             uint32_t hi = plan_count(cf, is_photon, b, c_rem, 1.0 + eps, 1.0 + eps, NULL);
@@ -516,6 +516,14 @@ static void process_particle(const orc_config* cf, orc_particles* P, int64_t i, 
             uint32_t hi2 = plan_count(cf, is_photon, b, c_rem, 1.0 - eps, 1.0 + eps, NULL);
             if (lo != N || hi != N || lo2 != N || hi2 != N) { tied = 1; log_tie(L, id, s, 2); }
         }
+        /* one sub-step per cell (first line of Algorithms 1/2): an initial
+         * row's first plan takes its cell's count when that is larger (a
+         * near-tie of the cell's count is the caller's to flag) */
+        if (cf->first_N && s == 0 && i < cf->first_N_rows && cf->first_N[i] > N)
+            N = cf->first_N[i];
+        st->plans++;
+        if (guard) st->guard_hits++;
+        if (N > st->max_N) st->max_N = N;
         double h = t_rem / (double)N;
         double c_h = k_sqrt3_pi * cf->R * h / gamma;
         int event = 0;

@@ -92,6 +92,7 @@ struct DevCtl {
                                     // after the thread pass's hot_tail entries
     int skip;                       // the tail pass does nothing
     unsigned long long push_head;   // push mode: next row of the generation to take
+    long long n_init;               // rows at the start of the step (the rest are children)
 };
 
 // Type byte of a child row that has been reserved but not yet written: in the
@@ -258,10 +259,12 @@ __global__ void __launch_bounds__(kSweepThreads) k_generate(uint32_t k0, uint32_
 __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParams SP, long long n,
                                                        float* chi_out, uint32_t* N_out,
                                                        const uint32_t* __restrict__ cell,
-                                                       long long ncells, unsigned int* N_cell) {
+                                                       long long ncells, unsigned int* N_cell,
+                                                       const long long* n_dev) {
     __shared__ SharedTables sm;
     stage_tables(sm);
     __syncthreads();
+    if (n_dev && *n_dev < n) n = *n_dev;   // rows in use (the store's count)
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint8_t type = P.type[i];
@@ -734,6 +737,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
     const bool first_pass = ctl->first_pass != 0;
     const long long begin = first_pass ? 0 : ctl->pass_begin;
     const long long n = ctl->pass_end - begin;
+    const long long n_init = ctl->n_init;
     constexpr unsigned int kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
@@ -796,6 +800,20 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
             pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, F.Ex, F.Ey,
                                F.Ez, F.Bx, F.By, F.Bz, t_rem, &chi, &eps);
             if (!(eps > 0.0f)) return true;
+            if (SP.N_cell && s == 0u && i < n_init) {
+                // per-cell counts: an initial row's first plan takes its
+                // cell's count when that is larger (the cell's sub-step)
+                const uint32_t c = SP.cell[i];
+                const uint32_t Nc = (long long)c < SP.ncells ? SP.N_cell[c] : 0u;
+                if (Nc > pl.N) {
+                    pl.N = Nc;
+                    pl.h = time_div(t_rem, Nc);
+                    pl.c_h = PC.K * pl.h.hi * __fdividef(1.0f, eps);
+                    const float b23 = pl.b > 0.0f ? exp2f(__log2f(pl.b) * (2.0f / 3.0f)) : 0.0f;
+                    pl.T = squeeze_threshold(
+                        squeeze_bound(sm.sqz_e, sm.sqz_p, photon, pl.b, pl.c_h, b23));
+                }
+            }
             stats.plans++;
             stats.guard += pl.guard ? 1 : 0;
             stats.max_N = max(stats.max_N, pl.N);
@@ -1672,6 +1690,7 @@ __global__ void k_step_init(DevCtl* ctl, long long* count, long long capacity, i
     *count = n;
     c.pass_begin = 0;
     c.pass_end = sticky ? 0 : n;
+    c.n_init = n;
     c.first_pass = 1;
     c.sticky = sticky;
     c.status = sticky;
@@ -1987,6 +2006,8 @@ struct qed_ctx {
     long long tail_rows;        // cascade generations below this size go to the tail pass
     int step_blocks, step_net_blocks;   // resident blocks of the tail pass's kernel
     int push_blocks;            // resident blocks of the push-mode kernel
+    unsigned int* d_Ncell;      // per-cell counts of the push mode with cells
+    long long ncell_cap;
     // compaction
     Mirror mirror;
     long long mirror_cap;
@@ -2077,6 +2098,9 @@ StepParams make_params(const qed_config& c, uint64_t step) {
     P.process_mask = c.process_mask;
     P.recoil = c.recoil;
     P.cascade = c.cascade_in_step;
+    P.cell = nullptr;
+    P.N_cell = nullptr;
+    P.ncells = 0;
     return P;
 }
 
@@ -2310,6 +2334,7 @@ qed_status qed_destroy(qed_ctx* ctx) {
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     if (ctx->d_trem) cudaFree(ctx->d_trem);
     if (ctx->d_hot) cudaFree(ctx->d_hot);
+    if (ctx->d_Ncell) cudaFree(ctx->d_Ncell);
     free_graph(ctx);
     float* f[] = {ctx->mirror.px, ctx->mirror.py, ctx->mirror.pz, ctx->mirror.Ex, ctx->mirror.Ey,
                   ctx->mirror.Ez, ctx->mirror.Bx, ctx->mirror.By, ctx->mirror.Bz, ctx->mirror.w};
@@ -2375,7 +2400,7 @@ qed_status qed_plan(qed_ctx* ctx, const qed_particles* p, int64_t n, float* chi,
     if (blocks > ctx->cold_blocks) blocks = ctx->cold_blocks;
     LaunchScope ls(ctx, QED_KERNEL_PLAN);
     k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(to_dev(p), SP, n, chi, N, nullptr, 0ll,
-                                                          nullptr);
+                                                          nullptr, nullptr);
     return cuda_check(ctx, cudaGetLastError(), "k_plan");
 }
 
@@ -2394,7 +2419,8 @@ qed_status qed_plan_cells(qed_ctx* ctx, const qed_particles* p, int64_t n, const
     LaunchScope ls(ctx, QED_KERNEL_PLAN);
     k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(to_dev(p), SP, n, nullptr, nullptr, cell,
                                                           (long long)ncells,
-                                                          reinterpret_cast<unsigned int*>(N_cell));
+                                                          reinterpret_cast<unsigned int*>(N_cell),
+                                                          nullptr);
     return cuda_check(ctx, cudaGetLastError(), "k_plan (cells)");
 }
 
@@ -2500,17 +2526,39 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
     return QED_OK;
 }
 
-qed_status qed_event_step_push(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
-                               qed_step_stats* out) {
-    if (!ctx) return QED_ERR_ARG;
-    if (!particles_ok(p) || step_index > 0xffffffffull)
-        return set_err(ctx, QED_ERR_ARG, "qed_event_step_push: bad argument");
+}  // extern "C"
+static qed_status push_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                            qed_step_stats* out, const uint32_t* cell, int64_t ncells) {
     qed_status st = ensure_scratch(ctx, p->capacity);
     if (st != QED_OK) return st;
-    const StepParams SP = make_params(ctx->cfg, step_index);   // the sampler is not used
+    StepParams SP = make_params(ctx->cfg, step_index);   // the sampler is not used
     const DevParticles D = to_dev(p);
     const Scratch S = make_scratch(ctx);
     const bool cascade = cascade_enabled(ctx->cfg);
+    if (cell && ncells > 0) {
+        // the cells' counts over the rows in use, before the step changes them
+        if (ncells > ctx->ncell_cap) {
+            if (ctx->d_Ncell) cudaFree(ctx->d_Ncell);
+            ctx->d_Ncell = nullptr;
+            ctx->ncell_cap = 0;
+            QED_CUDA(ctx, cudaMalloc(&ctx->d_Ncell, sizeof(unsigned int) * (size_t)ncells));
+            ctx->ncell_cap = ncells;
+        }
+        QED_CUDA(ctx, cudaMemsetAsync(ctx->d_Ncell, 0, sizeof(unsigned int) * (size_t)ncells,
+                                      ctx->stream));
+        long long blocks = (p->capacity + kColdThreads - 1) / kColdThreads;
+        if (blocks > ctx->cold_blocks) blocks = ctx->cold_blocks;
+        {
+            LaunchScope ls(ctx, QED_KERNEL_PLAN);
+            k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(
+                D, SP, D.capacity, nullptr, nullptr, cell, (long long)ncells, ctx->d_Ncell,
+                D.count);
+        }
+        QED_CUDA(ctx, cudaGetLastError());
+        SP.cell = cell;
+        SP.N_cell = ctx->d_Ncell;
+        SP.ncells = ncells;
+    }
     {
         LaunchScope ls(ctx, QED_KERNEL_CONTROL);
         k_step_init<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, 0);
@@ -2537,6 +2585,24 @@ qed_status qed_event_step_push(qed_ctx* ctx, const qed_particles* p, uint64_t st
     }
     if (out) return qed_read_stats(ctx, out);
     return QED_OK;
+}
+extern "C" {
+
+qed_status qed_event_step_push(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                               qed_step_stats* out) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!particles_ok(p) || step_index > 0xffffffffull)
+        return set_err(ctx, QED_ERR_ARG, "qed_event_step_push: bad argument");
+    return push_step(ctx, p, step_index, out, nullptr, 0);
+}
+
+qed_status qed_event_step_push_cells(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                                     const uint32_t* cell, int64_t ncells, qed_step_stats* out) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!particles_ok(p) || step_index > 0xffffffffull || !cell || ncells <= 0 ||
+        ncells > 0xffffffffll)
+        return set_err(ctx, QED_ERR_ARG, "qed_event_step_push_cells: bad argument");
+    return push_step(ctx, p, step_index, out, cell, ncells);
 }
 
 qed_status qed_read_stats(qed_ctx* ctx, qed_step_stats* out) {

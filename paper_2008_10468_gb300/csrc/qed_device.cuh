@@ -340,6 +340,9 @@ struct StepParams {
     uint32_t process_mask;
     int recoil;
     int cascade;
+    const uint32_t* cell;        // push mode with per-cell counts: cell of each initial row
+    const unsigned int* N_cell;  // ... and the count of each cell (NULL: per-particle plans)
+    long long ncells;
 };
 
 // Squeeze: an upper bound of the acceptance function over all x, from the

@@ -89,6 +89,9 @@ def lib():
         L.qed_event_step_push.restype = st
         L.qed_plan_cells.argtypes = [vp, C.POINTER(Particles), i64, vp, i64, vp]
         L.qed_plan_cells.restype = st
+        L.qed_event_step_push_cells.argtypes = [vp, C.POINTER(Particles), u64, vp, i64,
+                                                C.POINTER(StepStats)]
+        L.qed_event_step_push_cells.restype = st
         L.qed_read_stats.argtypes = [vp, C.POINTER(StepStats)]
         L.qed_read_stats.restype = st
         L.qed_set_event_log.argtypes = [vp, vp, i64, vp]
@@ -314,6 +317,17 @@ class Context:
             return stats_dict(s)
         self._check(fn(self._h, C.byref(p), int(step), None))
         return None
+
+    def event_step_push_cells(self, store, step, cell, ncells):
+        """Push-mode step with one sub-step per cell (cell: int32 CUDA tensor of
+        a cell index per row in use); returns the statistics dict."""
+        p = store.struct()
+        s = StepStats()
+        st = lib().qed_event_step_push_cells(self._h, C.byref(p), int(step), _ptr(cell),
+                                             int(ncells), C.byref(s))
+        if st not in (QED_OK, QED_ERR_CAPACITY):
+            self._check(st)
+        return stats_dict(s)
 
     def compact(self, store):
         """Squeeze removed rows out of the store; returns the rows removed."""

@@ -167,3 +167,65 @@ def test_push_empty_store_and_bad_arguments():
     assert st["status"] == 0 and st["substeps"] == 0
     with pytest.raises(qed.QEDError):
         ctx.event_step(store, 1 << 33, push=True)
+
+
+def _cells_check(arr, cell, ncells, seed, step=0, cap_mult=20):
+    n = len(arr["px"])
+    ctx = qed.Context(seed=seed, process_mask=3, cascade=True)
+    ctx.set_event_log(1 << 20)
+    store = qed.ParticleStore.from_numpy(arr, capacity=n * cap_mult)
+    cd = torch.from_numpy(cell.astype(np.uint32).view(np.int32)).cuda()
+    g_st = ctx.event_step_push_cells(store, step, cd, ncells)
+    g_ev, _ = ctx.read_event_log()
+    g_store = store.to_numpy()
+    cf = O.make_config(seed, process_mask=3, cascade=1, push=1)
+    Nc = O.plan_cells(cf, arr, cell, ncells)
+    first = np.where(cell < ncells, Nc[np.minimum(cell, ncells - 1)], 0)
+    o_store, o_st, o_ev, o_ties = O.event_step(cf, arr, step, capacity=n * cap_mult,
+                                               first_N=first)
+    # a cell whose count may differ (a member's own count is a near-tie) is
+    # exempt as a whole: its rows are marked tied from their first sub-step
+    from tests.test_gpu_parity import _oracle_plans
+    _, _, tie = _oracle_plans(cf, arr, np.arange(n))
+    bad_cells = set(cell[tie].tolist())
+    extra = [(int(arr["id"][i]), 0, 2) for i in range(n) if int(cell[i]) in bad_cells]
+    ties = np.concatenate([o_ties, np.array(extra, dtype=o_ties.dtype)]) if extra else o_ties
+    rep = parity.compare(g_ev, o_ev, ties, g_store, o_store, arr["id"])
+    print("push cells parity:", {k: v for k, v in rep.items() if k != "mismatches"},
+          "gpu", g_st, "oracle", o_st)
+    assert g_st["status"] == 0 and o_st["status"] == 0
+    assert not rep["mismatches"], rep["mismatches"][:5]
+    assert rep["final_checked"] > 0.5 * rep["particles"]
+    return g_st, o_st
+
+
+def test_push_cells_parity():
+    arr = I.clumped_mixed(4133, 20081049, hot_fraction=0.02)
+    cell = (np.arange(4133) // 16).astype(np.uint32)
+    cell[::97] = 10 ** 6    # out of range: these rows keep their own count
+    g_st, o_st = _cells_check(arr, cell, (4133 + 15) // 16, 20081049, step=3)
+    plain = qed.Context(seed=20081049, process_mask=3, cascade=True)
+    store = qed.ParticleStore.from_numpy(arr, capacity=4133 * 20)
+    assert g_st["substeps"] > plain.event_step(store, 3, push=True)["substeps"]
+
+
+def test_push_one_row_per_cell_is_the_push_step():
+    arr = I.clumped_mixed(2000, 31, hot_fraction=0.05)
+    n = 2000
+    a_ctx = qed.Context(seed=9, process_mask=3, cascade=True)
+    b_ctx = qed.Context(seed=9, process_mask=3, cascade=True)
+    a = qed.ParticleStore.from_numpy(arr, capacity=n * 20)
+    b = qed.ParticleStore.from_numpy(arr, capacity=n * 20)
+    sa = a_ctx.event_step(a, 1, push=True)
+    cd = torch.arange(n, dtype=torch.int32, device="cuda")
+    sb = b_ctx.event_step_push_cells(b, 1, cd, n)
+    for k in ("substeps", "emissions", "pairs", "children", "plans", "count", "status"):
+        assert sa[k] == sb[k], k
+    # initial rows in place; children (appended in reservation order) by id
+    A, B = a.to_numpy(), b.to_numpy()
+    ia, ib = np.argsort(A["id"][n:]), np.argsort(B["id"][n:])
+    for k in A:
+        assert np.array_equal(A[k][:n], B[k][:n]), k
+        assert np.array_equal(A[k][n:][ia], B[k][n:][ib]), k
+    with pytest.raises(qed.QEDError):
+        b_ctx.event_step_push_cells(b, 1, cd, 0)
