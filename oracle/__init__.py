@@ -358,10 +358,15 @@ def event_step(cf, arrs, step, capacity=None, log=True, first_N=None):
     else:
         cf.first_N = None
         cf.first_N_rows = 0
-    if log:
-        lib().orc_event_step(C.byref(cf), C.byref(P), int(step), C.byref(st), C.byref(L))
-    else:
-        lib().orc_event_step(C.byref(cf), C.byref(P), int(step), C.byref(st), None)
+    try:
+        if log:
+            lib().orc_event_step(C.byref(cf), C.byref(P), int(step), C.byref(st), C.byref(L))
+        else:
+            lib().orc_event_step(C.byref(cf), C.byref(P), int(step), C.byref(st), None)
+    finally:
+        # the counts live only for this call
+        cf.first_N = None
+        cf.first_N_rows = 0
     cnt = int(P.count)
     res = {k: v[:cnt].copy() for k, v in out.items()}
     ev_dt = np.dtype([("parent_id", np.uint64), ("child0", np.uint64), ("child1", np.uint64),
