@@ -203,3 +203,21 @@ def test_push_moves_the_momentum_by_the_lorentz_force():
 
 def arr_p(arr, j):
     return np.array([arr[k][j] for k in ("px", "py", "pz")], np.float32)
+
+
+@pytest.mark.parametrize("charge", [-1, 1])
+def test_crossed_fields_drift_at_e_cross_b(charge):
+    # |E| < |B|, E perpendicular to B: the velocity averaged over many
+    # gyrations is the drift E x B / B^2, whatever the charge (a kick with the
+    # wrong sign relative to the rotation would reverse or spoil it)
+    E = np.array([0.0, 150.0, 0.0])
+    B = np.array([0.0, 0.0, 300.0])
+    h, n = 2e-5, 40000
+    p = np.array([0.0, 0.0, 0.0])
+    v = np.zeros(3)
+    for _ in range(n):
+        p = O.boris64(charge, h, p, E, B)
+        v += p / math.sqrt(1.0 + p @ p)
+    v /= n
+    drift = np.cross(E, B) / (B @ B)
+    np.testing.assert_allclose(v, drift, atol=2e-3)
