@@ -12,7 +12,8 @@ HEADER = os.path.join(ROOT, "include", "qed.h")
 
 
 def _declared():
-    text = open(HEADER).read()
+    with open(HEADER) as f:
+        text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(qed_[A-Za-z0-9_]+)\s*\(", text)))
 

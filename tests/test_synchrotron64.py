@@ -35,7 +35,8 @@ def _sample(n, seed, lo=1e-7, hi=100.0):
 
 
 def _table():
-    txt = open(HEADER).read()
+    with open(HEADER) as f:
+        txt = f.read()
 
     def block(name):
         body = re.search(name + r"\[[^=]*=\s*\{(.*?)\n\};", txt, re.S).group(1)
