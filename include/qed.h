@@ -356,6 +356,17 @@ qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, uint32_t long_min,
  * Errors: QED_ERR_ARG (ctx null, tail_rows < 0). */
 qed_status qed_set_tail(qed_ctx* ctx, int64_t tail_rows);
 
+/* Longest bounded wait of the tail pass, in nanoseconds (0: the default,
+ * 1 s).  The persistent kernel of the tail pass waits for child rows that
+ * another warp is still writing and for queue entries not yet pushed, and
+ * its idle warps wait for new work; a warp that has waited this long in
+ * total without progress gives up, and the step ends with QED_ERR_TIMEOUT
+ * (in the statistics and as the return value when they are read) instead of
+ * hanging; the context stays usable.  A short limit makes idle warps give
+ * up early, so it is for tests of that path.  Applies to later steps and
+ * graph captures.  Errors: QED_ERR_ARG (ctx null). */
+qed_status qed_set_wait_limit(qed_ctx* ctx, uint64_t ns);
+
 /* Time qed_event_step on `p` (step index step_index) for a coordinate search
  * over the launch settings (hot_min 16 ... 256, long_min 128 ... 2048 or
  * never, blocks per SM of each pass, tail_rows 0 or 2^14 ... 2^22), keep the
@@ -393,17 +404,20 @@ qed_status qed_profile_read(qed_ctx* ctx, double* ms, int64_t* launches, int n);
 /* Largest store (rows of capacity) that qed_event_step_noalloc accepts. */
 #define QED_NOALLOC_MAX_ROWS 65536
 
-/* qed_event_step for callers that cannot allocate device memory: code that
- * runs while a CUDA stream is being captured, hosts that hand out a fixed
- * memory budget in advance, and plug-ins living inside another program's
- * memory pool.  No context: the run configuration is passed directly, and the
- * step's scratch (about 2.5 MB) lives in a device array built into this
- * library, which every GPU that loads the library keeps until the process
- * exits.  The paper has no counterpart; this is a packaging of the same step.
+/* qed_event_step for callers that cannot allocate device memory: hosts that
+ * hand each component a fixed memory budget in advance (an allocation of its
+ * own would fail, or take memory promised to another component), and plug-ins
+ * living inside another program's memory pool (which must not go around that
+ * pool to the CUDA allocator).  No context: the run configuration is passed
+ * directly, and the step's scratch (about 2.5 MB) lives in a device array
+ * built into this library, which every GPU that loads the library keeps until
+ * the process exits.  The paper has no counterpart; this is a packaging of
+ * the same step.
  *
- * Same arguments and results as qed_event_step (no event log), on `stream`
- * (a cudaStream_t, NULL: the legacy default stream); synchronises that
- * stream between cascade generations and, if out != NULL, at the end.
+ * Same arguments and results as qed_event_step (no event log, no learned
+ * sampler: cfg->sampler_mode must be 0), on `stream` (a cudaStream_t, NULL:
+ * the legacy default stream); with cfg->cascade_in_step it synchronises that
+ * stream after every cascade generation, and if out != NULL at the end.
  * The first call on a device looks up the array and the launch geometry with
  * that device current (make that first call before any stream capture);
  * later calls on the device reuse them.  The array is shared by every call
@@ -411,8 +425,9 @@ qed_status qed_profile_read(qed_ctx* ctx, double* ms, int64_t* launches, int n);
  * it reads, but calls whose work overlaps on the GPU (other streams, other
  * host threads) race with each other; serialise them.
  * Calls no cudaMalloc, cudaFree or allocating library routine.
- * Errors: QED_ERR_ARG (bad argument, or p->capacity > QED_NOALLOC_MAX_ROWS),
- * QED_ERR_CUDA, and the statuses of qed_event_step. */
+ * Errors: QED_ERR_ARG (bad argument, cfg->sampler_mode != 0, or
+ * p->capacity > QED_NOALLOC_MAX_ROWS), QED_ERR_CUDA (the next call on the
+ * device then repeats its set-up), and the statuses of qed_event_step. */
 qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_particles* p,
                                   uint64_t step_index, void* stream, qed_step_stats* out);
 

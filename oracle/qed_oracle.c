@@ -37,8 +37,9 @@
  *   * A validity guard keeps the largest per-sub-step probability (the x->0
  *     limit of 3x^2 P(x^3)) at or below one.
  *
- * Compile with -ffp-contract=off: the time accumulator is compared bit for
- * bit with the GPU path, which evaluates the same IEEE operations.
+ * Compile with -ffp-contract=off, so that every product and sum is rounded
+ * as written.  The remaining time is binary64 here; the CUDA path carries it
+ * as a float-float pair, which agrees with it to about 1e-14 of the step.
  */
 #include <math.h>
 #include <stdint.h>
@@ -277,13 +278,31 @@ void orc_boris32(int charge, float h, float p[3], const float E[3], const float 
 /* ------------------------------------------------------------------------ */
 /* Rate bounds, Sec. 3.1.1.  c = sqrt(3) R t / (pi gamma), b = 3 chi / 2.    */
 /* ------------------------------------------------------------------------ */
+/* The four pieces as printed: coefficient A_k of pi c b^{e_k} and exponent
+ * e_k, plus 0.1 c b on every piece.  The tests may replace them through
+ * orc_set_emission_bound (to check that their pins catch a mistyped value);
+ * nothing else does. */
+static const double ORC_BOUND_A[4] = {0.56, 0.45, 0.42, 0.55};
+static const double ORC_BOUND_E[4] = {1.0, 11.0 / 12.0, 19.0 / 24.0, 2.0 / 3.0};
+static double orc_bound_A[4] = {0.56, 0.45, 0.42, 0.55};
+static double orc_bound_e[4] = {1.0, 11.0 / 12.0, 19.0 / 24.0, 2.0 / 3.0};
+static double orc_bound_lin = 0.1;
+
+/* Test hook: A, e (4 values each) and the linear coefficient; NULL A
+ * restores the printed values. */
+void orc_set_emission_bound(const double* A, const double* e, double lin) {
+    for (int k = 0; k < 4; ++k) {
+        orc_bound_A[k] = A ? A[k] : ORC_BOUND_A[k];
+        orc_bound_e[k] = A ? e[k] : ORC_BOUND_E[k];
+    }
+    orc_bound_lin = A ? lin : 0.1;
+}
+
 double orc_bound_emission(double b, double c) {
-    double lead;
-    if (b < 0.1) lead = 0.56 * ORC_PI * c * b;
-    else if (b < 0.5) lead = 0.45 * ORC_PI * c * pow(b, 11.0 / 12.0);
-    else if (b < 10.0) lead = 0.42 * ORC_PI * c * pow(b, 19.0 / 24.0);
-    else lead = 0.55 * ORC_PI * c * pow(b, 2.0 / 3.0);
-    return lead + 0.1 * c * b;
+    /* pieces [0, 0.1) [0.1, 0.5) [0.5, 10) [10, inf) */
+    int k = b < 0.1 ? 0 : (b < 0.5 ? 1 : (b < 10.0 ? 2 : 3));
+    double lead = orc_bound_A[k] * ORC_PI * c * pow(b, orc_bound_e[k]);   /* pow(b, 1) == b */
+    return lead + orc_bound_lin * c * b;
 }
 
 double orc_bound_pair(double b, double c, double coeff) { return coeff * c * b; }
@@ -372,7 +391,7 @@ typedef struct {
     double E_s;           /* Schwinger field, code units                 */
     double p_max;         /* maximum per-sub-step event probability      */
     double pair_coeff;    /* coefficient of c b in the photon bound      */
-    double tie_draw;      /* |y - P| band that marks a draw as a tie     */
+    double tie_draw;      /* |y - P| <= tie_draw * P marks a draw as a tie */
     double tie_plan;      /* relative band on f/P_max that marks a tie   */
     uint32_t process_mask;/* 1 emission, 2 pair                          */
     int32_t cascade;      /* process children within the step            */
@@ -545,7 +564,7 @@ static void process_particle(const orc_config* cf, orc_particles* P, int64_t i, 
             st->substeps++;
             /* acceptance test */
             double P_acc = is_photon ? orc_Pp(b_k, c_k, x) : orc_Pm(b_k, c_k, x);
-            if (!tied && fabs(y - P_acc) <= cf->tie_draw) { tied = 1; log_tie(L, id, s, 1); }
+            if (!tied && fabs(y - P_acc) <= cf->tie_draw * P_acc) { tied = 1; log_tie(L, id, s, 1); }
             if (y < P_acc) {
                 /* the event closes sub-step k */
                 double t_after = (k + 1 == N) ? 0.0 : t_rem - (double)(k + 1) * h;

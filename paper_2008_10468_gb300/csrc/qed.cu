@@ -43,10 +43,6 @@ using namespace qed;
 
 namespace {
 
-constexpr double kAlpha = 7.2973525643e-3;          // CODATA 2022
-constexpr double kTauC = 1.2880886664441626e-21;    // hbar / (m c^2), s
-constexpr double kCLight = 299792458.0;             // m / s
-constexpr double kPiD = 3.14159265358979323846;
 
 // Defaults measured on the 2^24 clumped population (coordinate search over
 // hot_min 32..128 and long_min 128..2048)
@@ -1334,11 +1330,11 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
 // when they run out of work, so the count is exact whenever the test can
 // succeed.  Idle warps back off (256 ns doubling to 4 us), so that their
 // polls of the control words do not slow the atomics of the busy ones.  Every
-// wait is bounded: past 1 s idle (kIdleNs), or kIdleLimit polls for a queue
-// entry, the kernel records QED_ERR_TIMEOUT and returns.
+// wait is bounded: past SP.wait_ns idle (1 s unless qed_set_wait_limit says
+// otherwise), or as many 64 ns polls for a queue entry, the kernel records
+// QED_ERR_TIMEOUT and returns.
 // ---------------------------------------------------------------------------
-constexpr unsigned int kIdleLimit = 1u << 22;    // polls of ~0.25 us: about 1 s
-constexpr unsigned long long kIdleNs = 1000000000ull;   // idle time before giving up: 1 s
+constexpr unsigned long long kWaitNsDefault = 1000000000ull;   // idle time before giving up: 1 s
 
 __device__ __forceinline__ unsigned long long stored_rows(const DevParticles& P) {
     const long long c = *reinterpret_cast<volatile long long*>(P.count);
@@ -1426,7 +1422,8 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
                 it.idx = kNoItem;
                 if (lane == 0) {
                     const volatile uint32_t* vi = &S.hot[q].idx;
-                    for (unsigned int w = 0; w < kIdleLimit; ++w) {
+                    const unsigned long long polls = SP.wait_ns / 64 + 1;
+                    for (unsigned long long w = 0; w < polls; ++w) {
                         if (*vi != kNoItem) break;
                         __nanosleep(64);
                     }
@@ -1585,7 +1582,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
             const unsigned int nap = hold ? 64u : 256u << min(idle, 4u);
             ++idle;
             idle_ns += nap;
-            if (idle_ns > kIdleNs) {
+            if (idle_ns > SP.wait_ns) {
                 timed_out = true;
                 break;
             }
@@ -2004,6 +2001,7 @@ struct qed_ctx {
     int net_blocks;           // grid of the hot pass in sampler mode
     uint32_t hot_min, long_min;
     long long tail_rows;        // cascade generations below this size go to the tail pass
+    unsigned long long wait_ns; // longest bounded wait of the tail pass
     int step_blocks, step_net_blocks;   // resident blocks of the tail pass's kernel
     int push_blocks;            // resident blocks of the push-mode kernel
     unsigned int* d_Ncell;      // per-cell counts of the push mode with cells
@@ -2076,16 +2074,15 @@ StepParams make_params(const qed_config& c, uint64_t step) {
     StepParams P;
     P.seed = c.seed;
     P.dt = c.dt_periods;
-    const double period = c.lambda_m / kCLight;
-    const double R = kAlpha / kTauC * period;                 // 1 / period
-    P.K = (float)(1.7320508075688772 / kPiD * R);
+    P.K = (float)rate_K64(c.lambda_m);                        // sqrt3 R / pi, 1 / period
     P.t_step.hi = (float)c.dt_periods;
     P.t_step.lo = (float)(c.dt_periods - (double)P.t_step.hi);
-    const double omega = 2.0 * kPiD * kCLight / c.lambda_m;
-    P.inv_Es = (float)(omega * kTauC);                        // 1 / E_s in code units
+    P.inv_Es = (float)inv_schwinger64(c.lambda_m);            // 1 / E_s in code units
     P.p_max = c.p_max;
     P.inv_p_max = 1.0f / c.p_max;
     P.pair_coeff = c.pair_bound_coeff;
+    P.lambda_m = c.lambda_m;
+    P.wait_ns = kWaitNsDefault;
     P.step_base = nullptr;
     P.hot_min = kHotMinDefault;
     P.long_min = kLongMinDefault;
@@ -2313,6 +2310,7 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
         ctx->hot_min = kHotMinDefault;
         ctx->long_min = kLongMinDefault;
         ctx->tail_rows = kTailRowsDefault;
+        ctx->wait_ns = kWaitNsDefault;
         st = cuda_check(ctx, cudaGetLastError(), "occupancy");
     }
     if (st != QED_OK) {
@@ -2450,6 +2448,7 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
     StepParams SP = make_params(ctx->cfg, step_index);
     SP.hot_min = ctx->hot_min;
     SP.long_min = ctx->long_min;
+    SP.wait_ns = ctx->wait_ns;
     st = sampler_params(ctx, &SP);
     if (st != QED_OK) return st;
     const DevParticles D = to_dev(p);
@@ -2775,6 +2774,7 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         SP.step_base = step_base;
         SP.hot_min = ctx->hot_min;
         SP.long_min = ctx->long_min;
+        SP.wait_ns = ctx->wait_ns;
         st = sampler_params(ctx, &SP);
         if (st != QED_OK) break;
         qed_step_stats* rec = ctx->d_records + k;
@@ -2913,7 +2913,8 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
     putf(SPin.t_step.hi); putf(SPin.t_step.lo);
     put(SPin.hot_min); put(SPin.long_min); put((uint64_t)SPin.sampler); put((uint64_t)SPin.net_rows);
     put(SPin.net_bins); putp(SPin.net_w); putp(SPin.net_wtot); put(SPin.process_mask);
-    put((uint64_t)SPin.recoil); put((uint64_t)SPin.cascade);
+    put((uint64_t)SPin.recoil); put((uint64_t)SPin.cascade); put(SPin.wait_ns);
+    { uint64_t b; memcpy(&b, &SPin.lambda_m, 8); put(b); }
     put((uint64_t)ctx->cold_blocks); put((uint64_t)ctx->hot_blocks); put((uint64_t)ctx->net_blocks);
     put((uint64_t)ctx->cfg.max_passes);
     put((uint64_t)ctx->tail_rows); put((uint64_t)ctx->step_blocks); put((uint64_t)ctx->step_net_blocks);
@@ -3328,6 +3329,12 @@ qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, uint32_t long_min,
     return QED_OK;
 }
 
+qed_status qed_set_wait_limit(qed_ctx* ctx, uint64_t ns) {
+    if (!ctx) return QED_ERR_ARG;
+    ctx->wait_ns = ns ? (unsigned long long)ns : kWaitNsDefault;
+    return QED_OK;
+}
+
 qed_status qed_set_tail(qed_ctx* ctx, int64_t tail_rows) {
     if (!ctx || tail_rows < 0) return QED_ERR_ARG;
     ctx->tail_rows = tail_rows;
@@ -3456,16 +3463,16 @@ size_t qed_abi_struct_size(const char* name) {
 // ---------------------------------------------------------------------------
 // Event step without allocation.
 //
-// For callers that may not allocate device memory: code running while a CUDA
-// stream is being captured (an allocation there breaks or invalidates the
-// capture), hosts that hand out a fixed memory budget up front, and plug-ins
-// inside another application's memory pool.  The scratch of the event step
-// (control block, remaining times of children, queue of long sub-step
-// chains) lives in one file-scope device array sized for
-// QED_NOALLOC_MAX_ROWS rows; every GPU that loads this library keeps it
-// until the process exits.  The first call on a device looks up the array's
-// device address (cudaGetSymbolAddress) and the launch geometry with that
-// device current; later calls reuse them.
+// For callers that may not allocate device memory: hosts that hand each
+// component a fixed memory budget up front (a cudaMalloc of their own would
+// fail, or take memory promised to another component), and plug-ins living
+// inside another application's memory pool (which must not go around that
+// pool to the CUDA allocator).  The scratch of the event step (control block,
+// remaining times of children, queue of long sub-step chains) lives in one
+// file-scope device array sized for QED_NOALLOC_MAX_ROWS rows; every GPU that
+// loads this library keeps it until the process exits.  The first call on a
+// device looks up the array's device address (cudaGetSymbolAddress) and the
+// launch geometry with that device current; later calls reuse them.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -3524,6 +3531,15 @@ qed_status noalloc_setup(int dev, NoAllocDevice* out) {
 
 }  // namespace
 
+// After a failed launch the step may not have reached k_tail_end, which puts
+// the long-plan queue entries it used back to "not written"; the next call on
+// the device then clears the whole queue again in its set-up.
+static qed_status noalloc_fail(int dev, qed_status st) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    g_noalloc_dev[dev].ready = 0;
+    return st;
+}
+
 extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_particles* p,
                                              uint64_t step_index, void* stream,
                                              qed_step_stats* out) {
@@ -3532,6 +3548,7 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     if (!(cfg->p_max > 0.0f && cfg->p_max <= 1.0f) || !(cfg->dt_periods > 0.0) ||
         !(cfg->lambda_m > 0.0) || !(cfg->pair_bound_coeff > 0.0f))
         return QED_ERR_ARG;
+    if (cfg->sampler_mode != 0) return QED_ERR_ARG;   // the learned sampler needs a context
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return QED_ERR_CUDA;
     if (dev < 0 || dev >= kNoAllocMaxDevices) return QED_ERR_ARG;
@@ -3560,11 +3577,11 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
         k_hot_lanes<0><<<nd.hot_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
         k_advance<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, cascade ? 1 : 0, max_passes,
                                   kTailRowsDefault, 0ull, 0);
-        if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
+        if (cudaGetLastError() != cudaSuccess) return noalloc_fail(dev, QED_ERR_CUDA);
         if (!cascade) break;
         if (cudaMemcpyAsync(&h, ctl, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
-            return QED_ERR_CUDA;
+            return noalloc_fail(dev, QED_ERR_CUDA);
         if (!h.more) break;
     }
     // the tail pass (its kernels do nothing when the generations ran to the end)
@@ -3572,11 +3589,11 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
     k_step<0><<<nd.step_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
     k_tail_end<<<nd.sms * 8, 256, 0, s>>>(D, S, ctl);
-    if (cudaGetLastError() != cudaSuccess) return QED_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess) return noalloc_fail(dev, QED_ERR_CUDA);
     if (!out) return QED_OK;
     if (cudaMemcpyAsync(&h, ctl, sizeof h, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
-        return QED_ERR_CUDA;
+        return noalloc_fail(dev, QED_ERR_CUDA);
     fill_stats(h, out, h.pass_end);
     return (qed_status)h.status;
 }

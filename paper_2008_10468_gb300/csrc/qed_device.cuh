@@ -96,11 +96,11 @@ __device__ __forceinline__ ff ff_sqrt(ff a) {
 
 // chi = sqrt((eps E + p x B)^2 - (p . E)^2) / E_s with eps = sqrt(1 + p^2)
 // (e+-) or |p| (photon), Sec. 2.2.  The difference of squares cancels for
-// particles co-moving with a crossed field, so every product is kept exact.
-// Returns chi; *eps_out receives eps rounded to binary32.
-__device__ __forceinline__ float chi_ff(bool photon, float px, float py, float pz, float Ex,
-                                        float Ey, float Ez, float Bx, float By, float Bz,
-                                        float inv_Es, float* eps_out) {
+// particles co-moving with a crossed field, so every product is kept exact:
+// chi_sq_ff returns (chi E_s)^2 and eps as float-float pairs.
+__device__ __forceinline__ void chi_sq_ff(bool photon, float px, float py, float pz, float Ex,
+                                          float Ey, float Ez, float Bx, float By, float Bz,
+                                          ff* q_out, ff* eps_out) {
     const ff p2 = ff_add(ff_add(two_prod(px, px), two_prod(py, py)), two_prod(pz, pz));
     const ff g2 = photon ? p2 : ff_add(p2, ff{1.0f, 0.0f});
     const ff eps = ff_sqrt(g2);
@@ -109,7 +109,17 @@ __device__ __forceinline__ float chi_ff(bool photon, float px, float py, float p
     const ff az = ff_add(ff_mul_f(eps, Ez), ff_add(two_prod(px, By), ff_neg(two_prod(py, Bx))));
     const ff pe = ff_add(ff_add(two_prod(px, Ex), two_prod(py, Ey)), two_prod(pz, Ez));
     const ff a2 = ff_add(ff_add(ff_mul(ax, ax), ff_mul(ay, ay)), ff_mul(az, az));
-    const ff q = ff_add(a2, ff_neg(ff_mul(pe, pe)));
+    *q_out = ff_add(a2, ff_neg(ff_mul(pe, pe)));
+    *eps_out = eps;
+}
+
+// chi from chi_sq_ff, rounded to binary32; *eps_out receives eps rounded to
+// binary32.
+__device__ __forceinline__ float chi_ff(bool photon, float px, float py, float pz, float Ex,
+                                        float Ey, float Ez, float Bx, float By, float Bz,
+                                        float inv_Es, float* eps_out) {
+    ff q, eps;
+    chi_sq_ff(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, &q, &eps);
     const float qv = __fadd_rn(q.hi, q.lo);
     *eps_out = __fadd_rn(eps.hi, eps.lo);
     return qv > 0.0f ? __fsqrt_rn(qv) * inv_Es : 0.0f;
@@ -316,8 +326,24 @@ struct Plan {
 // out-of-line slow path takes them in registers (a reference to the kernel's
 // parameter block would make the whole block addressable, i.e. a local copy).
 struct PlanConst {
-    float K, inv_Es, inv_p_max, pair_coeff;
+    float K, inv_Es, inv_p_max, pair_coeff, p_max;
+    double lambda_m;   // laser wavelength (m): the binary64 constants of near-tie plans
 };
+
+// Physical constants (CODATA 2022) and the binary64 forms of K = sqrt3 R / pi
+// and 1 / E_s for wavelength lambda_m, evaluated in the same order on the host
+// and the device.
+constexpr double kAlphaD = 7.2973525643e-3;           // fine-structure constant
+constexpr double kTauCD = 1.2880886664441626e-21;     // hbar / (m c^2), s
+constexpr double kCLightD = 299792458.0;              // m / s
+constexpr double kPiD64 = 3.14159265358979323846;
+__host__ __device__ __forceinline__ double rate_K64(double lambda_m) {
+    const double R = kAlphaD / kTauCD * (lambda_m / kCLightD);   // 1 / period
+    return 1.7320508075688772 / kPiD64 * R;
+}
+__host__ __device__ __forceinline__ double inv_schwinger64(double lambda_m) {
+    return 2.0 * kPiD64 * kCLightD / lambda_m * kTauCD;
+}
 
 struct StepParams {
     uint64_t seed;
@@ -327,6 +353,8 @@ struct StepParams {
     float p_max;
     float inv_p_max;     // 1 / p_max
     float pair_coeff;
+    double lambda_m;     // laser wavelength (m)
+    unsigned long long wait_ns;  // tail pass: longest bounded wait before QED_ERR_TIMEOUT
     ftime t_step;        // dt as float-float
     const uint32_t* step_base;  // graph runs: device step base added to `step`
     uint32_t hot_min;           // plans with at least this many sub-steps go to the hot pass
@@ -381,7 +409,7 @@ __device__ __forceinline__ int emission_piece(float b) {
 // to 1e-5: every f(b) piece grows at most linearly in b, so f moves by less
 // than 2e-5 relative unless b crosses a piece boundary.
 __device__ __forceinline__ PlanConst plan_const(const StepParams& P) {
-    return PlanConst{P.K, P.inv_Es, P.inv_p_max, P.pair_coeff};
+    return PlanConst{P.K, P.inv_Es, P.inv_p_max, P.pair_coeff, P.p_max, P.lambda_m};
 }
 
 __device__ __forceinline__ Plan make_plan(const PlanConst& P, const float* __restrict__ sqz_e,
@@ -425,22 +453,59 @@ __device__ __forceinline__ Plan make_plan(const PlanConst& P, const float* __res
     return pl;
 }
 
-// Slow path of plan_particle: chi in float-float, then the plan.  Kept out of
-// line so that the common path does not carry its registers.
+// f(b) of Sec. 3.1.1 in binary64, in the order the products are written
+// there: A pi c b^e + 0.1 c b.
+__device__ __forceinline__ double bound_emission64(double b, double c) {
+    double lead;
+    if (b < 0.1) lead = 0.56 * 3.14159265358979323846 * c * b;
+    else if (b < 0.5) lead = 0.45 * 3.14159265358979323846 * c * pow(b, 11.0 / 12.0);
+    else if (b < 10.0) lead = 0.42 * 3.14159265358979323846 * c * pow(b, 19.0 / 24.0);
+    else lead = 0.55 * 3.14159265358979323846 * c * pow(b, 2.0 / 3.0);
+    return lead + 0.1 * c * b;
+}
+
+// Slow path of plan_particle, for plans whose binary32 count is not certain
+// (chi ill-conditioned, or f / P_max within 2e-5 of an integer, or b at a
+// piece edge): chi in float-float, then the count N = max(1, ceil(f/P_max),
+// guard) in binary64, so that N is the exact count unless f / P_max lies
+// within ~1e-13 of an integer.  Rare (a few per cent of the longest plans),
+// so its binary64 arithmetic stays off the sub-step path.  Kept out of line
+// so that the common path does not carry its registers.
 __device__ __noinline__ Plan plan_slow(PlanConst P, const float* __restrict__ sqz_e,
                                        const float* __restrict__ sqz_p, bool photon, float px,
                                        float py, float pz, float Ex, float Ey, float Ez, float Bx,
                                        float By, float Bz, ftime T) {
-    float eps;
-    const float chi = chi_ff(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps);
-    if (!(eps > 0.0f)) {
-        Plan pl;
+    ff q2, epsf;
+    chi_sq_ff(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, &q2, &epsf);
+    const double q2d = (double)q2.hi + (double)q2.lo;
+    const double chi_d = q2d > 0.0 ? sqrt(q2d) * inv_schwinger64(P.lambda_m) : 0.0;
+    const double eps_d = (double)epsf.hi + (double)epsf.lo;
+    Plan pl;
+    pl.chi = (float)chi_d;
+    pl.eps = (float)eps_d;
+    if (!(pl.eps > 0.0f)) {
         pl.N = 0;
-        pl.chi = chi;
-        pl.eps = eps;
         return pl;
     }
-    return make_plan(P, sqz_e, sqz_p, photon, chi, eps, T);
+    const double b = 1.5 * chi_d;
+    const double c_rem = rate_K64(P.lambda_m) * ((double)T.hi + (double)T.lo) / eps_d;  // hi + lo exact
+    const double f = photon ? (double)P.pair_coeff * c_rem * b
+                            : (b > 0.0 ? bound_emission64(b, c_rem) : 0.0);
+    double N = fmax(1.0, ceil(f / (double)P.p_max));
+    pl.guard = false;
+    if (!photon && b > 0.0) {
+        const double g = ceil(2.14952824153447863 * c_rem * pow(b, 2.0 / 3.0));
+        if (g > N) { N = g; pl.guard = true; }
+    }
+    N = fmin(N, 1073741824.0);   // 2^30
+    pl.N = (uint32_t)N;
+    pl.safe = true;
+    pl.b = 1.5f * pl.chi;
+    pl.h = time_div(T, pl.N);
+    pl.c_h = P.K * pl.h.hi * __fdividef(1.0f, pl.eps);
+    const float b23 = pl.b > 0.0f ? exp2f(__log2f(pl.b) * (2.0f / 3.0f)) : 0.0f;
+    pl.T = squeeze_threshold(squeeze_bound(sqz_e, sqz_p, photon, pl.b, pl.c_h, b23));
+    return pl;
 }
 
 // chi and the plan of a particle: binary32 chi when it is well conditioned and

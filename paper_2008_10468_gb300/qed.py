@@ -123,6 +123,8 @@ def lib():
         L.qed_set_launch.restype = st
         L.qed_set_tail.argtypes = [vp, C.c_int64]
         L.qed_set_tail.restype = st
+        L.qed_set_wait_limit.argtypes = [vp, u64]
+        L.qed_set_wait_limit.restype = st
         L.qed_autotune.argtypes = [vp, C.POINTER(Particles), u64, C.c_char_p]
         L.qed_autotune.restype = st
         L.qed_profile_enable.argtypes = [vp, C.c_int]
@@ -312,7 +314,7 @@ class Context:
         if sync:
             s = StepStats()
             st = fn(self._h, C.byref(p), int(step), C.byref(s))
-            if st not in (QED_OK, QED_ERR_CAPACITY):
+            if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_TIMEOUT):   # step outcomes
                 self._check(st)
             return stats_dict(s)
         self._check(fn(self._h, C.byref(p), int(step), None))
@@ -325,7 +327,7 @@ class Context:
         s = StepStats()
         st = lib().qed_event_step_push_cells(self._h, C.byref(p), int(step), _ptr(cell),
                                              int(ncells), C.byref(s))
-        if st not in (QED_OK, QED_ERR_CAPACITY):
+        if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_TIMEOUT):   # step outcomes
             self._check(st)
         return stats_dict(s)
 
@@ -356,7 +358,7 @@ class Context:
         n = self._graph_steps
         out = (StepStats * n)()
         st = lib().qed_graph_read_stats(self._h, out, n)
-        if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_STATE):
+        if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_TIMEOUT, QED_ERR_STATE):
             self._check(st)
         return [stats_dict(out[k]) for k in range(n)]
 
@@ -399,6 +401,10 @@ class Context:
         """Generations below tail_rows rows go to the tail pass (0: off)."""
         self._check(lib().qed_set_tail(self._h, int(tail_rows)))
 
+    def set_wait_limit(self, ns):
+        """Longest bounded wait of the tail pass in ns (0: the 1 s default)."""
+        self._check(lib().qed_set_wait_limit(self._h, int(ns)))
+
     def autotune(self, store, step, out_json=None):
         """Pick the fastest launch settings for `store` (left unchanged)."""
         p = store.struct()
@@ -418,6 +424,6 @@ class Context:
     def read_stats(self):
         s = StepStats()
         st = lib().qed_read_stats(self._h, C.byref(s))
-        if st not in (QED_OK, QED_ERR_CAPACITY):
+        if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_TIMEOUT):   # step outcomes
             self._check(st)
         return stats_dict(s)

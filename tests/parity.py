@@ -3,9 +3,10 @@
 Protocol:
   * Each particle's events (sub-step index s, kind, child ids) must be
     identical on both sides, up to the particle's first near-tie recorded by
-    the oracle: a draw with |y - P| <= 1e-5, or a plan whose sub-step count
-    flips inside the relative band of oracle.TIE_PLAN.  From that sub-step on
-    the particle (and any child created there or later) is exempt.
+    the oracle: a draw with |y - P| <= oracle.TIE_DRAW * P, or a plan whose
+    sub-step count flips inside the relative band of oracle.TIE_PLAN.  From
+    that sub-step on the particle (and any child created there or later) is
+    exempt.
   * Energy fractions agree to `delta_rtol` (binary32 x^3 against FP64).
   * Particles with no near-tie end in the same state: same type, momentum
     within `p_rtol` of |p|.

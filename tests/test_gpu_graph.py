@@ -247,3 +247,38 @@ def test_capacity_overflow_in_the_cascade(tail):
     assert store.n() == cap and st["count"] == cap
     if tail:
         assert st["tail"] == 1
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_tail_pass_wait_limit_ends_the_step_with_timeout(graph):
+    # failure detection without a fault: every wait of the tail pass is
+    # bounded.  With a limit of 1 ns the persistent kernel's warps give up at
+    # their first idle poll, so the step ends with QED_ERR_TIMEOUT instead of
+    # waiting; in a multi-step graph the following steps do nothing.  Back at
+    # the default limit the context steps as a fresh one does.
+    n = 4000
+    arr = I.clumped_mixed(n, 51, hot_fraction=0.05)
+    ctx = qed.Context(seed=3)
+    ctx.set_wait_limit(1)
+    store = qed.ParticleStore.from_numpy(arr, capacity=n * 60)
+    if graph:
+        ctx.graph_capture(store, 9, 2)
+        ctx.graph_launch()
+        stats = ctx.graph_read_stats()
+        assert stats[0]["status"] == qed.QED_ERR_TIMEOUT and stats[0]["tail"] == 1, stats[0]
+        assert stats[1]["status"] == qed.QED_ERR_TIMEOUT and stats[1]["substeps"] == 0
+    else:
+        st = ctx.event_step(store, 9)
+        assert st["status"] == qed.QED_ERR_TIMEOUT and st["tail"] == 1, st
+    ctx.set_wait_limit(0)
+    again = qed.ParticleStore.from_numpy(arr, capacity=n * 60)
+    st = ctx.event_step(again, 9)
+    ref_ctx = qed.Context(seed=3)
+    ref = qed.ParticleStore.from_numpy(arr, capacity=n * 60)
+    st_ref = ref_ctx.event_step(ref, 9)
+    assert st["status"] == 0 and st["tail"] == 1
+    for k in ("substeps", "emissions", "pairs", "children", "plans", "count"):
+        assert st[k] == st_ref[k], (k, st[k], st_ref[k])
+    a, b = _sorted(again.to_numpy()), _sorted(ref.to_numpy())
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])

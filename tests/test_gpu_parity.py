@@ -212,7 +212,7 @@ def _run_gpu(arr, step, capacity, log_cap=1 << 20, **cfg):
     return store.to_numpy(), st, ev
 
 
-def _check(arr, step, capacity, seed, mask=3, cascade=True, recoil=True, max_exempt=0.1):
+def _check(arr, step, capacity, seed, mask=3, cascade=True, recoil=True, max_exempt=1e-3):
     g_store, g_st, g_ev = _run_gpu(arr, step, capacity, seed=seed, process_mask=mask,
                                    cascade=cascade, recoil=recoil)
     cf = O.make_config(seed, process_mask=mask, cascade=int(cascade), recoil=int(recoil))
@@ -222,6 +222,7 @@ def _check(arr, step, capacity, seed, mask=3, cascade=True, recoil=True, max_exe
     print("parity:", {k: v for k, v in rep.items() if k != "mismatches"},
           "gpu", g_st, "oracle", o_st)
     assert not rep["mismatches"], rep["mismatches"][:5]
+    print("exempt fraction %.2e" % (rep["exempt"] / max(rep["particles"], 1)))
     assert rep["exempt"] <= max_exempt * rep["particles"]
     if len(o_ties) == 0:
         for k in ("substeps", "emissions", "pairs", "children", "plans"):
@@ -360,8 +361,10 @@ def _sampled_full_size(arr, capacity, seed, mask, roots, log_cap):
     cf = O.make_config(seed, process_mask=mask, cascade=1)
     o_store, o_st, o_ev, o_ties = O.event_step(cf, sub, 0, capacity=len(roots) * 4000)
     rep = parity.compare(g_ev, o_ev, o_ties, g_store, o_store, sub["id"])
-    print("sampled parity:", {k: v for k, v in rep.items() if k != "mismatches"}, g_st)
+    print("sampled parity:", {k: v for k, v in rep.items() if k != "mismatches"},
+          "exempt fraction %.2e" % (rep["exempt"] / max(rep["particles"], 1)), g_st)
     assert not rep["mismatches"], rep["mismatches"][:5]
+    assert rep["exempt"] <= 1e-3 * rep["particles"]
     return g_st
 
 
