@@ -380,8 +380,7 @@ __device__ __forceinline__ bool apply_event(const DevParticles& P, const Scratch
         j = reserve_rows(P, ctl, nch, true);
     }
     const uint4 cid = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, s),
-                                    (uint32_t)SP.seed ^ kChildKeyLo,
-                                    (uint32_t)(SP.seed >> 32) ^ kChildKeyHi);
+                                    SP.child_keys);
     const uint64_t id0 = ((uint64_t)cid.x | ((uint64_t)cid.y << 32)) | (1ull << 63);
     const uint64_t id1 = ((uint64_t)cid.z | ((uint64_t)cid.w << 32)) | (1ull << 63);
     float delta;
@@ -511,8 +510,8 @@ constexpr uint32_t kNoEvent = 0xffffffffu;
 __device__ __forceinline__ void warp_draw_round(const SharedTables& sm, uint32_t* facc,
                                                 bool active, uint32_t s, uint32_t s_end,
                                                 uint32_t T, float b, float c_h, uint64_t id,
-                                                bool photon, uint32_t step, uint32_t k0,
-                                                uint32_t k1, unsigned int& cand) {
+                                                bool photon, uint32_t step, const PhiloxKeys& K,
+                                                unsigned int& cand) {
     constexpr unsigned int kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t b0 = s >> 1;
@@ -545,7 +544,7 @@ __device__ __forceinline__ void warp_draw_round(const SharedTables& sm, uint32_t
         const uint32_t o_hi = __shfl_sync(kAll, (uint32_t)(id >> 32), owner);
         const bool o_photon = __shfl_sync(kAll, photon ? 1 : 0, owner) != 0;
         if (f < total) {
-            const uint4 r = philox4x32_10(make_uint4(o_lo, o_hi, step, blk), k0, k1);
+            const uint4 r = philox4x32_10(make_uint4(o_lo, o_hi, step, blk), K);
             const uint32_t sA = 2u * blk;
             const bool cA = sA >= o_s && sA < o_end && (r.y >> 9) < o_T;
             const bool cB = sA + 1u >= o_s && sA + 1u < o_end && (r.w >> 9) < o_T;
@@ -572,10 +571,9 @@ __device__ __forceinline__ void warp_draw_round(const SharedTables& sm, uint32_t
 }
 
 // x of sub-step s (the first word of its draw pair).
-__device__ __forceinline__ float draw_x(uint64_t id, uint32_t step, uint32_t s, uint32_t k0,
-                                        uint32_t k1) {
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, s >> 1),
-                                  k0, k1);
+__device__ __forceinline__ float draw_x(uint64_t id, uint32_t step, uint32_t s,
+                                        const PhiloxKeys& K) {
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, s >> 1), K);
     return u01((s & 1u) ? r.z : r.x);
 }
 
@@ -607,7 +605,6 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
     uint32_t* facc = first_acc + (threadIdx.x & ~31);
     constexpr unsigned int kAll = 0xffffffffu;
     Stats stats;
-    const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
     for (long long base = begin + warp * 32; base < end; base += nwarps * 32) {
         const long long i = base + lane;
         bool active = false, photon = false, changed = false, removed = false;
@@ -672,8 +669,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                 }
             }
             const uint32_t s_end = active ? s + pl.N : 0u;
-            warp_draw_round(sm, facc, active, s, s_end, pl.T, pl.b, pl.c_h, id, photon, step, k0,
-                            k1, stats.cand);
+            warp_draw_round(sm, facc, active, s, s_end, pl.T, pl.b, pl.c_h, id, photon, step, SP.draw_keys, stats.cand);
             if (active) {
                 const uint32_t s_ev = facc[lane];
                 if (s_ev == kNoEvent) {
@@ -683,7 +679,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                 } else {
                     const uint32_t k = s_ev - s;
                     stats.substeps += k + 1u;
-                    const float x = draw_x(id, step, s_ev, k0, k1);
+                    const float x = draw_x(id, step, s_ev, SP.draw_keys);
                     const ftime t_after = (k + 1u == pl.N) ? ftime{0.0f, 0.0f}
                                                            : time_sub_mul(t_rem, k + 1u, pl.h);
                     removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
@@ -736,7 +732,6 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
     const long long n_init = ctl->n_init;
     constexpr unsigned int kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const uint32_t k0 = (uint32_t)SP.seed, k1 = (uint32_t)(SP.seed >> 32);
     const PlanConst PC = plan_const(SP);
     Stats stats;
     bool busy = false, drained = n <= 0, photon = false, electron = false, need_plan = false;
@@ -882,7 +877,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
                     T = squeeze_threshold(squeeze_bound(sm.sqz_e, sm.sqz_p, false, b, c_h, b23));
                 }
                 const uint32_t sj = os + (uint32_t)j;
-                const uint4 r = philox4x32_10(make_uint4(oid0, oid1, step, sj >> 1), k0, k1);
+                const uint4 r = philox4x32_10(make_uint4(oid0, oid1, step, sj >> 1), SP.draw_keys);
                 const uint32_t yw = (sj & 1u) ? r.w : r.y;
                 xj = u01((sj & 1u) ? r.z : r.x);
                 if ((yw >> 9) < T) {
@@ -943,7 +938,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
             }
             if ((s >> 1) != blk) {
                 blk = s >> 1;
-                r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, blk), k0, k1);
+                r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, blk), SP.draw_keys);
             }
             const uint32_t yw = (s & 1u) ? r.w : r.y;
             const float x = u01((s & 1u) ? r.z : r.x);
@@ -1067,7 +1062,7 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
             const uint32_t lim = sb + (pl.N - kdone);
             const uint32_t s0 = sa + 2u * (uint32_t)lane;
             const uint4 r = philox4x32_10(
-                make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, (sa >> 1) + lane), k0, k1);
+                make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, (sa >> 1) + lane), SP.draw_keys);
             const bool v0 = s0 >= sb && s0 < lim;
             const bool v1 = s0 + 1 >= sb && s0 + 1 < lim;
             bool c0, c1, a0 = false, a1 = false;
@@ -1253,7 +1248,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
         }
         const uint32_t n_win = active ? min(kWindow, pl.N - k_done) : 0u;
         const uint32_t s_end = s + n_win;
-        warp_draw_round(sm, facc, active, s, s_end, pl.T, pl.b, pl.c_h, id, photon, step, k0, k1,
+        warp_draw_round(sm, facc, active, s, s_end, pl.T, pl.b, pl.c_h, id, photon, step, SP.draw_keys,
                         stats.cand);
         if (active) {
             const uint32_t s_ev = facc[lane];
@@ -1266,7 +1261,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
             } else {
                 const uint32_t k = k_done + (s_ev - s);
                 stats.substeps += s_ev - s + 1u;
-                const float x = draw_x(id, step, s_ev, k0, k1);
+                const float x = draw_x(id, step, s_ev, SP.draw_keys);
                 const ftime t_after = (k + 1u == pl.N) ? ftime{0.0f, 0.0f}
                                                        : time_sub_mul(t_rem, k + 1u, pl.h);
                 removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
@@ -1594,7 +1589,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
         // ---- 5. one round of warp-shared draws for the active lanes
         const uint32_t n_win = active ? min(kWindow, pl.N - k_done) : 0u;
         const uint32_t s_end = s + n_win;
-        warp_draw_round(sm, facc, active, s, s_end, pl.T, pl.b, pl.c_h, id, photon, step, k0, k1,
+        warp_draw_round(sm, facc, active, s, s_end, pl.T, pl.b, pl.c_h, id, photon, step, SP.draw_keys,
                         stats.cand);
         if (active) {
             const uint32_t s_ev = facc[lane];
@@ -1607,7 +1602,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
             } else {
                 const uint32_t k = k_done + (s_ev - s);
                 stats.substeps += s_ev - s + 1u;
-                const float x = draw_x(id, step, s_ev, k0, k1);
+                const float x = draw_x(id, step, s_ev, SP.draw_keys);
                 const ftime t_after = (k + 1u == pl.N) ? ftime{0.0f, 0.0f}
                                                        : time_sub_mul(t_rem, k + 1u, pl.h);
                 removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
@@ -2082,6 +2077,8 @@ StepParams make_params(const qed_config& c, uint64_t step) {
     P.inv_p_max = 1.0f / c.p_max;
     P.pair_coeff = c.pair_bound_coeff;
     P.lambda_m = c.lambda_m;
+    P.draw_keys = philox_keys((uint32_t)c.seed, (uint32_t)(c.seed >> 32));
+    P.child_keys = philox_keys((uint32_t)c.seed ^ kChildKeyLo, (uint32_t)(c.seed >> 32) ^ kChildKeyHi);
     P.wait_ns = kWaitNsDefault;
     P.step_base = nullptr;
     P.hot_min = kHotMinDefault;

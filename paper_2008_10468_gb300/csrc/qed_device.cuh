@@ -35,6 +35,35 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// The same with the round keys given: round r uses (k0 + r 0x9E3779B9,
+// k1 + r 0xBB67AE85) from K.k[2r], K.k[2r+1].  The event kernels take them
+// from their parameter block, computed once on the host (philox_keys), so a
+// block costs only its multiplies and xors.
+struct PhiloxKeys {
+    uint32_t k[20];
+};
+
+__host__ __device__ inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+    PhiloxKeys K;
+    for (int r = 0; r < 10; ++r) {
+        K.k[2 * r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        K.k[2 * r + 1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+    return K;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ K.k[2 * r], lo1, hi0 ^ c.w ^ K.k[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 // ((r >> 9) + 1/2) * 2^-23: open interval (0, 1), exact in binary32.
 __device__ __forceinline__ float u01(uint32_t r) {
     return fmaf((float)(r >> 9), 0x1p-23f, 0x1p-24f);
@@ -126,10 +155,11 @@ __device__ __forceinline__ float chi_ff(bool photon, float px, float py, float p
 }
 
 // chi in binary32 (Sec. 2.2).  Sets *well_conditioned when the rounding
-// error of chi is certainly below 3.2e-6 relative: the error of the computed
-// chi^2 is at most ~13 eps M^2 with M = eps|E| + |p||B| (a bound on |eps E +
-// p x B| and |p.E|), so kappa = 2 (eps^2 E^2 + p^2 B^2) / chi^2 >= M^2 / chi^2
-// <= 8 keeps it below 6.5 eps kappa ~ 3.2e-6.  Otherwise use chi_ff.
+// error of chi is certainly below 8e-7 relative: the error of the computed
+// chi^2 is at most ~13 u M^2 (u = 2^-24) with M = eps|E| + |p||B| (a bound on
+// |eps E + p x B| and |p.E|), so kappa = 2 (eps^2 E^2 + p^2 B^2) / chi^2 >=
+// M^2 / chi^2 below 2 keeps the error of chi below 13 u = 7.8e-7 (sqrt and
+// the scaling add ~1 u).  Otherwise use chi_ff.
 __device__ __forceinline__ float chi_f32(bool photon, float px, float py, float pz, float Ex,
                                          float Ey, float Ez, float Bx, float By, float Bz,
                                          float inv_Es, float* eps_out, bool* well_conditioned) {
@@ -145,7 +175,7 @@ __device__ __forceinline__ float chi_f32(bool photon, float px, float py, float 
     const float B2 = fmaf(Bx, Bx, fmaf(By, By, Bz * Bz));
     const float M2 = 2.0f * fmaf(eps * eps, E2, p2 * B2);
     *eps_out = eps;
-    *well_conditioned = q > 0.125f * M2;
+    *well_conditioned = q > 0.5f * M2;
     return q > 0.0f ? sqrtf(q) * inv_Es : 0.0f;
 }
 
@@ -263,8 +293,7 @@ __device__ __forceinline__ void stage_syn_table(SynTable& tb) {
 constexpr float kPi = 3.14159265358979f;
 
 // The emission bound from l2b = log2(b) (b > 0): the powers as exp2(a l2b) on
-// the special-function unit (relative error ~3e-7, far inside the planner's
-// 2e-5 safety band).
+// the special-function unit (error budget in make_plan).
 __device__ __forceinline__ float bound_emission_l2(float b, float l2b, float c) {
     float lead;
     if (b < 0.1f) lead = 0.56f * kPi * b;
@@ -318,7 +347,7 @@ struct Plan {
     uint32_t T;      // squeeze threshold on (r >> 9): candidates have (r >> 9) < T
     ftime h;         // sub-step length (periods)
     bool guard;      // N raised by the validity guard
-    bool safe;       // N cannot change within +-1e-5 (relative) of chi and f
+    bool safe;       // N is certain (the count of the exact q)
     float chi, eps;  // quantum parameter and energy the plan was made from
 };
 
@@ -354,6 +383,8 @@ struct StepParams {
     float inv_p_max;     // 1 / p_max
     float pair_coeff;
     double lambda_m;     // laser wavelength (m)
+    PhiloxKeys draw_keys;   // round keys of the draw stream (key: seed)
+    PhiloxKeys child_keys;  // ... of the child-id stream (key: seed ^ kChildKey)
     unsigned long long wait_ns;  // tail pass: longest bounded wait before QED_ERR_TIMEOUT
     ftime t_step;        // dt as float-float
     const uint32_t* step_base;  // graph runs: device step base added to `step`
@@ -404,10 +435,25 @@ __device__ __forceinline__ int emission_piece(float b) {
     return b < 0.1f ? 0 : (b < 0.5f ? 1 : (b < 10.0f ? 2 : 3));
 }
 
+// log2 b within 5e-7 for every b > 0: the exponent exactly, plus __log2f of
+// the mantissa in [1, 2), where its absolute error is at most 2^-22 (for a
+// subnormal or zero b, __log2f of b itself).
+__device__ __forceinline__ float log2_split(float b) {
+    const int bits = __float_as_int(b);
+    const int e = ((bits >> 23) & 0xff) - 127;
+    const float m = __int_as_float((bits & 0x007fffff) | 0x3f800000);
+    return e > -127 ? (float)e + __log2f(m) : __log2f(b);
+}
+
 // Plan the sub-steps of the remaining time T (Algorithms 1/2, planning).
-// `safe` reports whether N is certain when chi carries a relative error of up
-// to 1e-5: every f(b) piece grows at most linearly in b, so f moves by less
-// than 2e-5 relative unless b crosses a piece boundary.
+// `safe` reports whether N is certain.  The binary32 q = f / P_max carries a
+// relative error below 2.1e-6: chi 8.8e-7 (well-conditioned, see chi_f32;
+// every f(b) piece grows at most linearly in b), c 3.6e-7 (1/eps by the fast
+// divide, K and t rounded, two products), b^e 2.6e-7 (log2_split) plus 2.9e-7
+// (exp2f and the product in its argument), the constants A pi and 0.1 in
+// binary32 1.2e-7, the last three roundings 1.5e-7.  So N = max(1, ceil(q),
+// ceil(g)) is certain when it is the same at q (1 -+ 3e-6) and g (1 -+ 3e-6)
+// and b stays in its f piece within 2e-6; otherwise plan_slow recomputes it.
 __device__ __forceinline__ PlanConst plan_const(const StepParams& P) {
     return PlanConst{P.K, P.inv_Es, P.inv_p_max, P.pair_coeff, P.p_max, P.lambda_m};
 }
@@ -415,7 +461,7 @@ __device__ __forceinline__ PlanConst plan_const(const StepParams& P) {
 __device__ __forceinline__ Plan make_plan(const PlanConst& P, const float* __restrict__ sqz_e,
                                           const float* __restrict__ sqz_p, bool photon, float chi,
                                           float eps, ftime T) {
-    constexpr float d = 2e-5f;
+    constexpr float d = 3e-6f;
     Plan pl;
     pl.chi = chi;
     pl.eps = eps;
@@ -423,7 +469,7 @@ __device__ __forceinline__ Plan make_plan(const PlanConst& P, const float* __res
     const float inv_eps = __fdividef(1.0f, eps);
     const float c_rem = P.K * T.hi * inv_eps;
     const float b = pl.b;
-    const float l2b = __log2f(b);
+    const float l2b = log2_split(b);
     const float f = photon ? P.pair_coeff * c_rem * b
                            : (b > 0.0f ? bound_emission_l2(b, l2b, c_rem) : 0.0f);
     const float q = f * P.inv_p_max;
@@ -443,7 +489,7 @@ __device__ __forceinline__ Plan make_plan(const PlanConst& P, const float* __res
     const float n_hi = fmaxf(1.0f, fmaxf(ceilf(q * (1.0f + d)), ceilf(graw * (1.0f + d))));
     bool safe = n_lo == n_hi;
     if (!photon)
-        safe = safe && emission_piece(b * (1.0f - 1e-5f)) == emission_piece(b * (1.0f + 1e-5f));
+        safe = safe && emission_piece(b * (1.0f - 2e-6f)) == emission_piece(b * (1.0f + 2e-6f));
     N = fminf(N, 1073741824.0f);  // 2^30: keeps the 32-bit sub-step counter from wrapping
     pl.N = (uint32_t)N;
     pl.safe = safe;
@@ -465,11 +511,11 @@ __device__ __forceinline__ double bound_emission64(double b, double c) {
 }
 
 // Slow path of plan_particle, for plans whose binary32 count is not certain
-// (chi ill-conditioned, or f / P_max within 2e-5 of an integer, or b at a
+// (chi ill-conditioned, or f / P_max within 3e-6 of an integer, or b at a
 // piece edge): chi in float-float, then the count N = max(1, ceil(f/P_max),
 // guard) in binary64, so that N is the exact count unless f / P_max lies
-// within ~1e-13 of an integer.  Rare (a few per cent of the longest plans),
-// so its binary64 arithmetic stays off the sub-step path.  Kept out of line
+// within ~1e-13 of an integer.  Rare (0.6% of the longest plans, fewer of
+// the others), so its binary64 arithmetic stays off the sub-step path.  Kept out of line
 // so that the common path does not carry its registers.
 __device__ __noinline__ Plan plan_slow(PlanConst P, const float* __restrict__ sqz_e,
                                        const float* __restrict__ sqz_p, bool photon, float px,
@@ -537,9 +583,9 @@ __device__ __forceinline__ Plan plan_particle(const StepParams& SP, const float*
 //   3 x^2 P(x^3) = (c b / x) [(1 - delta) F(z) + delta^2 G(z)],  z = delta / (b (1-delta)).
 // Algorithm 2 (pair, delta = x, Eq. 2 with the positive bracket):
 //   P_p = (c b / 3) [G(z) - delta (1 - delta) F(z)],  z = 1 / (b delta (1 - delta)).
-// The quotients use the fast divide (within 2 ulp): P (at most ~0.02) moves
-// by a few 1e-7 relative, far inside the band |y - P| <= 1e-5 within which a
-// decision y < P counts as a tie.
+// The quotients use the fast divide (within 2 ulp): P moves by a few 1e-7
+// relative, inside the band |y - P| <= 1e-5 P within which a decision y < P
+// counts as a tie.
 __device__ __forceinline__ float acceptance(const SynTable& tbl, bool photon, float b,
                                             float c_h, float x, float* delta_out) {
     float F, G;
