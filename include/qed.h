@@ -66,7 +66,10 @@ typedef struct {
                                   sub-step is an event with the tabulated
                                   probability; 2: the same, event-driven: the
                                   sub-steps to the next event are drawn at once
-                                  (geometric), with no per-sub-step draws        */
+                                  (geometric), with no per-sub-step draws; its
+                                  particles run one per lane and each warp's
+                                  events go through the network together on
+                                  the tensor cores (no tail pass in this mode) */
     float sampler_max_err;     /* a chi bin is usable if its max CDF error <= this
                                   (1e-3)                                        */
 } qed_config;
@@ -312,7 +315,9 @@ qed_status qed_sampler_train(qed_ctx* ctx, uint64_t seed, int64_t samples, int b
 
 /* Measure the max CDF error per bin (bin_err: host array of
  * QED_SAMPLER_BINS) on 4 chi rows x 1024 u per bin against exact CDF rows,
- * and mark the usable bins.  Required before an event step in sampler mode.
+ * for both forms of the network the event kernels use (the larger error
+ * counts), and mark the usable bins.  Required before an event step in
+ * sampler mode.
  * Errors: ARG, STATE (no sampler), CUDA. */
 qed_status qed_sampler_evaluate(qed_ctx* ctx, float* bin_err, int nbins);
 
@@ -327,8 +332,11 @@ qed_status qed_sampler_gradient(qed_ctx* ctx, const float* params, const float* 
 
 /* x = delta^{1/3} at (log10chi[i], u[i]) for i < n (device arrays; log10 chi
  * clamped to [-2, 2]; u in the open interval (0, 1)): use_net = 0 the exact
- * inverse CDF from the tables
- * (bilinear in log10 chi and x), 1 the network.  Errors: ARG, STATE, CUDA. */
+ * inverse CDF from the tables (bilinear in log10 chi and x), 1 the network
+ * as the warp-mode event kernels evaluate it (FP32 activations), 2 the
+ * network on the tensor cores as the event-driven sampler evaluates it
+ * (mma.sync BF16 x BF16 -> FP32, activations as BF16 hi + lo pairs).
+ * Errors: ARG, STATE, CUDA. */
 qed_status qed_sampler_quantile(qed_ctx* ctx, const float* log10chi, const float* u, float* x,
                                 int64_t n, int use_net);
 
@@ -386,6 +394,7 @@ enum {
     QED_KERNEL_COLD = 3,       /* event step: thread-per-particle pass         */
     QED_KERNEL_HOT = 4,        /* event step: queue pass and tail pass         */
     QED_KERNEL_CONTROL = 5,    /* event step: per-step and per-pass bookkeeping */
+    QED_KERNEL_SAMPLER = 6,    /* event step: event-driven sampler, one lane per particle */
     QED_KERNEL_KINDS = 8
 };
 

@@ -88,6 +88,7 @@ struct DevCtl {
                                     // after the thread pass's hot_tail entries
     int skip;                       // the tail pass does nothing
     unsigned long long push_head;   // push mode: next row of the generation to take
+    unsigned int samp_tail, samp_head;   // event-driven sampler: its queue of this generation
     long long n_init;               // rows at the start of the step (the rest are children)
 };
 
@@ -117,6 +118,7 @@ struct Scratch {
                             // from both ends: long plans from the front,
                             // medium plans from the back
     long long hot_cap;
+    HotItem* samp;          // event-driven sampler's queue (capacity entries; null when off)
     qed_event_record* log;  // optional
     long long log_cap;
     long long* log_count;
@@ -358,6 +360,8 @@ __device__ __forceinline__ void write_child_fields(const DevParticles& P, const 
 }
 
 
+constexpr long long kReserveHere = -2;   // apply_event reserves the child rows itself
+
 // Apply an accepted event (recoil or decay, children, log).  Returns true if
 // the particle was removed (photon decay).  Thread callers (write_rows) do
 // everything themselves, sharing one reservation atomic per warp; warp
@@ -369,11 +373,13 @@ __device__ __forceinline__ bool apply_event(const DevParticles& P, const Scratch
                             DevCtl* ctl, long long i, uint64_t id, bool photon, float x,
                             float eps, float chi, uint32_t step, uint32_t s, ftime t_after, PState& st,
                             Stats& stats, bool write_rows, bool warp_caller, const Fields& F,
-                            bool publish) {
+                            bool publish, long long j_pre = kReserveHere) {
     const int nch = photon ? 2 : 1;
     const int lane = threadIdx.x & 31;
     long long j = -1;
-    if (warp_caller) {
+    if (j_pre != kReserveHere) {
+        j = j_pre;   // reserved by the caller (-1: it did not fit)
+    } else if (warp_caller) {
         // lane 0 reserves and stores; its result is first needed at the stores
         if (lane == 0) j = reserve_rows(P, ctl, nch, false);
     } else if (write_rows) {
@@ -651,9 +657,18 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                         }
                         // the hot pass plans again; long plans and the
                         // sampler's particles are stepped by a whole warp,
-                        // the others by a lane
-                        push_hot(S, ctl, i, s, t_rem,
-                                 pl.N >= SP.long_min || (!photon && sampler_bin_ok(SP, chi)));
+                        // the others by a lane (the event-driven sampler's
+                        // particles one lane each, in their own queue)
+                        const bool net = !photon && sampler_bin_ok(SP, chi);
+                        if (net && S.samp) {
+                            HotItem it;
+                            it.idx = (uint32_t)i;
+                            it.s = s;
+                            it.t_rem = t_rem;
+                            S.samp[atomicAdd(&ctl->samp_tail, 1u)] = it;
+                        } else {
+                            push_hot(S, ctl, i, s, t_rem, pl.N >= SP.long_min || net);
+                        }
                         active = false;
                     } else {
                         stats.plans++;
@@ -987,11 +1002,13 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
 template <int kSampler>
 __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& S,
                                           const StepParams& SP, DevCtl* ctl,
-                                          const SharedTables& sm, SamplerSmem& net,
+                                          const SharedTables& sm, unsigned char* net_smem,
                                           const HotItem& it, uint32_t step, uint32_t k0,
                                           uint32_t k1, Stats& stats, unsigned int& cand,
                                           bool publish) {
     const int lane = threadIdx.x & 31;
+    SamplerSmem& net = *reinterpret_cast<SamplerSmem*>(net_smem);      // mode 1
+    SamplerMma& mma = *reinterpret_cast<SamplerMma*>(net_smem);        // mode 2
     const long long i = it.idx;
     const bool photon = P.type[i] == QED_PHOTON;
     const uint64_t id = P.id[i];
@@ -1012,7 +1029,11 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
             stats.max_N = max(stats.max_N, pl.N);
         }
         const bool use_net = kSampler != 0 && !photon && sampler_bin_ok(SP, chi);
-        const float thr = use_net ? fminf(pl.c_h * sampler_wtot(net, chi), 1.0f) : 0.0f;
+        const float thr =
+            use_net ? fminf(pl.c_h * (kSampler == 2 ? wtot_at(mma.wtot, mma.nrows, chi)
+                                                    : sampler_wtot(net, chi)),
+                            1.0f)
+                    : 0.0f;
         uint32_t kdone = 0;
         bool event = false;
         if (!use_net && pl.T == 0u) {   // no candidates: count without drawing
@@ -1039,7 +1060,9 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
                 const uint32_t k = (uint32_t)wait;
                 const uint32_t s_ev = s + k;
                 const uint32_t k_ev = kdone + k;
-                const float x = mlp_infer_warp(net, log10f(chi) * 0.5f, mlp_input_u(u01(r.x)));
+                // the tensor-core form, as in k_samp (one sample: one tile)
+                const float x = mlp_infer_mma_one(mma, warp_mma_buf(net_smem),
+                                                  log10f(chi) * 0.5f, mlp_input_u(u01(r.x)));
                 if (lane == 0) {
                     stats.substeps += k + 1;
                     stats.sampled++;
@@ -1135,6 +1158,169 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
 }
 
 
+// Event-driven sampler, one lane per particle (sampler mode 2; reading of
+// Sec. 2.2's inverse sampling, with the sub-steps to the next event drawn at
+// once).  A lane holds one of the sampler's particles (e+- in a usable chi
+// bin, queued by the thread pass).  Per round, every busy lane draws the
+// sub-steps to its next event, geometric with the per-sub-step probability
+// c_h W(b) of its plan: floor(ln u / ln(1 - p)) from one Philox block at
+// counter (id, step, first sub-step of the plan) under the waiting-time key.
+// If the event falls beyond the plan, the particle's time runs out without an
+// event; otherwise the lanes with an event evaluate the network together on
+// the tensor cores (mlp_infer_mma, the block's other word as the uniform), and
+// apply their events (recoil, photon child, one reservation atomic per warp)
+// and re-plan from the remaining time.  A particle whose new chi leaves the
+// sampler's usable bins continues with rejection: its state goes back to the
+// store and it joins the hot pass's queue (the hot pass runs after this
+// kernel).  Idle lanes take queue entries, one atomic per warp.  Persistent.
+constexpr unsigned int kSampPerLane = 8;
+__global__ void __launch_bounds__(kLaneThreads) k_samp(DevParticles P, StepParams SP, Scratch S,
+                                                       DevCtl* ctl) {
+    const uint32_t step = step_index(SP);
+    __shared__ SharedTables sm;
+    __shared__ float fld[6][kLaneThreads];   // E, B at the lane's row
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    SamplerMma& net = *reinterpret_cast<SamplerMma*>(dyn_smem);
+    stage_tables(sm);
+    stage_sampler_mma(net, reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
+                      SP.net_rows, SP.net_bins);
+    __syncthreads();
+    if (ctl->status == (int)QED_ERR_TIMEOUT) return;
+    constexpr unsigned int kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t kw0 = (uint32_t)SP.seed ^ kWaitKeyLo, kw1 = (uint32_t)(SP.seed >> 32) ^ kWaitKeyHi;
+    const unsigned int tail = ctl->samp_tail;
+    // as many warps as keep their lanes busy: about kSampPerLane particles per
+    // lane (chains average a few events), spread over every block, at least a
+    // quarter of the launched warps; the others leave at once
+    {
+        const unsigned int wpb = blockDim.x >> 5;
+        const unsigned int need = max((tail + 32u * kSampPerLane - 1u) / (32u * kSampPerLane),
+                                      gridDim.x * wpb / 4u);
+        const unsigned int per_block = (need + gridDim.x - 1u) / gridDim.x;
+        if ((threadIdx.x >> 5) >= per_block) return;
+    }
+    Stats stats;
+    bool active = false, more = true;
+    uint32_t i = 0, s = 0;
+    uint64_t id = 0;
+    PState st{0.0f, 0.0f, 0.0f};
+    ftime t_rem{0.0f, 0.0f};
+    Plan pl;
+    pl.N = 0;
+    float chi = 0.0f, eps = 0.0f, thr = 0.0f;
+    // after a load or an event: plan the remaining time; false if the lane
+    // is done with the particle (no time left, or handed to rejection)
+    auto plan_lane = [&]() -> bool {
+        pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, false, st.px, st.py, st.pz,
+                           fld[0][threadIdx.x], fld[1][threadIdx.x], fld[2][threadIdx.x],
+                           fld[3][threadIdx.x], fld[4][threadIdx.x], fld[5][threadIdx.x], t_rem,
+                           &chi, &eps);
+        if (!(eps > 0.0f)) return false;
+        stats.max_N = max(stats.max_N, pl.N);
+        if (!sampler_bin_ok(SP, chi)) {
+            // rejection from here on: the hot pass plans again from the store
+            P.px[i] = st.px;
+            P.py[i] = st.py;
+            P.pz[i] = st.pz;
+            push_hot(S, ctl, i, s, t_rem, pl.N >= SP.long_min);
+            return false;
+        }
+        stats.plans++;
+        stats.guard += pl.guard ? 1 : 0;
+        thr = fminf(pl.c_h * wtot_at(net.wtot, net.nrows, chi), 1.0f);
+        return true;
+    };
+    while (true) {
+        if (more) {
+            const unsigned int idle = __ballot_sync(kAll, !active);
+            if (idle) {
+                unsigned int base = 0;
+                if (lane == 0) base = atomicAdd(&ctl->samp_head, (unsigned int)__popc(idle));
+                base = __shfl_sync(kAll, base, 0);
+                if (base + (unsigned int)__popc(idle) >= tail) more = false;
+                if (!active) {
+                    const unsigned int q = base + (unsigned int)__popc(idle & ((1u << lane) - 1u));
+                    if (q < tail) {
+                        const HotItem it = S.samp[q];
+                        i = it.idx;
+                        s = it.s;
+                        t_rem = it.t_rem;
+                        id = P.id[i];
+                        st = PState{P.px[i], P.py[i], P.pz[i]};
+                        fld[0][threadIdx.x] = P.Ex[i];
+                        fld[1][threadIdx.x] = P.Ey[i];
+                        fld[2][threadIdx.x] = P.Ez[i];
+                        fld[3][threadIdx.x] = P.Bx[i];
+                        fld[4][threadIdx.x] = P.By[i];
+                        fld[5][threadIdx.x] = P.Bz[i];
+                        active = plan_lane();
+                    }
+                }
+            }
+        }
+        if (!__any_sync(kAll, active)) {
+            if (!more) break;
+            continue;
+        }
+        // the sub-steps to the next event
+        bool ev = false, done = false;
+        uint32_t k = 0;
+        float u_net = 0.5f;
+        if (active) {
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)id, (uint32_t)(id >> 32), step, s),
+                                          kw0, kw1);
+            const float wait = floorf(logf(u01(r.y)) / log1pf(-thr));
+            if (!(wait < (float)pl.N && thr > 0.0f)) {   // no event in the rest of the plan
+                stats.substeps += pl.N;
+                s += pl.N;
+                done = true;
+            } else {
+                k = (uint32_t)wait;
+                ev = true;
+                u_net = u01(r.x);
+            }
+        }
+        if (__any_sync(kAll, ev)) {
+            // the photon's row, reserved first (one atomic for the warp's
+            // events) so that the atomic's latency overlaps the network
+            long long j = -1;
+            if (ev) j = reserve_rows(P, ctl, 1, true);
+            // the network for the lanes with an event, packed into one tile
+            // when at most 16 have one
+            const float x = mlp_infer_mma_some(net, warp_mma_buf(dyn_smem), ev,
+                                               log10f(chi) * 0.5f, mlp_input_u(u_net));
+            if (ev) {
+                const uint32_t s_ev = s + k;
+                stats.substeps += k + 1;
+                stats.sampled++;
+                const ftime t_after = (k + 1 == pl.N) ? ftime{0.0f, 0.0f}
+                                                      : time_sub_mul(t_rem, k + 1, pl.h);
+                apply_event(P, S, SP, ctl, i, id, false, x, eps, chi, step, s_ev, t_after, st,
+                            stats, true, false,
+                            Fields{fld[0][threadIdx.x], fld[1][threadIdx.x], fld[2][threadIdx.x],
+                                   fld[3][threadIdx.x], fld[4][threadIdx.x], fld[5][threadIdx.x]},
+                            false, j);
+                s = s_ev + 1;
+                t_rem = t_after;
+                if (!time_positive(t_rem)) {
+                    done = true;
+                } else if (!plan_lane()) {
+                    active = false;   // handed to rejection, or no energy left
+                }
+            }
+        }
+        if (done) {
+            P.px[i] = st.px;
+            P.py[i] = st.py;
+            P.pz[i] = st.pz;
+            active = false;
+        }
+    }
+    stats.warp_substeps = stats.substeps;
+    flush_stats(stats, ctl);
+}
+
 // Hot pass (rejection).  Long plans (N >= long_min, front of the queue) first,
 // one warp each (warp_item), so that their long chains start early; then the
 // medium plans (back of the queue), one lane each, with the same warp-shared
@@ -1156,11 +1342,15 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
     __shared__ SharedTables sm;
     __shared__ uint32_t first_acc[kLaneThreads];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    SamplerSmem& net = *reinterpret_cast<SamplerSmem*>(dyn_smem);
     stage_tables(sm);
-    if (kSampler)
-        stage_sampler(net, reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
-                      SP.net_rows, SP.net_bins);
+    if (kSampler == 1)
+        stage_sampler(*reinterpret_cast<SamplerSmem*>(dyn_smem),
+                      reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot, SP.net_rows,
+                      SP.net_bins);
+    else if (kSampler == 2)
+        stage_sampler_mma(*reinterpret_cast<SamplerMma*>(dyn_smem),
+                          reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
+                          SP.net_rows, SP.net_bins);
     __syncthreads();
     if (ctl->status == (int)QED_ERR_TIMEOUT) return;
     constexpr unsigned int kAll = 0xffffffffu;
@@ -1178,7 +1368,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
             if (lane == 0) q = atomicAdd(&ctl->hot_head, 1u);
             q = __shfl_sync(kAll, q, 0);
             if (q >= long_tail) break;
-            warp_item<kSampler>(P, S, SP, ctl, sm, net, S.hot[q], step, k0, k1, wstats, wcand,
+            warp_item<kSampler>(P, S, SP, ctl, sm, dyn_smem, S.hot[q], step, k0, k1, wstats, wcand,
                                 false);
         }
         if (lane == 0) stats = wstats;
@@ -1355,11 +1545,15 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
     __shared__ uint32_t first_acc[kLaneThreads];
     __shared__ float fld[6][kLaneThreads];   // E, B at the lane's row (read at plans and events)
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    SamplerSmem& net = *reinterpret_cast<SamplerSmem*>(dyn_smem);
     stage_tables(sm);
-    if (kSampler)
-        stage_sampler(net, reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
-                      SP.net_rows, SP.net_bins);
+    if (kSampler == 1)
+        stage_sampler(*reinterpret_cast<SamplerSmem*>(dyn_smem),
+                      reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot, SP.net_rows,
+                      SP.net_bins);
+    else if (kSampler == 2)
+        stage_sampler_mma(*reinterpret_cast<SamplerMma*>(dyn_smem),
+                          reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
+                          SP.net_rows, SP.net_bins);
     __syncthreads();
     if (ctl->skip) return;
     constexpr unsigned int kAll = 0xffffffffu;
@@ -1433,7 +1627,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
                 it.s = __shfl_sync(kAll, it.s, 0);
                 it.t_rem.hi = __shfl_sync(kAll, it.t_rem.hi, 0);
                 it.t_rem.lo = __shfl_sync(kAll, it.t_rem.lo, 0);
-                warp_item<kSampler>(P, S, SP, ctl, sm, net, it, step, k0, k1, stats, stats.cand,
+                warp_item<kSampler>(P, S, SP, ctl, sm, dyn_smem, it, step, k0, k1, stats, stats.cand,
                                     true);
                 if (lane == 0) ++done;
                 idle = 0;
@@ -1720,6 +1914,8 @@ __global__ void k_advance(DevCtl* ctl, long long* count, long long capacity, int
     ctl->hot_tail = 0;
     ctl->med_head = 0;
     ctl->med_tail = 0;
+    ctl->samp_head = 0;
+    ctl->samp_tail = 0;
     ctl->passes += 1;
     ctl->first_pass = 0;
     int more = (more_allowed && ctl->pass_end > ctl->pass_begin && ctl->status == 0) ? 1 : 0;
@@ -1998,6 +2194,9 @@ struct qed_ctx {
     long long tail_rows;        // cascade generations below this size go to the tail pass
     unsigned long long wait_ns; // longest bounded wait of the tail pass
     int step_blocks, step_net_blocks;   // resident blocks of the tail pass's kernel
+    int samp_blocks;            // resident blocks of the event-driven sampler kernel
+    HotItem* d_samp;            // its queue (capacity entries), allocated on first use
+    long long samp_cap;
     int push_blocks;            // resident blocks of the push-mode kernel
     unsigned int* d_Ncell;      // per-cell counts of the push mode with cells
     long long ncell_cap;
@@ -2133,6 +2332,29 @@ qed_status ensure_scratch(qed_ctx* ctx, long long cap) {
     return QED_OK;
 }
 
+// The event-driven sampler's queue (sampler mode 2): one entry per row at most
+// per generation.  Sets S->samp.
+qed_status ensure_samp(qed_ctx* ctx, long long cap, const StepParams& SP, Scratch* S) {
+    if (SP.sampler != 2) return QED_OK;
+    if (ctx->samp_cap < cap) {
+        if (ctx->d_samp) cudaFree(ctx->d_samp);
+        ctx->d_samp = nullptr;
+        ctx->samp_cap = 0;
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_samp, sizeof(HotItem) * cap));
+        ctx->samp_cap = cap;
+    }
+    S->samp = ctx->d_samp;
+    return QED_OK;
+}
+
+// Sampler mode of the generations' hot pass: with the event-driven sampler its
+// particles run in k_samp before the hot pass, which then steps rejection
+// plans only.
+int loop_hot_mode(const StepParams& SP) { return SP.sampler == 2 ? 0 : SP.sampler; }
+
+// Generations below this size go to the tail pass.
+long long tail_rows_for(const qed_ctx* ctx, const StepParams&) { return ctx->tail_rows; }
+
 // Bracket a launch with timing events when profiling is on; count it always.
 struct LaunchScope {
     qed_ctx* ctx;
@@ -2212,6 +2434,7 @@ Scratch make_scratch(const qed_ctx* ctx) {
     S.t_rem = ctx->d_trem;
     S.hot = ctx->d_hot;
     S.hot_cap = 2 * ctx->scratch_cap;
+    S.samp = nullptr;
     S.log = ctx->log;
     S.log_cap = ctx->log_cap;
     S.log_count = ctx->log_count;
@@ -2287,23 +2510,27 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
         per_sm = 0;
         for (int m = 1; m <= 2; ++m) {
             cudaFuncSetAttribute(hot_kernel(m), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(SamplerSmem));
+                                 (int)kNetSmemBytes);
             cudaFuncSetAttribute(step_kernel(m), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(SamplerSmem));
+                                 (int)kNetSmemBytes);
         }
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<1>, kLaneThreads,
-                                                      sizeof(SamplerSmem));
+                                                      kNetSmemBytes);
         ctx->net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<0>, kLaneThreads, 0);
         ctx->step_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<1>, kLaneThreads,
-                                                      sizeof(SamplerSmem));
+                                                      kNetSmemBytes);
         ctx->step_net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push, kLaneThreads, 0);
         ctx->push_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
+        per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_samp, kLaneThreads,
+                                                      kMmaSmemBytes);
+        ctx->samp_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         ctx->hot_min = kHotMinDefault;
         ctx->long_min = kLongMinDefault;
         ctx->tail_rows = kTailRowsDefault;
@@ -2330,6 +2557,7 @@ qed_status qed_destroy(qed_ctx* ctx) {
     if (ctx->d_trem) cudaFree(ctx->d_trem);
     if (ctx->d_hot) cudaFree(ctx->d_hot);
     if (ctx->d_Ncell) cudaFree(ctx->d_Ncell);
+    if (ctx->d_samp) cudaFree(ctx->d_samp);
     free_graph(ctx);
     float* f[] = {ctx->mirror.px, ctx->mirror.py, ctx->mirror.pz, ctx->mirror.Ex, ctx->mirror.Ey,
                   ctx->mirror.Ez, ctx->mirror.Bx, ctx->mirror.By, ctx->mirror.Bz, ctx->mirror.w};
@@ -2449,7 +2677,9 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
     st = sampler_params(ctx, &SP);
     if (st != QED_OK) return st;
     const DevParticles D = to_dev(p);
-    const Scratch S = make_scratch(ctx);
+    Scratch S = make_scratch(ctx);
+    st = ensure_samp(ctx, p->capacity, SP, &S);
+    if (st != QED_OK) return st;
     const bool cascade = cascade_enabled(ctx->cfg);
     if (cascade && !ctx->prof_on) {
         // the generations run in a device-side loop: no host round trip per
@@ -2468,6 +2698,11 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
             LaunchScope ls(ctx, QED_KERNEL_COLD);
             k_cold<<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
         }
+        if (SP.sampler == 2) {
+            LaunchScope ls(ctx, QED_KERNEL_SAMPLER);
+            k_samp<<<ctx->samp_blocks, kLaneThreads, kMmaSmemBytes, ctx->stream>>>(
+                D, SP, S, ctx->d_ctl);
+        }
         {
             LaunchScope ls(ctx, QED_KERNEL_HOT);
             DevParticles d = D;
@@ -2475,15 +2710,17 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
             Scratch sc = S;
             DevCtl* c = ctx->d_ctl;
             void* a[] = {&d, &sp, &sc, &c};
-            QED_CUDA(ctx, cudaLaunchKernel(hot_kernel(SP.sampler),
-                                           dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks),
-                                           dim3(kLaneThreads), a,
-                                           SP.sampler ? sizeof(SamplerSmem) : 0, ctx->stream));
+            const int hm = loop_hot_mode(SP);
+            QED_CUDA(ctx, cudaLaunchKernel(hot_kernel(hm),
+                                           dim3(hm ? ctx->net_blocks : ctx->hot_blocks),
+                                           dim3(kLaneThreads), a, hm ? kNetSmemBytes : 0,
+                                           ctx->stream));
         }
         {
             LaunchScope ls(ctx, QED_KERNEL_CONTROL);
             k_advance<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, cascade ? 1 : 0,
-                                                ctx->cfg.max_passes, ctx->tail_rows, 0ull, 0);
+                                                ctx->cfg.max_passes, tail_rows_for(ctx, SP), 0ull,
+                                                0);
         }
         QED_CUDA(ctx, cudaGetLastError());
         if (!cascade) break;
@@ -2492,7 +2729,9 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
         QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         if (!ctx->h_ctl->more) break;
     }
-    // the tail pass (its kernels do nothing when the generations ran to the end)
+    // the tail pass (its kernels do nothing when the generations ran to the end);
+    // there the sampler's particles go to the warp mode
+    S.samp = nullptr;
     {
         LaunchScope ls(ctx, QED_KERNEL_CONTROL);
         k_tail_begin<<<ctx->sms * 8, 256, 0, ctx->stream>>>(D, S, ctx->d_ctl);
@@ -2511,7 +2750,7 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
         QED_CUDA(ctx, cudaLaunchKernel(step_kernel(SP.sampler),
                                        dim3(SP.sampler ? ctx->step_net_blocks : ctx->step_blocks),
                                        dim3(kLaneThreads), a,
-                                       SP.sampler ? sizeof(SamplerSmem) : 0, ctx->stream));
+                                       SP.sampler ? kNetSmemBytes : 0, ctx->stream));
     }
     {
         LaunchScope ls(ctx, QED_KERNEL_CONTROL);
@@ -2693,6 +2932,7 @@ qed_status add_tail_nodes(qed_ctx* ctx, cudaGraph_t g, cudaGraphNode_t dep, cons
     DevParticles D = Din;
     StepParams SP = SPin;
     Scratch S = Sin;
+    S.samp = nullptr;   // in the tail pass the sampler's particles go to the warp mode
     DevCtl* ctl = ctl_in;
     cudaGraphNode_t tb, tc, ts, te;
     qed_status st;
@@ -2710,7 +2950,7 @@ qed_status add_tail_nodes(qed_ctx* ctx, cudaGraph_t g, cudaGraphNode_t dep, cons
         void* a[] = {&D, &SP, &S, &ctl};
         st = add_kernel(ctx, g, &ts, step_kernel(SP.sampler),
                         dim3(SP.sampler ? ctx->step_net_blocks : ctx->step_blocks),
-                        dim3(kLaneThreads), a, &tc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
+                        dim3(kLaneThreads), a, &tc, 1, SP.sampler ? kNetSmemBytes : 0);
     }
     if (st == QED_OK) {
         void* a[] = {&D, &S, &ctl};
@@ -2746,6 +2986,15 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
     cudaGraph_t g = ctx->graph;
     DevParticles D = to_dev(p);
     Scratch S = make_scratch(ctx);
+    {
+        StepParams SP0 = make_params(ctx->cfg, 0);
+        st = sampler_params(ctx, &SP0);
+        if (st == QED_OK) st = ensure_samp(ctx, p->capacity, SP0, &S);
+        if (st != QED_OK) {
+            free_graph(ctx);
+            return st;
+        }
+    }
     DevCtl* ctl = ctx->d_ctl;
     long long* count = D.count;
     long long capacity = D.capacity;
@@ -2794,19 +3043,25 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         st = cuda_check(ctx, cudaGraphAddNode(&wnode, g, &init, nullptr, 1, &cp), "cudaGraphAddNode");
         if (st != QED_OK) break;
         cudaGraph_t body = cp.conditional.phGraph_out[0];
-        cudaGraphNode_t bc, bh, ba;
+        cudaGraphNode_t bc, bs, bh, ba;
         int use_handle = 1;
         {
             void* a[] = {&D, &SP, &S, &ctl};
             st = add_kernel(ctx, body, &bc, (const void*)k_cold, dim3(ctx->cold_blocks),
                             dim3(kColdThreads), a, nullptr, 0);
         }
+        bs = bc;
+        if (st == QED_OK && SP.sampler == 2) {
+            void* a[] = {&D, &SP, &S, &ctl};
+            st = add_kernel(ctx, body, &bs, (const void*)k_samp, dim3(ctx->samp_blocks),
+                            dim3(kLaneThreads), a, &bc, 1, kMmaSmemBytes);
+        }
         if (st == QED_OK) {
             void* a[] = {&D, &SP, &S, &ctl};
-            st = add_kernel(ctx, body, &bh,
-                            hot_kernel(SP.sampler),
-                            dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks), dim3(kLaneThreads),
-                            a, &bc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
+            const int hm = loop_hot_mode(SP);
+            st = add_kernel(ctx, body, &bh, hot_kernel(hm),
+                            dim3(hm ? ctx->net_blocks : ctx->hot_blocks), dim3(kLaneThreads), a,
+                            &bs, 1, hm ? kNetSmemBytes : 0);
         }
         if (st == QED_OK) {
             void* a[] = {&ctl,        &count, &capacity, &more_allowed, &max_passes,
@@ -2903,7 +3158,7 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
         putp(q);
     put((uint64_t)Din.capacity);
     putp(Sin.t_rem); putp(Sin.hot); put((uint64_t)Sin.hot_cap); putp(Sin.log);
-    put((uint64_t)Sin.log_cap); putp(Sin.log_count);
+    put((uint64_t)Sin.log_cap); putp(Sin.log_count); putp(Sin.samp);
     put(SPin.seed);
     { uint64_t b; memcpy(&b, &SPin.dt, 8); put(b); }
     putf(SPin.K); putf(SPin.inv_Es); putf(SPin.p_max); putf(SPin.inv_p_max); putf(SPin.pair_coeff);
@@ -2915,6 +3170,7 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
     put((uint64_t)ctx->cold_blocks); put((uint64_t)ctx->hot_blocks); put((uint64_t)ctx->net_blocks);
     put((uint64_t)ctx->cfg.max_passes);
     put((uint64_t)ctx->tail_rows); put((uint64_t)ctx->step_blocks); put((uint64_t)ctx->step_net_blocks);
+    put((uint64_t)ctx->samp_blocks);
     const bool same = ctx->step_exec && nk == ctx->step_key_n &&
                       memcmp(key, ctx->step_key, sizeof(uint64_t) * nk) == 0;
     if (!same) {
@@ -2932,8 +3188,8 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
         long long* count = D.count;
         long long capacity = D.capacity;
         int keep_sticky = 0, more_allowed = 1, max_passes = ctx->cfg.max_passes, use_handle = 1;
-        long long tail_rows = ctx->tail_rows;
-        cudaGraphNode_t init, wnode, bc, bh, ba, tend;
+        long long tail_rows = tail_rows_for(ctx, SP);
+        cudaGraphNode_t init, wnode, bc, bs, bh, ba, tend;
         qed_status st;
         {
             void* a[] = {&ctl, &count, &capacity, &keep_sticky};
@@ -2957,11 +3213,15 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
             void* a[] = {&D, &SP, &S, &ctl};
             st = add_kernel(ctx, body, &bc, (const void*)k_cold, dim3(ctx->cold_blocks),
                             dim3(kColdThreads), a, nullptr, 0);
+            bs = bc;
+            if (st == QED_OK && SP.sampler == 2)
+                st = add_kernel(ctx, body, &bs, (const void*)k_samp, dim3(ctx->samp_blocks),
+                                dim3(kLaneThreads), a, &bc, 1, kMmaSmemBytes);
+            const int hm = loop_hot_mode(SP);
             if (st == QED_OK)
-                st = add_kernel(ctx, body, &bh,
-                                hot_kernel(SP.sampler),
-                                dim3(SP.sampler ? ctx->net_blocks : ctx->hot_blocks),
-                                dim3(kLaneThreads), a, &bc, 1, SP.sampler ? sizeof(SamplerSmem) : 0);
+                st = add_kernel(ctx, body, &bh, hot_kernel(hm),
+                                dim3(hm ? ctx->net_blocks : ctx->hot_blocks), dim3(kLaneThreads),
+                                a, &bs, 1, hm ? kNetSmemBytes : 0);
             if (st == QED_OK) {
                 void* b[] = {&ctl,        &count, &capacity, &more_allowed, &max_passes,
                              &tail_rows, &h,     &use_handle};
@@ -3103,6 +3363,52 @@ __global__ void k_sampler_eval(const __nv_bfloat16* __restrict__ w, const float*
     atomicMax(&bin_err_bits[bin], __float_as_uint(worst));
 }
 
+// The same error measurement for the tensor-core form of the network (the
+// event-driven sampler's arithmetic): each lane evaluates its own u, the warp
+// together.
+__global__ void k_sampler_eval_mma(const __nv_bfloat16* __restrict__ w,
+                                   const float* __restrict__ cdf, int nrows, int M, float log10_lo,
+                                   float log10_hi, unsigned int* __restrict__ bin_err_bits) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    SamplerMma& S = *reinterpret_cast<SamplerMma*>(dyn_smem);
+    stage_sampler_mma(S, w, nullptr, 0, 0ull);
+    __syncthreads();
+    const int row = blockIdx.x;
+    if (row >= nrows) return;
+    const float l10 = log10_lo + (log10_hi - log10_lo) * ((float)row + 0.5f) / (float)nrows;
+    const int bin = min(max((int)((l10 - kMlpLog10Lo) * 16.0f), 0), 63);
+    float worst = 0.0f;
+    for (int k0 = 0; k0 < kEvalU; k0 += blockDim.x) {   // uniform trip count (kEvalU % blockDim == 0)
+        const int k = k0 + threadIdx.x;
+        const float u = ((float)k + 0.5f) / (float)kEvalU;
+        const float x = mlp_infer_mma(S, l10 * 0.5f, mlp_input_u(u));
+        const float c = cdf_row_at(cdf + (size_t)row * (M + 1), M, x);
+        worst = fmaxf(worst, fabsf(c - u));
+    }
+    atomicMax(&bin_err_bits[bin], __float_as_uint(worst));
+}
+
+// x = Q(chi, u) through the tensor-core form of the network; every lane of a
+// warp takes part in each round (indices past n compute and drop a value).
+__global__ void k_sampler_quantile_mma(const __nv_bfloat16* __restrict__ w,
+                                       const float* __restrict__ log10chi,
+                                       const float* __restrict__ u, float* __restrict__ x,
+                                       long long n) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    SamplerMma& S = *reinterpret_cast<SamplerMma*>(dyn_smem);
+    stage_sampler_mma(S, w, nullptr, 0, 0ull);
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x; b < n; b += stride) {
+        const long long i = b + threadIdx.x;
+        const bool ok = i < n;
+        const float l10 = ok ? fminf(fmaxf(log10chi[i], kMlpLog10Lo), kMlpLog10Hi) : 0.0f;
+        const float uu = ok ? u[i] : 0.5f;
+        const float xv = mlp_infer_mma(S, l10 * 0.5f, mlp_input_u(uu));
+        if (ok) x[i] = xv;
+    }
+}
+
 // x = Q(chi, u): the exact table inverse (bilinear in log10 chi and the CDF
 // node interval) or the network in its per-thread form.
 __global__ void k_sampler_quantile(const __nv_bfloat16* __restrict__ w, const float* __restrict__ cdf,
@@ -3135,11 +3441,17 @@ qed_status qed_sampler_quantile(qed_ctx* ctx, const float* log10chi, const float
                                 int64_t n, int use_net) {
     if (!ctx || n < 0 || (n > 0 && (!log10chi || !u || !x)))
         return set_err(ctx, QED_ERR_ARG, "qed_sampler_quantile: bad argument");
+    if (use_net < 0 || use_net > 2) return set_err(ctx, QED_ERR_ARG, "qed_sampler_quantile: use_net");
     if (use_net && !ctx->net_ready) return set_err(ctx, QED_ERR_STATE, "no sampler trained or loaded");
     qed_status st = sampler_alloc(ctx, 0);
     if (st != QED_OK || n == 0) return st;
     long long blocks = (n + 127) / 128;
     if (blocks > ctx->sms * 8) blocks = ctx->sms * 8;
+    if (use_net == 2) {
+        k_sampler_quantile_mma<<<(int)blocks, 128, sizeof(SamplerMma), ctx->stream>>>(
+            ctx->d_wbf, log10chi, u, x, n);
+        return cuda_check(ctx, cudaGetLastError(), "qed_sampler_quantile");
+    }
     k_sampler_quantile<<<(int)blocks, 128, use_net ? sizeof(SamplerSmem) : 0, ctx->stream>>>(
         ctx->d_wbf, ctx->d_cdf, kCdfRows, kCdfM, log10chi, u, x, n, use_net);
     return cuda_check(ctx, cudaGetLastError(), "qed_sampler_quantile");
@@ -3215,7 +3527,11 @@ qed_status qed_sampler_evaluate(qed_ctx* ctx, float* bin_err, int nbins) {
     const float half = 0.5f * (kMlpLog10Hi - kMlpLog10Lo) / rows;
     k_cdf_rows<<<rows, 256, 0, ctx->stream>>>(kMlpLog10Lo + half, kMlpLog10Hi - half, rows, kCdfM,
                                               cdf, tot);
+    // both forms of the network the event kernels use: a bin's error is the
+    // larger of the two
     k_sampler_eval<<<rows, 128, sizeof(SamplerSmem), ctx->stream>>>(
+        ctx->d_wbf, cdf, rows, kCdfM, kMlpLog10Lo, kMlpLog10Hi, bits);
+    k_sampler_eval_mma<<<rows, 128, sizeof(SamplerMma), ctx->stream>>>(
         ctx->d_wbf, cdf, rows, kCdfM, kMlpLog10Lo, kMlpLog10Hi, bits);
     unsigned int hb[QED_SAMPLER_BINS];
     st = cuda_check(ctx, cudaMemcpyAsync(hb, bits, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream),

@@ -535,11 +535,252 @@ __device__ __forceinline__ float mlp_infer_warp(SamplerSmem& S, float v0, float 
 
 // Tabulated total probability per c at b = 3 chi / 2 (linear in log10 chi,
 // on the logarithm of the table values); chi must be inside the trained range.
-__device__ __forceinline__ float sampler_wtot(const SamplerSmem& S, float chi) {
-    const float pos = (log10f(chi) - kMlpLog10Lo) / (kMlpLog10Hi - kMlpLog10Lo) * (float)(S.nrows - 1);
-    const int i = min(max((int)pos, 0), S.nrows - 2);
+__device__ __forceinline__ float wtot_at(const float* wtot, int nrows, float chi) {
+    const float pos = (log10f(chi) - kMlpLog10Lo) / (kMlpLog10Hi - kMlpLog10Lo) * (float)(nrows - 1);
+    const int i = min(max((int)pos, 0), nrows - 2);
     const float w = pos - (float)i;
-    return __expf((1.0f - w) * __logf(S.wtot[i]) + w * __logf(S.wtot[i + 1]));
+    return __expf((1.0f - w) * __logf(wtot[i]) + w * __logf(wtot[i + 1]));
+}
+__device__ __forceinline__ float sampler_wtot(const SamplerSmem& S, float chi) {
+    return wtot_at(S.wtot, S.nrows, chi);
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core form of the inference: the 32 lanes of a warp evaluate their 32
+// samples together, one sample (row) per lane, as two tiles of 16 rows through
+// mma.sync m16n8k16 (BF16 x BF16 -> FP32).  The weights are the BF16 values
+// themselves.  Each activation enters the next layer as two BF16 numbers,
+// hi = bf16(a) and lo = bf16(a - hi), with two products per tile, so that the
+// activations keep ~16 significant bits (BF16 activations alone gave a CDF
+// error of 2e-3).  The accumulator fragment of one layer (rows g, g + 8,
+// columns 2t, 2t + 1 of each 8-column tile, g = lane / 4, t = lane % 4) is the
+// A fragment of the next one for the same rows, so activations stay in
+// registers between layers.  A row's result depends on that row's inputs only.
+// ---------------------------------------------------------------------------
+constexpr int kHPad = 72;   // BF16 row stride of W2, W3 ([n][k], 64 + 8): the
+                            // 32-bit fragment loads of a warp hit 32 banks
+
+struct SamplerMma {
+    __align__(16) __nv_bfloat16 W2[kMlpW * kHPad];
+    __align__(16) __nv_bfloat16 W3[kMlpW * kHPad];
+    float W1[kMlpW * 2], b1[kMlpW], b2[kMlpW], b3[kMlpW], w4[kMlpW];
+    float b4;
+    float wtot[1024];
+    unsigned long long bin_ok;
+    int nrows;
+};
+
+__device__ __forceinline__ void stage_sampler_mma(SamplerMma& S, const __nv_bfloat16* __restrict__ w,
+                                                  const float* __restrict__ wtot, int nrows,
+                                                  unsigned long long bin_ok) {
+    for (int i = threadIdx.x; i < kMlpW * kMlpW; i += blockDim.x) {
+        const int n = i / kMlpW, k = i % kMlpW;
+        S.W2[n * kHPad + k] = w[kMlpOffW2 + i];
+        S.W3[n * kHPad + k] = w[kMlpOffW3 + i];
+    }
+    for (int i = threadIdx.x; i < 128; i += blockDim.x) S.W1[i] = __bfloat162float(w[kMlpOffW1 + i]);
+    for (int i = threadIdx.x; i < kMlpW; i += blockDim.x) {
+        S.b1[i] = __bfloat162float(w[kMlpOffB1 + i]);
+        S.b2[i] = __bfloat162float(w[kMlpOffB2 + i]);
+        S.b3[i] = __bfloat162float(w[kMlpOffB3 + i]);
+        S.w4[i] = __bfloat162float(w[kMlpOffW4 + i]);
+    }
+    for (int i = threadIdx.x; i < nrows && i < 1024; i += blockDim.x) S.wtot[i] = wtot[i];
+    if (threadIdx.x == 0) {
+        S.b4 = __bfloat162float(w[kMlpOffB4]);
+        S.bin_ok = bin_ok;
+        S.nrows = nrows;
+    }
+}
+
+// D += A B for one m16n8k16 tile (A: 4 registers of BF16 pairs, B: 2).
+__device__ __forceinline__ void mma_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                          uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// (x0, x1) as BF16 pairs: hi rounds each value, lo rounds what hi leaves.
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);   // .x (low half) = x0
+    const __nv_bfloat162 l =
+        __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+
+// One hidden layer for one 16-row tile: C = W a + b from the A fragments
+// (hi, lo) of the layer below, then SiLU; the result replaces (hi, lo).
+__device__ __forceinline__ void mma_hidden(const __nv_bfloat16* __restrict__ W,
+                                           const float* __restrict__ bias, uint32_t (&Ah)[4][4],
+                                           uint32_t (&Al)[4][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    float C[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float b0 = bias[8 * nt + 2 * t], b1 = bias[8 * nt + 2 * t + 1];
+        C[nt][0] = b0;
+        C[nt][1] = b1;
+        C[nt][2] = b0;
+        C[nt][3] = b1;
+    }
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const __nv_bfloat16* row = W + (8 * nt + g) * kHPad + 16 * kt + 2 * t;
+            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(row);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(row + 8);
+            mma_16816(C[nt], Ah[kt], b0, b1);
+            mma_16816(C[nt], Al[kt], b0, b1);
+        }
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int kt = nt >> 1, q = (nt & 1) * 2;
+        split_bf16x2(silu_fast(C[nt][0]), silu_fast(C[nt][1]), Ah[kt][q], Al[kt][q]);
+        split_bf16x2(silu_fast(C[nt][2]), silu_fast(C[nt][3]), Ah[kt][q + 1], Al[kt][q + 1]);
+    }
+}
+
+// The network's output logit (before b4 and the anchor) for rows g and g + 8
+// of one tile, whose inputs are (v0a, v1a) and (v0b, v1b); every lane of the
+// group g gets both.
+__device__ __forceinline__ void mma_tile(const SamplerMma& S, float v0a, float v1a, float v0b,
+                                         float v1b, float& oa, float& ob) {
+    const int lane = threadIdx.x & 31, t = lane & 3;
+    uint32_t Ah[4][4], Al[4][4];
+    // layer 1 (two inputs) on the CUDA cores, in the fragment layout
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int n = 8 * nt + 2 * t;
+        const float w00 = S.W1[2 * n], w01 = S.W1[2 * n + 1];
+        const float w10 = S.W1[2 * n + 2], w11 = S.W1[2 * n + 3];
+        const float za0 = fmaf(w00, v0a, fmaf(w01, v1a, S.b1[n]));
+        const float za1 = fmaf(w10, v0a, fmaf(w11, v1a, S.b1[n + 1]));
+        const float zb0 = fmaf(w00, v0b, fmaf(w01, v1b, S.b1[n]));
+        const float zb1 = fmaf(w10, v0b, fmaf(w11, v1b, S.b1[n + 1]));
+        const int kt = nt >> 1, q = (nt & 1) * 2;
+        split_bf16x2(silu_fast(za0), silu_fast(za1), Ah[kt][q], Al[kt][q]);
+        split_bf16x2(silu_fast(zb0), silu_fast(zb1), Ah[kt][q + 1], Al[kt][q + 1]);
+    }
+    mma_hidden(S.W2, S.b2, Ah, Al);
+    // layer 3 and the output dot product with w4
+    const int g = lane >> 2;
+    float C[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float b0 = S.b3[8 * nt + 2 * t], b1 = S.b3[8 * nt + 2 * t + 1];
+        C[nt][0] = b0;
+        C[nt][1] = b1;
+        C[nt][2] = b0;
+        C[nt][3] = b1;
+    }
+#pragma unroll
+    for (int kt = 0; kt < 4; ++kt) {
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const __nv_bfloat16* row = S.W3 + (8 * nt + g) * kHPad + 16 * kt + 2 * t;
+            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(row);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(row + 8);
+            mma_16816(C[nt], Ah[kt], b0, b1);
+            mma_16816(C[nt], Al[kt], b0, b1);
+        }
+    }
+    float pa = 0.0f, pb = 0.0f;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const float w0 = S.w4[8 * nt + 2 * t], w1 = S.w4[8 * nt + 2 * t + 1];
+        pa = fmaf(w0, silu_fast(C[nt][0]), fmaf(w1, silu_fast(C[nt][1]), pa));
+        pb = fmaf(w0, silu_fast(C[nt][2]), fmaf(w1, silu_fast(C[nt][3]), pb));
+    }
+    pa += __shfl_xor_sync(0xffffffffu, pa, 1);
+    pa += __shfl_xor_sync(0xffffffffu, pa, 2);
+    pb += __shfl_xor_sync(0xffffffffu, pb, 1);
+    pb += __shfl_xor_sync(0xffffffffu, pb, 2);
+    oa = pa;
+    ob = pb;
+}
+
+// x(v0, v1) for the lanes with `want` set, the others get 0; called by all 32
+// lanes together.  The wanted samples are packed into the first rows (in lane
+// order), so that a warp with at most 16 of them runs one tile: the result of
+// a sample does not depend on its row or on the other rows.  `buf` is this
+// warp's staging area in shared memory.
+struct MmaBuf {
+    float2 in[32];
+    float out[32];
+};
+__device__ __forceinline__ float mlp_infer_mma_some(const SamplerMma& S, MmaBuf& buf, bool want,
+                                                    float v0, float v1) {
+    constexpr unsigned int kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const unsigned int m = __ballot_sync(kAll, want);
+    const int n = __popc(m);
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    if (want) buf.in[rank] = make_float2(v0, v1);
+    __syncwarp();
+    const int tiles = (n + 15) >> 4;
+#pragma unroll 1
+    for (int mt = 0; mt < tiles; ++mt) {
+        const int ra = 16 * mt + g, rb = ra + 8;
+        const float2 a = ra < n ? buf.in[ra] : make_float2(0.0f, 0.0f);
+        const float2 b = rb < n ? buf.in[rb] : make_float2(0.0f, 0.0f);
+        float oa, ob;
+        mma_tile(S, a.x, a.y, b.x, b.y, oa, ob);
+        if (t == 0) {
+            buf.out[ra] = oa;
+            buf.out[rb] = ob;
+        }
+    }
+    __syncwarp();
+    const float o = want ? buf.out[rank] : 0.0f;
+    __syncwarp();   // buf is reused by the next call
+    return want ? sigmoidf_(o + S.b4 + anchor_of_v1(v1)) : 0.0f;
+}
+
+// One sample through the tensor-core form, for a warp that steps one particle
+// (lane 0's inputs; every lane gets x).  Out of line, so that the kernels that
+// call it do not carry its registers on their other paths.
+__device__ __noinline__ float mlp_infer_mma_one(const SamplerMma& S, MmaBuf& buf, float v0,
+                                                float v1) {
+    const float x = mlp_infer_mma_some(S, buf, (threadIdx.x & 31) == 0, v0, v1);
+    return __shfl_sync(0xffffffffu, x, 0);
+}
+
+// Dynamic shared memory of the event kernels in a sampler mode: mode 1 the
+// FP32 form (SamplerSmem), mode 2 the tensor-core form (SamplerMma) followed by
+// one MmaBuf per warp (up to 8 warps per block).
+constexpr size_t kMmaSmemBytes = sizeof(SamplerMma) + 8 * sizeof(MmaBuf);
+constexpr size_t kNetSmemBytes =
+    sizeof(SamplerSmem) > kMmaSmemBytes ? sizeof(SamplerSmem) : kMmaSmemBytes;
+__device__ __forceinline__ MmaBuf& warp_mma_buf(unsigned char* dyn) {
+    return reinterpret_cast<MmaBuf*>(dyn + sizeof(SamplerMma))[(threadIdx.x >> 5) & 7];
+}
+
+// x(v0, v1) for the sample of every lane; called by all 32 lanes together.
+__device__ __forceinline__ float mlp_infer_mma(const SamplerMma& S, float v0, float v1) {
+    constexpr unsigned int kAll = 0xffffffffu;
+    const int lane = threadIdx.x & 31, g = lane >> 2;
+    float out = 0.0f;
+#pragma unroll 1
+    for (int mt = 0; mt < 2; ++mt) {
+        // rows 16 mt + g and 16 mt + g + 8 are the samples of those lanes
+        const int ra = 16 * mt + g, rb = ra + 8;
+        const float v0a = __shfl_sync(kAll, v0, ra), v1a = __shfl_sync(kAll, v1, ra);
+        const float v0b = __shfl_sync(kAll, v0, rb), v1b = __shfl_sync(kAll, v1, rb);
+        float oa, ob;
+        mma_tile(S, v0a, v1a, v0b, v1b, oa, ob);
+        // lane 16 mt + r takes its row from lane 4 (r % 8), first of group r % 8
+        const int src = 4 * (lane & 7);
+        const float ga = __shfl_sync(kAll, oa, src), gb = __shfl_sync(kAll, ob, src);
+        if ((lane >> 4) == mt) out = (lane & 8) ? gb : ga;
+    }
+    return sigmoidf_(out + S.b4 + anchor_of_v1(v1));
 }
 
 }  // namespace qed

@@ -19,7 +19,7 @@ QED_OK, QED_ERR_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY, QED_ERR_TIMEOUT, QED_ERR_ST
 PROC_EMISSION, PROC_PAIR = 1, 2
 ELECTRON, POSITRON, PHOTON, REMOVED = 0, 1, 2, 3
 FLOAT_FIELDS = ("px", "py", "pz", "Ex", "Ey", "Ez", "Bx", "By", "Bz", "w")
-KERNEL_KINDS = ("sweep", "generate", "plan", "cold", "hot", "control")
+KERNEL_KINDS = ("sweep", "generate", "plan", "cold", "hot", "control", "sampler")
 SPECTRUM_BINS, SPECTRUM_LOG10_MIN, SPECTRUM_LOG10_MAX = 240, -4, 8
 SAMPLER_PARAMS, SAMPLER_BINS = 8577, 64
 
@@ -379,8 +379,11 @@ class Context:
                                                _ptr(loss)))
 
     def sampler_quantile(self, log10chi, u, x, use_net=True):
+        """use_net: False the exact table inverse, True the network (FP32
+        activations), "mma" the network on the tensor cores."""
+        mode = 2 if use_net == "mma" else int(bool(use_net))
         self._check(lib().qed_sampler_quantile(self._h, _ptr(log10chi), _ptr(u), _ptr(x),
-                                               int(x.numel()), int(bool(use_net))))
+                                               int(x.numel()), mode))
 
     def sampler_load(self, params):
         a = np.ascontiguousarray(params, dtype=np.float32)

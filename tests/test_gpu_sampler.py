@@ -66,6 +66,31 @@ def test_network_inference_matches_oracle_network():
     assert np.median(d) < 1e-5 and d.max() < 1e-4
 
 
+def test_tensor_core_inference_matches_oracle_network():
+    # the event-driven sampler's arithmetic for the network (mma.sync BF16 x
+    # BF16 -> FP32, activations as BF16 hi + lo pairs, ~16 significant bits)
+    # against the FP64 oracle network with the same BF16-rounded weights, on
+    # a ragged size (the last warp's extra lanes compute and drop a value)
+    ctx = qed.Context()
+    rng = np.random.default_rng(13)
+    th = mlp.init(22)
+    th_bf = torch.from_numpy(th.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    ctx.sampler_load(th.astype(np.float32))
+    n = 4099
+    l10 = rng.uniform(-2, 2, n).astype(np.float32)
+    u = rng.uniform(1e-6, 1 - 1e-6, n).astype(np.float32)
+    x = torch.zeros(n, device="cuda")
+    ctx.sampler_quantile(_dev(l10), _dev(u), x, use_net="mma")
+    ref, _ = mlp.forward(th_bf, mlp.inputs(l10.astype(np.float64), u.astype(np.float64)))
+    d = np.abs(x.cpu().numpy().astype(np.float64) - ref)
+    print("tensor-core inference vs FP64 network: median %.2e max %.2e" % (np.median(d), d.max()))
+    assert np.median(d) < 1e-5 and d.max() < 1e-4
+    # a sample's result does not depend on its neighbours in the warp
+    x2 = torch.zeros(n - 7, device="cuda")
+    ctx.sampler_quantile(_dev(l10[7:]), _dev(u[7:]), x2, use_net="mma")
+    np.testing.assert_array_equal(x2.cpu().numpy(), x.cpu().numpy()[7:])
+
+
 def _oracle_cdf(b, x):
     """int_0^x 3x'^2 P(x'^3) dx' / int_0^1 (oracle acceptance function, Gauss-Legendre)."""
     xs, ws = np.polynomial.legendre.leggauss(24)
