@@ -109,6 +109,8 @@ typedef struct {
     int32_t tail;              /* 1: the step's last generations ran as the tail pass */
     uint64_t substeps_warp;    /* of `substeps`, those run by the hot pass and the tail pass's persistent kernel */
     uint64_t sampler_events;   /* emissions whose energy came from the learned sampler */
+    uint64_t sampler_pairs;    /* pair events whose electron fraction came from the
+                                  learned pair sampler */
 } qed_step_stats;
 
 /* One event, written to the optional device event log (validation). */
@@ -298,6 +300,19 @@ qed_status qed_graph_read_stats(qed_ctx* ctx, qed_step_stats* out, int nsteps);
  * most cfg.sampler_max_err. */
 #define QED_SAMPLER_PARAMS 8577
 #define QED_SAMPLER_BINS 64
+
+/* The learned samplers are two networks of the same form: for photon emission
+ * (x = delta^{1/3} of Eq. 1, the default) and for pair production (x =
+ * delta_e, the electron's energy fraction of Eq. 2, a spectrum symmetric
+ * about 1/2).  qed_sampler_train, _evaluate, _gradient, _quantile, _load and
+ * _save address the network chosen here (QED_PROC_EMISSION or
+ * QED_PROC_PAIR).  In sampler_mode 2 the event step uses the pair network,
+ * once trained and evaluated, for photon plans with a nonzero squeeze
+ * threshold, at least hot_min sub-steps and chi_gamma in a usable bin: the
+ * sub-steps to the decay are drawn at once from the tabulated total pair
+ * probability and delta_e comes from the network; all other photon plans
+ * keep rejection.  Errors: QED_ERR_ARG. */
+qed_status qed_sampler_process(qed_ctx* ctx, uint32_t process);
 
 /* Train with Adam (cosine-decayed step `lr`) on `samples` pairs drawn in
  * batches of `batch` (64 <= batch <= 2^20): log10 chi and u uniform, target x

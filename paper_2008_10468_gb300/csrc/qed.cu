@@ -67,6 +67,7 @@ struct DevCtl {
     unsigned long long substeps, emissions, pairs, children, guard_hits, plans, candidates;
     unsigned long long substeps_warp;
     unsigned long long sampler_events;
+    unsigned long long sampler_pairs;
     unsigned int max_N;
     int status;
     long long required;
@@ -128,7 +129,7 @@ struct Scratch {
 // stays far below 2^32); summed per warp and added to the control block.
 struct Stats {
     unsigned int substeps = 0, emissions = 0, pairs = 0, children = 0, guard = 0, plans = 0,
-                 cand = 0, warp_substeps = 0, sampled = 0;
+                 cand = 0, warp_substeps = 0, sampled = 0, sampled_p = 0;
     unsigned int max_N = 0;
 };
 
@@ -148,7 +149,7 @@ __device__ void flush_stats(const Stats& st, DevCtl* ctl) {
                              c = warp_sum(st.pairs), d = warp_sum(st.children),
                              e = warp_sum(st.guard), f = warp_sum(st.plans), g = warp_sum(st.cand),
                              h = warp_sum(st.warp_substeps),  // 64-bit sums of 32-bit counters
-                             q = warp_sum(st.sampled);
+                             q = warp_sum(st.sampled), qp = warp_sum(st.sampled_p);
     const unsigned int m = warp_max(st.max_N);
     if ((threadIdx.x & 31) == 0) {
         if (a) atomicAdd(&ctl->substeps, a);
@@ -160,6 +161,7 @@ __device__ void flush_stats(const Stats& st, DevCtl* ctl) {
         if (g) atomicAdd(&ctl->candidates, g);
         if (h) atomicAdd(&ctl->substeps_warp, h);
         if (q) atomicAdd(&ctl->sampler_events, q);
+        if (qp) atomicAdd(&ctl->sampler_pairs, qp);
         if (m) atomicMax(&ctl->max_N, m);
     }
 }
@@ -498,6 +500,16 @@ __device__ __forceinline__ bool sampler_bin_ok(const StepParams& SP, float chi) 
     return (SP.net_bins >> bin) & 1ull;
 }
 
+// With the event-driven sampler, photons whose plan has candidates (a nonzero
+// squeeze threshold) and whose chi_gamma lies in a usable bin of the pair
+// sampler decide their decay from the tabulated total pair probability and
+// take delta_e from the pair network.
+__device__ __forceinline__ bool pair_sampler_ok(const StepParams& SP, float chi, uint32_t T) {
+    if (!SP.pnet_bins || T == 0u || !(chi >= 1e-2f && chi < 1e2f)) return false;
+    const int bin = min(max((int)((log10f(chi) - kMlpLog10Lo) * 16.0f), 0), 63);
+    return (SP.pnet_bins >> bin) & 1ull;
+}
+
 // Graph runs keep the global step index as a device base plus the node's
 // offset, so that relaunching a graph continues with new step indices.
 __device__ __forceinline__ uint32_t step_index(const StepParams& SP) {
@@ -659,7 +671,8 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                         // sampler's particles are stepped by a whole warp,
                         // the others by a lane (the event-driven sampler's
                         // particles one lane each, in their own queue)
-                        const bool net = !photon && sampler_bin_ok(SP, chi);
+                        const bool net = photon ? pair_sampler_ok(SP, chi, pl.T)
+                                                : sampler_bin_ok(SP, chi);
                         if (net && S.samp) {
                             HotItem it;
                             it.idx = (uint32_t)i;
@@ -1028,9 +1041,13 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
             stats.guard += pl.guard ? 1 : 0;
             stats.max_N = max(stats.max_N, pl.N);
         }
-        const bool use_net = kSampler != 0 && !photon && sampler_bin_ok(SP, chi);
+        // event-driven mode: photons in a usable bin of the pair sampler too
+        const bool use_pnet =
+            kSampler == 2 && photon && pl.N >= SP.hot_min && pair_sampler_ok(SP, chi, pl.T);
+        const bool use_net = (kSampler != 0 && !photon && sampler_bin_ok(SP, chi)) || use_pnet;
+        const SamplerMma& tab = use_pnet ? pair_mma(net_smem) : mma;
         const float thr =
-            use_net ? fminf(pl.c_h * (kSampler == 2 ? wtot_at(mma.wtot, mma.nrows, chi)
+            use_net ? fminf(pl.c_h * (kSampler == 2 ? wtot_at(tab.wtot, tab.nrows, chi)
                                                     : sampler_wtot(net, chi)),
                             1.0f)
                     : 0.0f;
@@ -1061,11 +1078,12 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
                 const uint32_t s_ev = s + k;
                 const uint32_t k_ev = kdone + k;
                 // the tensor-core form, as in k_samp (one sample: one tile)
-                const float x = mlp_infer_mma_one(mma, warp_mma_buf(net_smem),
+                const float x = mlp_infer_mma_one(tab, warp_mma_buf(net_smem),
                                                   log10f(chi) * 0.5f, mlp_input_u(u01(r.x)));
                 if (lane == 0) {
                     stats.substeps += k + 1;
-                    stats.sampled++;
+                    if (photon) stats.sampled_p++;
+                    else stats.sampled++;
                 }
                 const ftime t_after = (k_ev + 1 == pl.N) ? ftime{0.0f, 0.0f}
                                                          : time_sub_mul(t_rem, k_ev + 1, pl.h);
@@ -1173,35 +1191,28 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
 // sampler's usable bins continues with rejection: its state goes back to the
 // store and it joins the hot pass's queue (the hot pass runs after this
 // kernel).  Idle lanes take queue entries, one atomic per warp.  Persistent.
-constexpr unsigned int kSampPerLane = 8;
 __global__ void __launch_bounds__(kLaneThreads) k_samp(DevParticles P, StepParams SP, Scratch S,
                                                        DevCtl* ctl) {
     const uint32_t step = step_index(SP);
     __shared__ SharedTables sm;
     __shared__ float fld[6][kLaneThreads];   // E, B at the lane's row
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    SamplerMma& net = *reinterpret_cast<SamplerMma*>(dyn_smem);
+    SamplerMma& net = *reinterpret_cast<SamplerMma*>(dyn_smem);   // emission
+    SamplerMma& pnet = pair_mma(dyn_smem);                           // pair production
     stage_tables(sm);
     stage_sampler_mma(net, reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
                       SP.net_rows, SP.net_bins);
+    if (SP.pnet_bins)
+        stage_sampler_mma(pnet, reinterpret_cast<const __nv_bfloat16*>(SP.pnet_w), SP.pnet_wtot,
+                          SP.net_rows, SP.pnet_bins);
     __syncthreads();
     if (ctl->status == (int)QED_ERR_TIMEOUT) return;
     constexpr unsigned int kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t kw0 = (uint32_t)SP.seed ^ kWaitKeyLo, kw1 = (uint32_t)(SP.seed >> 32) ^ kWaitKeyHi;
     const unsigned int tail = ctl->samp_tail;
-    // as many warps as keep their lanes busy: about kSampPerLane particles per
-    // lane (chains average a few events), spread over every block, at least a
-    // quarter of the launched warps; the others leave at once
-    {
-        const unsigned int wpb = blockDim.x >> 5;
-        const unsigned int need = max((tail + 32u * kSampPerLane - 1u) / (32u * kSampPerLane),
-                                      gridDim.x * wpb / 4u);
-        const unsigned int per_block = (need + gridDim.x - 1u) / gridDim.x;
-        if ((threadIdx.x >> 5) >= per_block) return;
-    }
     Stats stats;
-    bool active = false, more = true;
+    bool active = false, more = true, photon = false;
     uint32_t i = 0, s = 0;
     uint64_t id = 0;
     PState st{0.0f, 0.0f, 0.0f};
@@ -1209,26 +1220,32 @@ __global__ void __launch_bounds__(kLaneThreads) k_samp(DevParticles P, StepParam
     Plan pl;
     pl.N = 0;
     float chi = 0.0f, eps = 0.0f, thr = 0.0f;
+    bool removed = false;
     // after a load or an event: plan the remaining time; false if the lane
     // is done with the particle (no time left, or handed to rejection)
     auto plan_lane = [&]() -> bool {
-        pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, false, st.px, st.py, st.pz,
+        pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz,
                            fld[0][threadIdx.x], fld[1][threadIdx.x], fld[2][threadIdx.x],
                            fld[3][threadIdx.x], fld[4][threadIdx.x], fld[5][threadIdx.x], t_rem,
                            &chi, &eps);
         if (!(eps > 0.0f)) return false;
         stats.max_N = max(stats.max_N, pl.N);
-        if (!sampler_bin_ok(SP, chi)) {
+        const bool usable = photon ? pl.N >= SP.hot_min && pair_sampler_ok(SP, chi, pl.T)
+                                   : sampler_bin_ok(SP, chi);
+        if (!usable) {
             // rejection from here on: the hot pass plans again from the store
-            P.px[i] = st.px;
-            P.py[i] = st.py;
-            P.pz[i] = st.pz;
+            if (!photon) {
+                P.px[i] = st.px;
+                P.py[i] = st.py;
+                P.pz[i] = st.pz;
+            }
             push_hot(S, ctl, i, s, t_rem, pl.N >= SP.long_min);
             return false;
         }
         stats.plans++;
         stats.guard += pl.guard ? 1 : 0;
-        thr = fminf(pl.c_h * wtot_at(net.wtot, net.nrows, chi), 1.0f);
+        const SamplerMma& tab = photon ? pnet : net;
+        thr = fminf(pl.c_h * wtot_at(tab.wtot, tab.nrows, chi), 1.0f);
         return true;
     };
     while (true) {
@@ -1246,6 +1263,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_samp(DevParticles P, StepParam
                         i = it.idx;
                         s = it.s;
                         t_rem = it.t_rem;
+                        photon = P.type[i] == QED_PHOTON;
                         id = P.id[i];
                         st = PState{P.px[i], P.py[i], P.pz[i]};
                         fld[0][threadIdx.x] = P.Ex[i];
@@ -1282,28 +1300,38 @@ __global__ void __launch_bounds__(kLaneThreads) k_samp(DevParticles P, StepParam
             }
         }
         if (__any_sync(kAll, ev)) {
-            // the photon's row, reserved first (one atomic for the warp's
-            // events) so that the atomic's latency overlaps the network
+            // the child rows (one photon, or an e- and an e+), reserved first
+            // (one atomic for the warp's events) so that the atomic's latency
+            // overlaps the network
             long long j = -1;
-            if (ev) j = reserve_rows(P, ctl, 1, true);
-            // the network for the lanes with an event, packed into one tile
-            // when at most 16 have one
-            const float x = mlp_infer_mma_some(net, warp_mma_buf(dyn_smem), ev,
-                                               log10f(chi) * 0.5f, mlp_input_u(u_net));
+            if (ev) j = reserve_rows(P, ctl, photon ? 2 : 1, true);
+            // the emission and the pair network for the lanes with such an
+            // event, each packed into one tile when at most 16 have one
+            const float v0 = log10f(chi) * 0.5f, v1 = mlp_input_u(u_net);
+            float x = 0.0f;
+            if (__any_sync(kAll, ev && !photon))
+                x = mlp_infer_mma_some(net, warp_mma_buf(dyn_smem), ev && !photon, v0, v1);
+            if (__any_sync(kAll, ev && photon)) {
+                const float xp = mlp_infer_mma_some(pnet, warp_mma_buf(dyn_smem), ev && photon,
+                                                    v0, v1);
+                if (photon) x = xp;
+            }
             if (ev) {
                 const uint32_t s_ev = s + k;
                 stats.substeps += k + 1;
-                stats.sampled++;
+                if (photon) stats.sampled_p++;
+                else stats.sampled++;
                 const ftime t_after = (k + 1 == pl.N) ? ftime{0.0f, 0.0f}
                                                       : time_sub_mul(t_rem, k + 1, pl.h);
-                apply_event(P, S, SP, ctl, i, id, false, x, eps, chi, step, s_ev, t_after, st,
-                            stats, true, false,
-                            Fields{fld[0][threadIdx.x], fld[1][threadIdx.x], fld[2][threadIdx.x],
-                                   fld[3][threadIdx.x], fld[4][threadIdx.x], fld[5][threadIdx.x]},
-                            false, j);
+                removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps, chi, step, s_ev,
+                                      t_after, st, stats, true, false,
+                                      Fields{fld[0][threadIdx.x], fld[1][threadIdx.x],
+                                             fld[2][threadIdx.x], fld[3][threadIdx.x],
+                                             fld[4][threadIdx.x], fld[5][threadIdx.x]},
+                                      false, j);
                 s = s_ev + 1;
                 t_rem = t_after;
-                if (!time_positive(t_rem)) {
+                if (removed || !time_positive(t_rem)) {
                     done = true;
                 } else if (!plan_lane()) {
                     active = false;   // handed to rejection, or no energy left
@@ -1311,9 +1339,14 @@ __global__ void __launch_bounds__(kLaneThreads) k_samp(DevParticles P, StepParam
             }
         }
         if (done) {
-            P.px[i] = st.px;
-            P.py[i] = st.py;
-            P.pz[i] = st.pz;
+            if (removed) {
+                P.type[i] = QED_REMOVED;   // a decayed photon (Algorithm 2)
+            } else if (!photon) {
+                P.px[i] = st.px;
+                P.py[i] = st.py;
+                P.pz[i] = st.pz;
+            }
+            removed = false;
             active = false;
         }
     }
@@ -1347,10 +1380,14 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
         stage_sampler(*reinterpret_cast<SamplerSmem*>(dyn_smem),
                       reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot, SP.net_rows,
                       SP.net_bins);
-    else if (kSampler == 2)
+    else if (kSampler == 2) {
         stage_sampler_mma(*reinterpret_cast<SamplerMma*>(dyn_smem),
                           reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
                           SP.net_rows, SP.net_bins);
+        if (SP.pnet_bins)
+            stage_sampler_mma(pair_mma(dyn_smem), reinterpret_cast<const __nv_bfloat16*>(SP.pnet_w),
+                              SP.pnet_wtot, SP.net_rows, SP.pnet_bins);
+    }
     __syncthreads();
     if (ctl->status == (int)QED_ERR_TIMEOUT) return;
     constexpr unsigned int kAll = 0xffffffffu;
@@ -1550,10 +1587,14 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
         stage_sampler(*reinterpret_cast<SamplerSmem*>(dyn_smem),
                       reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot, SP.net_rows,
                       SP.net_bins);
-    else if (kSampler == 2)
+    else if (kSampler == 2) {
         stage_sampler_mma(*reinterpret_cast<SamplerMma*>(dyn_smem),
                           reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
                           SP.net_rows, SP.net_bins);
+        if (SP.pnet_bins)
+            stage_sampler_mma(pair_mma(dyn_smem), reinterpret_cast<const __nv_bfloat16*>(SP.pnet_w),
+                              SP.pnet_wtot, SP.net_rows, SP.pnet_bins);
+    }
     __syncthreads();
     if (ctl->skip) return;
     constexpr unsigned int kAll = 0xffffffffu;
@@ -1728,7 +1769,9 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
                     ++done;
                 } else {
                     stats.max_N = max(stats.max_N, pl.N);
-                    if (pl.N >= SP.long_min || (!photon && sampler_bin_ok(SP, chi))) {
+                    if (pl.N >= SP.long_min || (!photon && sampler_bin_ok(SP, chi)) ||
+                        (kSampler == 2 && photon && pl.N >= SP.hot_min &&
+                         pair_sampler_ok(SP, chi, pl.T))) {
                         push_long(S, ctl, cold_long, i, s, t_rem);   // the warp mode plans again
                     } else {
                         stats.plans++;
@@ -1820,7 +1863,9 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
                         fin = true;
                     } else {
                         stats.max_N = max(stats.max_N, pl.N);
-                        if (pl.N >= SP.long_min || (!photon && sampler_bin_ok(SP, chi))) {
+                        if (pl.N >= SP.long_min || (!photon && sampler_bin_ok(SP, chi)) ||
+                        (kSampler == 2 && photon && pl.N >= SP.hot_min &&
+                         pair_sampler_ok(SP, chi, pl.T))) {
                             // continue in the warp mode; its state goes with the row
                             P.px[i] = st.px;
                             P.py[i] = st.py;
@@ -2001,6 +2046,7 @@ __global__ void k_step_close(DevCtl* ctl, const long long* count, qed_step_stats
         r.tail = c.tail;
         r.substeps_warp = c.substeps_warp;
         r.sampler_events = c.sampler_events;
+        r.sampler_pairs = c.sampler_pairs;
         *rec = r;
     }
     if (c.status != 0 && c.sticky == 0) ctl->sticky = c.status;
@@ -2174,6 +2220,19 @@ __global__ void k_compact_finish(DevParticles P, const DevCtl* ctl) {
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// One learned sampler's state (context-owned).
+struct NetState {
+    float* d_theta;            // FP32 master parameters
+    float* d_m1;               // Adam moments
+    float* d_m2;
+    __nv_bfloat16* d_wbf;      // BF16 copy used by the event kernels
+    float* d_cdf;              // exact CDF rows (training targets)
+    float* d_wtot;             // total probability per c along log10 chi
+    int net_ready;             // parameters loaded or trained
+    unsigned long long net_bins;
+    long long adam_t;
+};
+
 struct qed_ctx {
     qed_config cfg;
     cudaStream_t stream;
@@ -2205,20 +2264,14 @@ struct qed_ctx {
     long long mirror_cap;
     unsigned int* d_block_live;
     double* d_hist;
-    // learned sampler
-    float* d_theta;            // FP32 master parameters
-    float* d_m1;               // Adam moments
-    float* d_m2;
-    __nv_bfloat16* d_wbf;      // BF16 copy used by the event kernels
-    float* d_cdf;              // exact CDF rows (training targets)
-    float* d_wtot;             // total probability per c along log10 chi
+    // learned samplers: nets[0] emission (Eq. 1), nets[1] pair production
+    // (Eq. 2); net_sel is the one the qed_sampler_* calls address
+    NetState nets[2];
+    int net_sel;
     float* d_partial;          // per-block partial gradients
     float* d_batch;            // training inputs (2 per sample), targets and weights
     int batch_cap;
     float* d_loss;
-    int net_ready;             // parameters loaded or trained
-    unsigned long long net_bins;
-    long long adam_t;
     // multi-step graph
     cudaGraph_t graph;
     cudaGraphExec_t graph_exec;
@@ -2287,6 +2340,9 @@ StepParams make_params(const qed_config& c, uint64_t step) {
     P.net_bins = 0;
     P.net_w = nullptr;
     P.net_wtot = nullptr;
+    P.pnet_bins = 0;
+    P.pnet_w = nullptr;
+    P.pnet_wtot = nullptr;
     P.step = (uint32_t)step;
     P.process_mask = c.process_mask;
     P.recoil = c.recoil;
@@ -2457,6 +2513,7 @@ void fill_stats(const DevCtl& c, qed_step_stats* out, long long count) {
     out->tail = c.tail;
     out->substeps_warp = c.substeps_warp;
     out->sampler_events = c.sampler_events;
+    out->sampler_pairs = c.sampler_pairs;
 }
 
 }  // namespace
@@ -2528,6 +2585,8 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push, kLaneThreads, 0);
         ctx->push_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
+        cudaFuncSetAttribute(k_samp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kMmaSmemBytes);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_samp, kLaneThreads,
                                                       kMmaSmemBytes);
         ctx->samp_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
@@ -2567,8 +2626,12 @@ qed_status qed_destroy(qed_ctx* ctx) {
     if (ctx->mirror.type) cudaFree(ctx->mirror.type);
     if (ctx->d_block_live) cudaFree(ctx->d_block_live);
     if (ctx->d_hist) cudaFree(ctx->d_hist);
-    void* sp[] = {ctx->d_theta, ctx->d_m1, ctx->d_m2, ctx->d_wbf, ctx->d_cdf, ctx->d_wtot,
-                  ctx->d_partial, ctx->d_batch, ctx->d_loss};
+    for (NetState& N : ctx->nets) {
+        void* np[] = {N.d_theta, N.d_m1, N.d_m2, N.d_wbf, N.d_cdf, N.d_wtot};
+        for (void* a : np)
+            if (a) cudaFree(a);
+    }
+    void* sp[] = {ctx->d_partial, ctx->d_batch, ctx->d_loss};
     for (void* a : sp)
         if (a) cudaFree(a);
     delete ctx;
@@ -3165,6 +3228,7 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
     putf(SPin.t_step.hi); putf(SPin.t_step.lo);
     put(SPin.hot_min); put(SPin.long_min); put((uint64_t)SPin.sampler); put((uint64_t)SPin.net_rows);
     put(SPin.net_bins); putp(SPin.net_w); putp(SPin.net_wtot); put(SPin.process_mask);
+    put(SPin.pnet_bins); putp(SPin.pnet_w); putp(SPin.pnet_wtot);
     put((uint64_t)SPin.recoil); put((uint64_t)SPin.cascade); put(SPin.wait_ns);
     { uint64_t b; memcpy(&b, &SPin.lambda_m, 8); put(b); }
     put((uint64_t)ctx->cold_blocks); put((uint64_t)ctx->hot_blocks); put((uint64_t)ctx->net_blocks);
@@ -3252,26 +3316,31 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
 namespace {
 
 constexpr int kCdfRows = 1024;      // rows of the exact CDF along log10 chi in [-2, 2]
+constexpr float kPairLog10Lo = -0.60206f;   // log10 0.25: lower end of the pair network's training
 constexpr int kCdfM = 4096;         // x intervals per row
 constexpr int kEvalSub = 4;         // evaluation rows per error bin
 constexpr int kEvalU = 1024;        // evaluation points in u per row
 
+// The network the qed_sampler_* calls address (qed_sampler_process).
+NetState& cur_net(qed_ctx* ctx) { return ctx->nets[ctx->net_sel]; }
+
 qed_status sampler_alloc(qed_ctx* ctx, int max_batch) {
-    if (!ctx->d_theta) {
-        QED_CUDA(ctx, cudaMalloc(&ctx->d_theta, sizeof(float) * kMlpParams));
-        QED_CUDA(ctx, cudaMalloc(&ctx->d_m1, sizeof(float) * kMlpParams));
-        QED_CUDA(ctx, cudaMalloc(&ctx->d_m2, sizeof(float) * kMlpParams));
-        QED_CUDA(ctx, cudaMalloc(&ctx->d_wbf, sizeof(__nv_bfloat16) * kMlpParams));
+    if (!cur_net(ctx).d_theta) {
+        QED_CUDA(ctx, cudaMalloc(&cur_net(ctx).d_theta, sizeof(float) * kMlpParams));
+        QED_CUDA(ctx, cudaMalloc(&cur_net(ctx).d_m1, sizeof(float) * kMlpParams));
+        QED_CUDA(ctx, cudaMalloc(&cur_net(ctx).d_m2, sizeof(float) * kMlpParams));
+        QED_CUDA(ctx, cudaMalloc(&cur_net(ctx).d_wbf, sizeof(__nv_bfloat16) * kMlpParams));
         QED_CUDA(ctx, cudaMalloc(&ctx->d_partial, sizeof(float) * kMlpParams * ctx->sms * 2));
         QED_CUDA(ctx, cudaMalloc(&ctx->d_loss, sizeof(float)));
         QED_CUDA(ctx, cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)sizeof(TrainSmem)));
     }
-    if (!ctx->d_cdf) {
-        QED_CUDA(ctx, cudaMalloc(&ctx->d_cdf, sizeof(float) * kCdfRows * (kCdfM + 1)));
-        QED_CUDA(ctx, cudaMalloc(&ctx->d_wtot, sizeof(float) * kCdfRows));
+    if (!cur_net(ctx).d_cdf) {
+        QED_CUDA(ctx, cudaMalloc(&cur_net(ctx).d_cdf, sizeof(float) * kCdfRows * (kCdfM + 1)));
+        QED_CUDA(ctx, cudaMalloc(&cur_net(ctx).d_wtot, sizeof(float) * kCdfRows));
         k_cdf_rows<<<kCdfRows, 256, 0, ctx->stream>>>(kMlpLog10Lo, kMlpLog10Hi, kCdfRows, kCdfM,
-                                                      ctx->d_cdf, ctx->d_wtot);
+                                                      ctx->net_sel, cur_net(ctx).d_cdf,
+                                                      cur_net(ctx).d_wtot);
         QED_CUDA(ctx, cudaGetLastError());
     }
     if (max_batch > 0 && ctx->d_batch && ctx->batch_cap < max_batch) {
@@ -3287,13 +3356,21 @@ qed_status sampler_alloc(qed_ctx* ctx, int max_batch) {
 
 qed_status sampler_params(qed_ctx* ctx, StepParams* SP) {
     if (!ctx->cfg.sampler_mode) return QED_OK;
-    if (!ctx->net_ready || !ctx->d_wtot)
+    const NetState& E = ctx->nets[0];
+    if (!E.net_ready || !E.d_wtot)
         return set_err(ctx, QED_ERR_STATE, "sampler_mode set but no sampler trained or loaded");
     SP->sampler = ctx->cfg.sampler_mode;   // 1: per sub-step, 2: event-driven
     SP->net_rows = kCdfRows;
-    SP->net_bins = ctx->net_bins;
-    SP->net_w = ctx->d_wbf;
-    SP->net_wtot = ctx->d_wtot;
+    SP->net_bins = E.net_bins;
+    SP->net_w = E.d_wbf;
+    SP->net_wtot = E.d_wtot;
+    // the pair sampler (event-driven mode only), once trained and evaluated
+    const NetState& Q = ctx->nets[1];
+    if (SP->sampler == 2 && Q.net_ready && Q.d_wtot && Q.net_bins) {
+        SP->pnet_bins = Q.net_bins;
+        SP->pnet_w = Q.d_wbf;
+        SP->pnet_wtot = Q.d_wtot;
+    }
     return QED_OK;
 }
 
@@ -3343,8 +3420,8 @@ __device__ float mlp_infer_thread(const SamplerSmem& S, float v0, float v1) {
 // Max |CDF(chi, x_net(chi, u)) - u| per bin over kEvalSub rows per bin and a
 // uniform grid of u; rows of `cdf` are the evaluation rows.
 __global__ void k_sampler_eval(const __nv_bfloat16* __restrict__ w, const float* __restrict__ cdf,
-                               int nrows, int M, float log10_lo, float log10_hi,
-                               unsigned int* __restrict__ bin_err_bits) {
+                               const float* __restrict__ tot, int nrows, int M, float log10_lo,
+                               float log10_hi, unsigned int* __restrict__ bin_err_bits) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     SamplerSmem& S = *reinterpret_cast<SamplerSmem*>(dyn_smem);
     stage_sampler(S, w, cdf, 0, 0ull);
@@ -3360,6 +3437,7 @@ __global__ void k_sampler_eval(const __nv_bfloat16* __restrict__ w, const float*
         const float c = cdf_row_at(cdf + (size_t)row * (M + 1), M, x);
         worst = fmaxf(worst, fabsf(c - u));
     }
+    if (!(tot[row] > 0.0f)) worst = 1.0f;   // no probability to sample
     atomicMax(&bin_err_bits[bin], __float_as_uint(worst));
 }
 
@@ -3367,8 +3445,9 @@ __global__ void k_sampler_eval(const __nv_bfloat16* __restrict__ w, const float*
 // event-driven sampler's arithmetic): each lane evaluates its own u, the warp
 // together.
 __global__ void k_sampler_eval_mma(const __nv_bfloat16* __restrict__ w,
-                                   const float* __restrict__ cdf, int nrows, int M, float log10_lo,
-                                   float log10_hi, unsigned int* __restrict__ bin_err_bits) {
+                                   const float* __restrict__ cdf, const float* __restrict__ tot,
+                                   int nrows, int M, float log10_lo, float log10_hi,
+                                   unsigned int* __restrict__ bin_err_bits) {
     extern __shared__ __align__(16) unsigned char dyn_smem[];
     SamplerMma& S = *reinterpret_cast<SamplerMma*>(dyn_smem);
     stage_sampler_mma(S, w, nullptr, 0, 0ull);
@@ -3385,6 +3464,7 @@ __global__ void k_sampler_eval_mma(const __nv_bfloat16* __restrict__ w,
         const float c = cdf_row_at(cdf + (size_t)row * (M + 1), M, x);
         worst = fmaxf(worst, fabsf(c - u));
     }
+    if (!(tot[row] > 0.0f)) worst = 1.0f;   // no probability to sample
     atomicMax(&bin_err_bits[bin], __float_as_uint(worst));
 }
 
@@ -3437,23 +3517,30 @@ __global__ void k_sampler_quantile(const __nv_bfloat16* __restrict__ w, const fl
 
 extern "C" {
 
+qed_status qed_sampler_process(qed_ctx* ctx, uint32_t process) {
+    if (!ctx || (process != QED_PROC_EMISSION && process != QED_PROC_PAIR))
+        return set_err(ctx, QED_ERR_ARG, "qed_sampler_process: bad argument");
+    ctx->net_sel = process == QED_PROC_PAIR ? 1 : 0;
+    return QED_OK;
+}
+
 qed_status qed_sampler_quantile(qed_ctx* ctx, const float* log10chi, const float* u, float* x,
                                 int64_t n, int use_net) {
     if (!ctx || n < 0 || (n > 0 && (!log10chi || !u || !x)))
         return set_err(ctx, QED_ERR_ARG, "qed_sampler_quantile: bad argument");
     if (use_net < 0 || use_net > 2) return set_err(ctx, QED_ERR_ARG, "qed_sampler_quantile: use_net");
-    if (use_net && !ctx->net_ready) return set_err(ctx, QED_ERR_STATE, "no sampler trained or loaded");
+    if (use_net && !cur_net(ctx).net_ready) return set_err(ctx, QED_ERR_STATE, "no sampler trained or loaded");
     qed_status st = sampler_alloc(ctx, 0);
     if (st != QED_OK || n == 0) return st;
     long long blocks = (n + 127) / 128;
     if (blocks > ctx->sms * 8) blocks = ctx->sms * 8;
     if (use_net == 2) {
         k_sampler_quantile_mma<<<(int)blocks, 128, sizeof(SamplerMma), ctx->stream>>>(
-            ctx->d_wbf, log10chi, u, x, n);
+            cur_net(ctx).d_wbf, log10chi, u, x, n);
         return cuda_check(ctx, cudaGetLastError(), "qed_sampler_quantile");
     }
     k_sampler_quantile<<<(int)blocks, 128, use_net ? sizeof(SamplerSmem) : 0, ctx->stream>>>(
-        ctx->d_wbf, ctx->d_cdf, kCdfRows, kCdfM, log10chi, u, x, n, use_net);
+        cur_net(ctx).d_wbf, cur_net(ctx).d_cdf, kCdfRows, kCdfM, log10chi, u, x, n, use_net);
     return cuda_check(ctx, cudaGetLastError(), "qed_sampler_quantile");
 }
 
@@ -3464,15 +3551,15 @@ qed_status qed_sampler_train(qed_ctx* ctx, uint64_t seed, int64_t samples, int b
         return set_err(ctx, QED_ERR_ARG, "qed_sampler_train: bad argument");
     qed_status st = sampler_alloc(ctx, batch);
     if (st != QED_OK) return st;
-    if (!ctx->net_ready) {
+    if (!cur_net(ctx).net_ready) {
         float th[kMlpParams];
         sampler_init_host(seed, th);
-        QED_CUDA(ctx, cudaMemcpyAsync(ctx->d_theta, th, sizeof th, cudaMemcpyHostToDevice,
+        QED_CUDA(ctx, cudaMemcpyAsync(cur_net(ctx).d_theta, th, sizeof th, cudaMemcpyHostToDevice,
                                       ctx->stream));
         QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     }
-    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_m1, 0, sizeof(float) * kMlpParams, ctx->stream));
-    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_m2, 0, sizeof(float) * kMlpParams, ctx->stream));
+    QED_CUDA(ctx, cudaMemsetAsync(cur_net(ctx).d_m1, 0, sizeof(float) * kMlpParams, ctx->stream));
+    QED_CUDA(ctx, cudaMemsetAsync(cur_net(ctx).d_m2, 0, sizeof(float) * kMlpParams, ctx->stream));
     const long long steps = (samples + batch - 1) / batch;
     const int ntiles = (batch + kTileS - 1) / kTileS;
     const int grid = std::min(ntiles, ctx->sms * 2);
@@ -3481,27 +3568,30 @@ qed_status qed_sampler_train(qed_ctx* ctx, uint64_t seed, int64_t samples, int b
     float* wgt = ctx->d_batch + 3 * (size_t)batch;
     const float b1 = 0.9f, b2 = 0.999f;
     double p1 = 1.0, p2 = 1.0;
+    // the pair network learns chi_gamma >= 0.25 only: below, the pair rate
+    // is negligible and the spectrum a spike at 1/2 (rejection keeps those)
+    const float l10_lo = ctx->net_sel == 1 ? kPairLog10Lo : kMlpLog10Lo;
     for (long long k = 0; k < steps; ++k) {
         k_sampler_batch<<<(batch + 255) / 256, 256, 0, ctx->stream>>>(
-            (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)k, batch, ctx->d_cdf, kCdfRows, kCdfM,
-            v, tgt, wgt);
+            (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)k, batch, l10_lo, kMlpLog10Hi,
+            cur_net(ctx).d_cdf, kCdfRows, kCdfM, v, tgt, wgt);
         const bool last = k + 1 == steps;
         if (last) QED_CUDA(ctx, cudaMemsetAsync(ctx->d_loss, 0, sizeof(float), ctx->stream));
         k_mlp_grad<<<grid, 256, sizeof(TrainSmem), ctx->stream>>>(
-            ctx->d_theta, v, tgt, wgt, batch, 1, ctx->d_cdf, kCdfRows, kCdfM, ctx->d_partial,
+            cur_net(ctx).d_theta, v, tgt, wgt, batch, 1, cur_net(ctx).d_cdf, kCdfRows, kCdfM, ctx->d_partial,
             last ? ctx->d_loss : nullptr);
         p1 *= b1;
         p2 *= b2;
         // cosine decay of the step size over the run
         const float lr_k = lr * 0.5f * (1.0f + cosf(3.14159265f * (float)k / (float)steps));
         k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, ctx->stream>>>(
-            ctx->d_partial, grid, ctx->d_theta, ctx->d_m1, ctx->d_m2, ctx->d_wbf, lr_k, b1, b2,
+            ctx->d_partial, grid, cur_net(ctx).d_theta, cur_net(ctx).d_m1, cur_net(ctx).d_m2, cur_net(ctx).d_wbf, lr_k, b1, b2,
             1e-8f, (float)(1.0 - p1), (float)(1.0 - p2), 1, nullptr);
         QED_CUDA(ctx, cudaGetLastError());
     }
-    ctx->adam_t += steps;
-    ctx->net_ready = 1;
-    ctx->net_bins = 0;   // evaluate before use
+    cur_net(ctx).adam_t += steps;
+    cur_net(ctx).net_ready = 1;
+    cur_net(ctx).net_bins = 0;   // evaluate before use
     if (final_loss) {
         QED_CUDA(ctx, cudaMemcpyAsync(final_loss, ctx->d_loss, sizeof(float), cudaMemcpyDeviceToHost,
                                       ctx->stream));
@@ -3512,7 +3602,7 @@ qed_status qed_sampler_train(qed_ctx* ctx, uint64_t seed, int64_t samples, int b
 
 qed_status qed_sampler_evaluate(qed_ctx* ctx, float* bin_err, int nbins) {
     if (!ctx || !bin_err || nbins != QED_SAMPLER_BINS) return QED_ERR_ARG;
-    if (!ctx->net_ready) return set_err(ctx, QED_ERR_STATE, "no sampler trained or loaded");
+    if (!cur_net(ctx).net_ready) return set_err(ctx, QED_ERR_STATE, "no sampler trained or loaded");
     qed_status st = sampler_alloc(ctx, 0);
     if (st != QED_OK) return st;
     const int rows = QED_SAMPLER_BINS * kEvalSub;
@@ -3526,13 +3616,13 @@ qed_status qed_sampler_evaluate(qed_ctx* ctx, float* bin_err, int nbins) {
     // rows at the centres of rows equal sub-intervals of [-2, 2]
     const float half = 0.5f * (kMlpLog10Hi - kMlpLog10Lo) / rows;
     k_cdf_rows<<<rows, 256, 0, ctx->stream>>>(kMlpLog10Lo + half, kMlpLog10Hi - half, rows, kCdfM,
-                                              cdf, tot);
+                                              ctx->net_sel, cdf, tot);
     // both forms of the network the event kernels use: a bin's error is the
     // larger of the two
     k_sampler_eval<<<rows, 128, sizeof(SamplerSmem), ctx->stream>>>(
-        ctx->d_wbf, cdf, rows, kCdfM, kMlpLog10Lo, kMlpLog10Hi, bits);
+        cur_net(ctx).d_wbf, cdf, tot, rows, kCdfM, kMlpLog10Lo, kMlpLog10Hi, bits);
     k_sampler_eval_mma<<<rows, 128, sizeof(SamplerMma), ctx->stream>>>(
-        ctx->d_wbf, cdf, rows, kCdfM, kMlpLog10Lo, kMlpLog10Hi, bits);
+        cur_net(ctx).d_wbf, cdf, tot, rows, kCdfM, kMlpLog10Lo, kMlpLog10Hi, bits);
     unsigned int hb[QED_SAMPLER_BINS];
     st = cuda_check(ctx, cudaMemcpyAsync(hb, bits, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream),
                     "copy bins");
@@ -3548,7 +3638,7 @@ qed_status qed_sampler_evaluate(qed_ctx* ctx, float* bin_err, int nbins) {
         bin_err[b] = e;
         if (e <= ctx->cfg.sampler_max_err) ok |= 1ull << b;
     }
-    ctx->net_bins = ok;
+    cur_net(ctx).net_bins = ok;
     return QED_OK;
 }
 
@@ -3575,26 +3665,26 @@ qed_status qed_sampler_load(qed_ctx* ctx, const float* params, int64_t n) {
     if (!ctx || !params || n != kMlpParams) return QED_ERR_ARG;
     qed_status st = sampler_alloc(ctx, 0);
     if (st != QED_OK) return st;
-    QED_CUDA(ctx, cudaMemcpyAsync(ctx->d_theta, params, sizeof(float) * kMlpParams,
+    QED_CUDA(ctx, cudaMemcpyAsync(cur_net(ctx).d_theta, params, sizeof(float) * kMlpParams,
                                   cudaMemcpyHostToDevice, ctx->stream));
     // refresh the BF16 copy with a zero-step Adam pass over a zero gradient
     QED_CUDA(ctx, cudaMemsetAsync(ctx->d_partial, 0, sizeof(float) * kMlpParams, ctx->stream));
-    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_m1, 0, sizeof(float) * kMlpParams, ctx->stream));
-    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_m2, 0, sizeof(float) * kMlpParams, ctx->stream));
+    QED_CUDA(ctx, cudaMemsetAsync(cur_net(ctx).d_m1, 0, sizeof(float) * kMlpParams, ctx->stream));
+    QED_CUDA(ctx, cudaMemsetAsync(cur_net(ctx).d_m2, 0, sizeof(float) * kMlpParams, ctx->stream));
     k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, ctx->stream>>>(
-        ctx->d_partial, 1, ctx->d_theta, ctx->d_m1, ctx->d_m2, ctx->d_wbf, 0.0f, 0.9f, 0.999f, 1e-8f,
+        ctx->d_partial, 1, cur_net(ctx).d_theta, cur_net(ctx).d_m1, cur_net(ctx).d_m2, cur_net(ctx).d_wbf, 0.0f, 0.9f, 0.999f, 1e-8f,
         1.0f, 1.0f, 1, nullptr);
     QED_CUDA(ctx, cudaGetLastError());
     QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    ctx->net_ready = 1;
-    ctx->net_bins = 0;
+    cur_net(ctx).net_ready = 1;
+    cur_net(ctx).net_bins = 0;
     return QED_OK;
 }
 
 qed_status qed_sampler_save(qed_ctx* ctx, float* params, int64_t n) {
     if (!ctx || !params || n != kMlpParams) return QED_ERR_ARG;
-    if (!ctx->net_ready) return set_err(ctx, QED_ERR_STATE, "no sampler trained or loaded");
-    QED_CUDA(ctx, cudaMemcpyAsync(params, ctx->d_theta, sizeof(float) * kMlpParams,
+    if (!cur_net(ctx).net_ready) return set_err(ctx, QED_ERR_STATE, "no sampler trained or loaded");
+    QED_CUDA(ctx, cudaMemcpyAsync(params, cur_net(ctx).d_theta, sizeof(float) * kMlpParams,
                                   cudaMemcpyDeviceToHost, ctx->stream));
     QED_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return QED_OK;

@@ -395,6 +395,9 @@ struct StepParams {
     unsigned long long net_bins;  // usable bins (64, uniform in log10 chi over [-2, 2))
     const void* net_w;          // BF16 network weights (8577)
     const float* net_wtot;      // total probability per c along log10 chi
+    unsigned long long pnet_bins;  // pair sampler (event-driven mode): usable bins (0: off)
+    const void* pnet_w;            // its BF16 weights
+    const float* pnet_wtot;        // its total probability per c along log10 chi
     uint32_t step;       // global step index (Philox counter word 2)
     uint32_t process_mask;
     int recoil;

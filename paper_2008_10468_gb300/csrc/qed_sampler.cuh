@@ -44,10 +44,12 @@ __device__ __forceinline__ float siluf_(float z) { return z * sigmoidf_(z); }
 // ---------------------------------------------------------------------------
 // Exact CDF rows.  Row i has chi_i = 10^(lo + i (hi - lo)/(n - 1)); node m has
 // x_m = m / M.  cdf[i][m] = int_0^{x_m} P / int_0^1 P (trapezoid rule, FP64
-// prefix sums), total[i] = int_0^1 P dx / c.
+// prefix sums), total[i] = int_0^1 P dx / c.  P is the acceptance function
+// of Algorithm 1 (emission, x = delta^{1/3}) or, with `pair`, of Algorithm 2
+// (x = delta_e, the electron's energy fraction).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_cdf_rows(float log10_lo, float log10_hi, int nrows,
-                                                  int M, float* __restrict__ cdf,
+                                                  int M, int pair, float* __restrict__ cdf,
                                                   float* __restrict__ total) {
     __shared__ SynTable tbl;
     __shared__ double warp_sums[8];
@@ -69,8 +71,11 @@ __global__ void __launch_bounds__(256) k_cdf_rows(float log10_lo, float log10_hi
         float pm = 0.0f, pprev = 0.0f;
         if (m <= M) {
             float d;
-            pm = m < M ? acceptance(tbl, false, b, 1.0f, (float)m * dx, &d) : 0.0f;
-            pprev = m - 1 == 0 ? kSmallF * b23 : acceptance(tbl, false, b, 1.0f, (float)(m - 1) * dx, &d);
+            // emission: x = delta^{1/3}, the density at x -> 0 is kSmallF c b^{2/3};
+            // pair production: x = delta_e, the density vanishes at both ends
+            pm = m < M ? acceptance(tbl, pair != 0, b, 1.0f, (float)m * dx, &d) : 0.0f;
+            pprev = m - 1 == 0 ? (pair ? 0.0f : kSmallF * b23)
+                               : acceptance(tbl, pair != 0, b, 1.0f, (float)(m - 1) * dx, &d);
         }
         double a = (m <= M) ? 0.5 * ((double)pm + (double)pprev) * (double)dx : 0.0;
         // inclusive scan within the block
@@ -97,8 +102,11 @@ __global__ void __launch_bounds__(256) k_cdf_rows(float log10_lo, float log10_hi
         total[row] = (float)tot;
     }
     __syncthreads();
-    const float inv = (float)(1.0 / tot);
-    for (int m = 1 + threadIdx.x; m <= M; m += 256) out[m] = fminf(out[m] * inv, 1.0f);
+    // a row whose probability underflows binary32 (pairs at small chi) keeps
+    // total 0 and a uniform CDF, and its bin is never usable
+    const float inv = tot > 0.0 ? (float)(1.0 / tot) : 0.0f;
+    for (int m = 1 + threadIdx.x; m <= M; m += 256)
+        out[m] = tot > 0.0 ? fminf(out[m] * inv, 1.0f) : (float)m / (float)M;
 }
 
 // Inverse of one CDF row at u: the node interval by binary search, then
@@ -129,20 +137,21 @@ __device__ __forceinline__ float cdf_row_density(const float* __restrict__ row, 
     return (row[m + 1] - row[m]) * (float)M;
 }
 
-// Training samples: log10 chi uniform in the trained range; u uniform for
+// Training samples: log10 chi uniform in [l10_lo, l10_hi]; u uniform for
 // half of the samples and, for the other half, logit u uniform in [-16, 16]
 // (the tails of u, where the inverse CDF is steepest, get their own share);
 // target x from the two neighbouring CDF rows (linear in log10 chi), and the
 // weight p(x), the density of x at the target: with it the squared error
 // p^2 (x - t)^2 is, to first order, the squared error of the CDF.
 __global__ void k_sampler_batch(uint32_t k0, uint32_t k1, uint32_t batch_index, int B,
+                                float l10_lo, float l10_hi,
                                 const float* __restrict__ cdf, int nrows, int M,
                                 float* __restrict__ v, float* __restrict__ target,
                                 float* __restrict__ weight) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= B) return;
     const uint4 r = philox4x32_10(make_uint4((uint32_t)s, batch_index, 0x5A4D4C50u, 0u), k0, k1);
-    const float l10 = kMlpLog10Lo + (kMlpLog10Hi - kMlpLog10Lo) * u01(r.x);
+    const float l10 = l10_lo + (l10_hi - l10_lo) * u01(r.x);
     float u, L;
     if (r.z & 1u) {
         u = u01(r.y);
@@ -753,13 +762,18 @@ __device__ __noinline__ float mlp_infer_mma_one(const SamplerMma& S, MmaBuf& buf
 }
 
 // Dynamic shared memory of the event kernels in a sampler mode: mode 1 the
-// FP32 form (SamplerSmem), mode 2 the tensor-core form (SamplerMma) followed by
-// one MmaBuf per warp (up to 8 warps per block).
-constexpr size_t kMmaSmemBytes = sizeof(SamplerMma) + 8 * sizeof(MmaBuf);
+// FP32 form (SamplerSmem), mode 2 the tensor-core form (SamplerMma) of the
+// emission and the pair networks followed by one MmaBuf per warp (up to 8
+// warps per block).
+// Mode 2 holds the emission network, then the pair network, then the buffers.
+constexpr size_t kMmaSmemBytes = 2 * sizeof(SamplerMma) + 8 * sizeof(MmaBuf);
 constexpr size_t kNetSmemBytes =
     sizeof(SamplerSmem) > kMmaSmemBytes ? sizeof(SamplerSmem) : kMmaSmemBytes;
+__device__ __forceinline__ SamplerMma& pair_mma(unsigned char* dyn) {
+    return *reinterpret_cast<SamplerMma*>(dyn + sizeof(SamplerMma));
+}
 __device__ __forceinline__ MmaBuf& warp_mma_buf(unsigned char* dyn) {
-    return reinterpret_cast<MmaBuf*>(dyn + sizeof(SamplerMma))[(threadIdx.x >> 5) & 7];
+    return reinterpret_cast<MmaBuf*>(dyn + 2 * sizeof(SamplerMma))[(threadIdx.x >> 5) & 7];
 }
 
 // x(v0, v1) for the sample of every lane; called by all 32 lanes together.

@@ -49,7 +49,7 @@ class StepStats(C.Structure):
                 ("candidates", C.c_uint64), ("max_N", C.c_uint32), ("status", C.c_int32),
                 ("required_capacity", C.c_int64), ("count", C.c_int64), ("passes", C.c_int32),
                 ("tail", C.c_int32), ("substeps_warp", C.c_uint64),
-                ("sampler_events", C.c_uint64)]
+                ("sampler_events", C.c_uint64), ("sampler_pairs", C.c_uint64)]
 
 
 EVENT_DTYPE = np.dtype([("parent_id", np.uint64), ("child0", np.uint64), ("child1", np.uint64),
@@ -109,6 +109,8 @@ def lib():
         fp = C.POINTER(C.c_float)
         L.qed_sampler_train.argtypes = [vp, u64, i64, C.c_int, C.c_float, fp]
         L.qed_sampler_train.restype = st
+        L.qed_sampler_process.argtypes = [vp, C.c_uint32]
+        L.qed_sampler_process.restype = st
         L.qed_sampler_evaluate.argtypes = [vp, fp, C.c_int]
         L.qed_sampler_evaluate.restype = st
         L.qed_sampler_gradient.argtypes = [vp, vp, vp, vp, vp, i64, vp, vp]
@@ -361,6 +363,11 @@ class Context:
         if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_TIMEOUT, QED_ERR_STATE):
             self._check(st)
         return [stats_dict(out[k]) for k in range(n)]
+
+    def sampler_process(self, process):
+        """Address the emission (PROC_EMISSION) or the pair (PROC_PAIR) network
+        with the sampler_* calls that follow."""
+        self._check(lib().qed_sampler_process(self._h, int(process)))
 
     def sampler_train(self, seed, samples, batch=4096, lr=3e-3):
         loss = C.c_float()

@@ -284,3 +284,104 @@ def test_event_driven_sampler_matches_sub_stepped_in_a_cascade(trained):
     da = ea["delta"][ea["kind"] == 1].astype(np.float64)
     db = eb["delta"][eb["kind"] == 1].astype(np.float64)
     assert stats.ks_2samp(np.cbrt(da), np.cbrt(db)).pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------
+# The learned pair sampler (Eq. 2, Algorithm 2): the same network form with
+# x = delta_e, the electron's energy fraction
+# --------------------------------------------------------------------------
+def test_exact_pair_quantile_table_matches_oracle():
+    ctx = qed.Context()
+    ctx.sampler_process(qed.PROC_PAIR)
+    rng = np.random.default_rng(19)
+    l10 = rng.uniform(-0.5, 2, 10).astype(np.float32)
+    u = rng.uniform(0.02, 0.98, 10).astype(np.float32)
+    x = torch.zeros(10, device="cuda")
+    ctx.sampler_quantile(_dev(l10), _dev(u), x, use_net=False)
+    xh = x.cpu().numpy()
+    from tests.test_gpu_parity import _x_cdf
+    for i in range(10):
+        b = 1.5 * 10.0 ** float(l10[i])
+        assert abs(_x_cdf(1, b, float(xh[i])) - float(u[i])) < 3e-5, (l10[i], u[i], xh[i])
+
+
+@pytest.fixture(scope="module")
+def trained_pair():
+    ctx = qed.Context(seed=12, sampler="event", sampler_max_err=1e-3)
+    ctx.sampler_process(qed.PROC_PAIR)
+    loss = ctx.sampler_train(2025, 1 << 26, batch=2048, lr=3e-3)
+    err = ctx.sampler_evaluate()
+    print("pair sampler: final loss %.3e, per-bin max CDF error: median %.2e, max %.2e over "
+          "chi_gamma >= 0.3" % (loss, np.median(err), err[int((math.log10(0.3) + 2) * 16):].max()))
+    return ctx, err
+
+
+def test_pair_sampler_reaches_a_small_cdf_error(trained_pair):
+    ctx, err = trained_pair
+    # where pairs are produced at a noticeable rate (chi_gamma >= 0.3) every
+    # bin is within the 1e-3 spectrum error; below, the spectrum narrows to a
+    # spike at 1/2 and the rejection method keeps the (rare) decays
+    assert err[int((math.log10(0.3) + 2) * 16):].max() <= 1e-3
+    p = ctx.sampler_save()
+    ctx.sampler_load(p)
+    np.testing.assert_array_equal(ctx.sampler_save(), p)
+
+
+def _identical_photons(M, gamma, chi_t):
+    E0 = np.float32(chi_t * O.schwinger_field() / (2.0 * gamma))
+    f32 = np.float32
+    arr = {"px": np.full(M, -gamma, f32), "py": np.zeros(M, f32), "pz": np.zeros(M, f32),
+           "Ex": np.zeros(M, f32), "Ey": np.full(M, E0, f32), "Ez": np.zeros(M, f32),
+           "Bx": np.zeros(M, f32), "By": np.zeros(M, f32), "Bz": np.full(M, E0, f32),
+           "w": np.ones(M, f32), "id": np.arange(M, dtype=np.uint64),
+           "type": np.full(M, 2, np.uint8)}
+    chi, g = O.chi((-gamma, 0.0, 0.0), (0.0, float(E0), 0.0), (0.0, 0.0, float(E0)), photon=True)
+    return arr, chi, g
+
+
+def test_pair_sampler_events_follow_rate_and_spectrum(trained, trained_pair):
+    # identical photons at chi_gamma ~ 5 with plans of ~80 sub-steps, no recoil
+    # (the photon stays, so its decays are independent draws): the decays per
+    # photon are W_p dt, delta_e follows the exact pair spectrum and is
+    # symmetric about 1/2, and the counts agree with rejection
+    from scipy import stats
+    ectx, _ = trained
+    pctx, perr = trained_pair
+    M = 4000
+    arr, chi, g = _identical_photons(M, 100.0, 5.0)
+    assert perr[int((math.log10(chi) + 2) * 16)] <= 1e-3
+    sctx = qed.Context(seed=88, process_mask=2, cascade=False, recoil=False, sampler="event",
+                       sampler_max_err=1e-3)
+    sctx.sampler_load(ectx.sampler_save())
+    sctx.sampler_evaluate()
+    sctx.sampler_process(qed.PROC_PAIR)
+    sctx.sampler_load(pctx.sampler_save())
+    sctx.sampler_evaluate()
+    sctx.set_event_log(1 << 17)
+    st = sctx.event_step(qed.ParticleStore.from_numpy(arr, capacity=M * 40), 7)
+    ev, _ = sctx.read_event_log()
+    assert st["status"] == 0 and st["pairs"] > 2000
+    # (without recoil a photon re-plans after each decay; a plan shorter than
+    # hot_min sub-steps keeps rejection, so a few decays are rejection's)
+    assert st["sampler_pairs"] > 0.95 * st["pairs"]
+    b = 1.5 * chi
+    Wp_dt = SQRT3 / math.pi * O.rate_unit() * 0.1 / g * O.total_per_c(1, b, 128, 16)
+    assert abs(st["pairs"] / M - Wp_dt) < 4 * math.sqrt(Wp_dt / M)
+    d = ev["delta"].astype(np.float64)
+    from tests.test_gpu_parity import _x_cdf
+    grid = np.linspace(0.0, 1.0, 161)
+    cdf = np.array([_x_cdf(1, b, v) if v > 0 else 0.0 for v in grid])
+    p1 = stats.kstest(d, lambda v: np.interp(v, grid, cdf)).pvalue
+    left, right = 0.5 - d[d < 0.5], d[d > 0.5] - 0.5
+    ps = stats.ks_2samp(left, right).pvalue
+    rctx = qed.Context(seed=88, process_mask=2, cascade=False, recoil=False)
+    rctx.set_event_log(1 << 17)
+    rst = rctx.event_step(qed.ParticleStore.from_numpy(arr, capacity=M * 40), 7)
+    rev, _ = rctx.read_event_log()
+    p2 = stats.ks_2samp(d, rev["delta"].astype(np.float64)).pvalue
+    print("pair sampler: %d decays (rejection %d), KS vs closed form p=%.3f, vs rejection "
+          "p=%.3f, symmetry p=%.3f" % (st["pairs"], rst["pairs"], p1, p2, ps))
+    assert abs(st["pairs"] - rst["pairs"]) < 5 * math.sqrt(st["pairs"] + rst["pairs"])
+    assert p1 > 0.01 and p2 > 0.01 and ps > 0.01
+    # every sub-step of every photon is accounted for
+    assert st["substeps"] == rst["substeps"]
