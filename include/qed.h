@@ -425,6 +425,19 @@ qed_status qed_profile_enable(qed_ctx* ctx, int enable);
  * accumulators.  Errors: QED_ERR_ARG, QED_ERR_CUDA. */
 qed_status qed_profile_read(qed_ctx* ctx, double* ms, int64_t* launches, int n);
 
+/* Validation of the remaining-time arithmetic the event kernels use (Sec. 2,
+ * Algorithms 1 and 2: the global step split into N sub-steps of length
+ * h = t / N; after an event at sub-step m - 1 the time left is t - m h).  The
+ * kernels carry t as a float-float pair (t_hi + t_lo, about 48 significant
+ * bits) on the FP32 pipe; for each i < n this computes h = t / N[i] and
+ * t - m[i] h (0 when m[i] >= N[i], the plan's last sub-step ending it
+ * exactly) that way and returns both as binary64 (h, t_after: device arrays
+ * of n doubles; t_hi, t_lo: device floats, |t_lo| <= ulp(t_hi) / 2; N, m:
+ * device uint32, N >= 1).  Asynchronous on `stream` (a cudaStream_t).
+ * Errors: QED_ERR_ARG, QED_ERR_CUDA. */
+qed_status qed_time_split(const float* t_hi, const float* t_lo, const uint32_t* N,
+                          const uint32_t* m, int64_t n, double* h, double* t_after, void* stream);
+
 /* Largest store (rows of capacity) that qed_event_step_noalloc accepts. */
 #define QED_NOALLOC_MAX_ROWS 65536
 
@@ -454,6 +467,22 @@ qed_status qed_profile_read(qed_ctx* ctx, double* ms, int64_t* launches, int n);
  * device then repeats its set-up), and the statuses of qed_event_step. */
 qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_particles* p,
                                   uint64_t step_index, void* stream, qed_step_stats* out);
+
+/* Peak probes: the rate, on the current device, of the arithmetic the event
+ * kernels run on, for the denominators of their roofline (not part of the
+ * paper's method).  Each thread of a full grid runs eight independent chains
+ * of one operation for `iters` steps, timed with CUDA events on `stream`
+ * (a cudaStream_t, NULL: the default stream) after a short warm-up:
+ *   QED_PROBE_MUL32  32 x 32 -> 64-bit multiplies as Philox4x32-10 issues
+ *                    them, counting the high and the low word (2 per step)
+ *   QED_PROBE_FMA32  binary32 fused multiply-adds, 2 flops per step
+ *   QED_PROBE_EX2    special-function exp2 (ex2.approx), 1 per step
+ *   QED_PROBE_ALU    integer xor and add, 2 per step
+ * *ops_per_s receives operations per second, *ms (nullable) the kernel's
+ * time.  Synchronises.  Allocates one word of device memory.
+ * Errors: QED_ERR_ARG (kind, iters <= 0, null ops_per_s), QED_ERR_CUDA. */
+enum { QED_PROBE_MUL32 = 0, QED_PROBE_FMA32 = 1, QED_PROBE_EX2 = 2, QED_PROBE_ALU = 3 };
+qed_status qed_peak_probe(int kind, int64_t iters, double* ops_per_s, double* ms, void* stream);
 
 /* sizeof of a public struct by name ("qed_config", "qed_particles",
  * "qed_step_stats", "qed_event_record"), or 0 for an unknown name.  Host

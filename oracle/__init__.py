@@ -69,6 +69,10 @@ def lib():
         L.orc_schwinger_field.restype = d; L.orc_schwinger_field.argtypes = [d]
         L.orc_event_step.restype = i32
         L.orc_event_step.argtypes = [P(Config), P(Particles), u32, P(Stats), P(Log)]
+        L.orc_table_build.restype = None
+        L.orc_table_build.argtypes = [i32]
+        L.orc_table_off.restype = None
+        L.orc_table_off.argtypes = []
         L.orc_event_step_mt.restype = i32
         L.orc_event_step_mt.argtypes = [P(Config), P(Particles), u32, P(Stats)]
         L.orc_log_free.restype = None; L.orc_log_free.argtypes = [P(Log)]
@@ -411,6 +415,24 @@ def event_step(cf, arrs, step, capacity=None, log=True, first_N=None):
     if log:
         lib().orc_log_free(C.byref(L))
     return res, _stats_dict(st), ev, ties
+
+
+class memoised_F1F2:
+    """Context manager: inside it F1 and F2 come from a table of the
+    quadrature (8192 nodes uniform in ln x over [1e-8, 700], Lagrange
+    interpolation through the 8 nearest nodes), as a production CPU code would
+    evaluate them; used to time the CPU baseline.  Outside it, the quadrature."""
+
+    def __init__(self, threads=None):
+        self.threads = int(threads or os.cpu_count() or 1)
+
+    def __enter__(self):
+        lib().orc_table_build(self.threads)
+        return self
+
+    def __exit__(self, *exc):
+        lib().orc_table_off()
+        return False
 
 
 def event_step_mt(cf, arrs, step, capacity=None):

@@ -103,10 +103,44 @@ static double sync_trapezoid(double x, double nu, int divide_by_cosh) {
     return x * tau * sum;
 }
 
+/* Memoised form (for the timed CPU baseline only): ln F and ln G from a table
+ * of the quadrature at nodes uniform in t = ln x over [ORC_TAB_LO,
+ * ORC_TAB_HI], interpolated by the Lagrange polynomial through the 8 nearest
+ * nodes (ln F is smooth in t: about t/3 at small x, -e^t at large x); the
+ * quadrature itself outside that range.  Built by orc_table_build; off until
+ * then and after orc_table_off. */
+#define ORC_TAB_N 8192
+#define ORC_TAB_LO 1e-8
+#define ORC_TAB_HI 700.0
+static double orc_tab_f[2][ORC_TAB_N];
+static double orc_tab_t0, orc_tab_h;
+static int orc_tab_on = 0;
+
+static double tab_eval(int which, double x) {
+    const double u = (log(x) - orc_tab_t0) / orc_tab_h;
+    long k = (long)floor(u) - 3;
+    if (k < 0) k = 0;
+    if (k > ORC_TAB_N - 8) k = ORC_TAB_N - 8;
+    double sum = 0.0;
+    for (int a = 0; a < 8; ++a) {
+        double w = 1.0;
+        for (int b = 0; b < 8; ++b)
+            if (b != a) w *= (u - (double)(k + b)) / (double)(a - b);
+        sum += w * orc_tab_f[which][k + a];
+    }
+    return exp(sum);
+}
+
 /* F(x): first synchrotron function (F1). */
-double orc_F1(double x) { return sync_trapezoid(x, 5.0 / 3.0, 1); }
+double orc_F1(double x) {
+    if (orc_tab_on && x >= ORC_TAB_LO && x <= ORC_TAB_HI) return tab_eval(0, x);
+    return sync_trapezoid(x, 5.0 / 3.0, 1);
+}
 /* G(x): second synchrotron function (F2). */
-double orc_F2(double x) { return sync_trapezoid(x, 2.0 / 3.0, 0); }
+double orc_F2(double x) {
+    if (orc_tab_on && x >= ORC_TAB_LO && x <= ORC_TAB_HI) return tab_eval(1, x);
+    return sync_trapezoid(x, 2.0 / 3.0, 0);
+}
 
 typedef struct {
     const double* x; double* f1; double* f2; int64_t begin, end;
@@ -122,6 +156,25 @@ static void* sync_worker(void* arg) {
 }
 
 /* F1 and F2 over an array, on `threads` host threads. */
+void orc_F1F2(int64_t n, const double* x, double* f1, double* f2, int threads);
+
+/* Build the memoised table from the quadrature (on `threads` threads) and
+ * switch it on. */
+void orc_table_build(int threads) {
+    static double xs[ORC_TAB_N];
+    orc_tab_on = 0;
+    orc_tab_t0 = log(ORC_TAB_LO);
+    orc_tab_h = (log(ORC_TAB_HI) - orc_tab_t0) / (double)(ORC_TAB_N - 1);
+    for (int k = 0; k < ORC_TAB_N; ++k) xs[k] = exp(orc_tab_t0 + orc_tab_h * (double)k);
+    orc_F1F2(ORC_TAB_N, xs, orc_tab_f[0], orc_tab_f[1], threads);
+    for (int k = 0; k < ORC_TAB_N; ++k) {
+        orc_tab_f[0][k] = log(orc_tab_f[0][k]);
+        orc_tab_f[1][k] = log(orc_tab_f[1][k]);
+    }
+    orc_tab_on = 1;
+}
+void orc_table_off(void) { orc_tab_on = 0; }
+
 void orc_F1F2(int64_t n, const double* x, double* f1, double* f2, int threads) {
     if (threads < 1) threads = 1;
     if (threads > 256) threads = 256;
@@ -675,44 +728,58 @@ int orc_event_step(const orc_config* cf, orc_particles* P, uint32_t step, orc_st
 }
 
 /* Multi-threaded variant used only to time the oracle on the host cores: the
- * particles are split into contiguous ranges, each thread runs its range and
- * its own children, and the children are appended afterwards in thread
- * order.  No event log.  Emission and pairs as configured. */
+ * particles are taken in chunks of ORC_CHUNK rows from a shared counter (so
+ * that a clump of long plans does not fall on one thread), each chunk's
+ * children are processed locally from a FIFO, and the chunks' children are
+ * appended afterwards in chunk order.  No event log.  Emission and pairs as
+ * configured. */
+#define ORC_CHUNK 32
 typedef struct {
-    const orc_config* cf; orc_particles* P; int64_t begin, end; uint32_t step;
-    orc_stats st; orc_childbuf out;
+    const orc_config* cf; orc_particles* P; int64_t n0; uint32_t step;
+    int64_t* next; orc_childbuf* outs; orc_stats st;
 } mt_job;
+
+static void mt_chunk(mt_job* j, int64_t c, orc_childbuf* kids, orc_childbuf* fifo) {
+    const int64_t begin = c * ORC_CHUNK;
+    const int64_t end = begin + ORC_CHUNK < j->n0 ? begin + ORC_CHUNK : j->n0;
+    fifo->n = 0;
+    for (int64_t i = begin; i < end; ++i) {
+        process_particle(j->cf, j->P, i, j->cf->dt, j->step, &j->st, NULL, kids);
+        for (int64_t k = 0; k < kids->n; ++k) push_child(fifo, &kids->c[k]);
+        kids->n = 0;
+    }
+    /* children are not written into the shared store by workers; a child
+     * with remaining time is processed on a private one-row store */
+    orc_childbuf* out = &j->outs[c];
+    for (int64_t q = 0; q < fifo->n; ++q) {
+        orc_child ch = fifo->c[q];
+        if (j->cf->cascade && ch.t_rem > 0.0) {
+            float px = ch.px, py = ch.py, pz = ch.pz, w = j->P->w[ch.parent];
+            float Ex = j->P->Ex[ch.parent], Ey = j->P->Ey[ch.parent], Ez = j->P->Ez[ch.parent];
+            float Bx = j->P->Bx[ch.parent], By = j->P->By[ch.parent], Bz = j->P->Bz[ch.parent];
+            uint64_t id = ch.id; uint8_t type = ch.type;
+            orc_particles one = {&px, &py, &pz, &Ex, &Ey, &Ez, &Bx, &By, &Bz, &w, &id, &type, 1, 1};
+            process_particle(j->cf, &one, 0, ch.t_rem, j->step, &j->st, NULL, kids);
+            for (int64_t k = 0; k < kids->n; ++k) {
+                kids->c[k].parent = ch.parent;   /* same fields and weight */
+                push_child(fifo, &kids->c[k]);
+            }
+            kids->n = 0;
+            ch.px = px; ch.py = py; ch.pz = pz; ch.type = type;
+        }
+        push_child(out, &ch);
+    }
+}
 
 static void* mt_worker(void* arg) {
     mt_job* j = (mt_job*)arg;
     memset(&j->st, 0, sizeof j->st);
-    orc_childbuf kids = {0};
-    /* children of this range are processed locally from a FIFO */
-    orc_childbuf fifo = {0};
-    for (int64_t i = j->begin; i < j->end; ++i) {
-        process_particle(j->cf, j->P, i, j->cf->dt, j->step, &j->st, NULL, &kids);
-        for (int64_t k = 0; k < kids.n; ++k) push_child(&fifo, &kids.c[k]);
-        kids.n = 0;
-    }
-    /* children are not written into the shared store by workers; a child
-     * with remaining time is processed on a private one-row store */
-    for (int64_t q = 0; q < fifo.n; ++q) {
-        orc_child c = fifo.c[q];
-        if (j->cf->cascade && c.t_rem > 0.0) {
-            float px = c.px, py = c.py, pz = c.pz, w = j->P->w[c.parent];
-            float Ex = j->P->Ex[c.parent], Ey = j->P->Ey[c.parent], Ez = j->P->Ez[c.parent];
-            float Bx = j->P->Bx[c.parent], By = j->P->By[c.parent], Bz = j->P->Bz[c.parent];
-            uint64_t id = c.id; uint8_t type = c.type;
-            orc_particles one = {&px, &py, &pz, &Ex, &Ey, &Ez, &Bx, &By, &Bz, &w, &id, &type, 1, 1};
-            process_particle(j->cf, &one, 0, c.t_rem, j->step, &j->st, NULL, &kids);
-            for (int64_t k = 0; k < kids.n; ++k) {
-                kids.c[k].parent = c.parent;   /* same fields and weight */
-                push_child(&fifo, &kids.c[k]);
-            }
-            kids.n = 0;
-            c.px = px; c.py = py; c.pz = pz; c.type = type;
-        }
-        push_child(&j->out, &c);
+    orc_childbuf kids = {0}, fifo = {0};
+    const int64_t nchunks = (j->n0 + ORC_CHUNK - 1) / ORC_CHUNK;
+    for (;;) {
+        const int64_t c = __atomic_fetch_add(j->next, 1, __ATOMIC_RELAXED);
+        if (c >= nchunks) break;
+        mt_chunk(j, c, &kids, &fifo);
     }
     free(kids.c);
     free(fifo.c);
@@ -723,10 +790,13 @@ int orc_event_step_mt(const orc_config* cf, orc_particles* P, uint32_t step, orc
     int T = cf->threads < 1 ? 1 : (cf->threads > 256 ? 256 : cf->threads);
     pthread_t th[256];
     mt_job* jobs = (mt_job*)calloc((size_t)T, sizeof(mt_job));
-    int64_t n0 = P->count;
+    const int64_t n0 = P->count;
+    const int64_t nchunks = (n0 + ORC_CHUNK - 1) / ORC_CHUNK;
+    orc_childbuf* outs = (orc_childbuf*)calloc((size_t)(nchunks > 0 ? nchunks : 1), sizeof(orc_childbuf));
+    int64_t next = 0;
     for (int t = 0; t < T; ++t) {
-        jobs[t].cf = cf; jobs[t].P = P; jobs[t].step = step;
-        jobs[t].begin = n0 * t / T; jobs[t].end = n0 * (t + 1) / T;
+        jobs[t].cf = cf; jobs[t].P = P; jobs[t].step = step; jobs[t].n0 = n0;
+        jobs[t].next = &next; jobs[t].outs = outs;
         pthread_create(&th[t], NULL, mt_worker, &jobs[t]);
     }
     memset(st, 0, sizeof *st);
@@ -736,17 +806,20 @@ int orc_event_step_mt(const orc_config* cf, orc_particles* P, uint32_t step, orc
         st->substeps += s->substeps; st->emissions += s->emissions; st->pairs += s->pairs;
         st->children += s->children; st->guard_hits += s->guard_hits; st->plans += s->plans;
         if (s->max_N > st->max_N) st->max_N = s->max_N;
-        for (int64_t k = 0; k < jobs[t].out.n && st->status == 0; ++k) {
-            orc_child* c = &jobs[t].out.c[k];
+    }
+    for (int64_t c = 0; c < nchunks; ++c) {
+        for (int64_t k = 0; k < outs[c].n && st->status == 0; ++k) {
+            orc_child* ch = &outs[c].c[k];
             if (P->count >= P->capacity) { st->status = 3; st->required_capacity = P->count + 1; break; }
             int64_t j = P->count++;
-            P->px[j] = c->px; P->py[j] = c->py; P->pz[j] = c->pz;
-            P->Ex[j] = P->Ex[c->parent]; P->Ey[j] = P->Ey[c->parent]; P->Ez[j] = P->Ez[c->parent];
-            P->Bx[j] = P->Bx[c->parent]; P->By[j] = P->By[c->parent]; P->Bz[j] = P->Bz[c->parent];
-            P->w[j] = P->w[c->parent]; P->id[j] = c->id; P->type[j] = c->type;
+            P->px[j] = ch->px; P->py[j] = ch->py; P->pz[j] = ch->pz;
+            P->Ex[j] = P->Ex[ch->parent]; P->Ey[j] = P->Ey[ch->parent]; P->Ez[j] = P->Ez[ch->parent];
+            P->Bx[j] = P->Bx[ch->parent]; P->By[j] = P->By[ch->parent]; P->Bz[j] = P->Bz[ch->parent];
+            P->w[j] = P->w[ch->parent]; P->id[j] = ch->id; P->type[j] = ch->type;
         }
-        free(jobs[t].out.c);
+        free(outs[c].c);
     }
+    free(outs);
     free(jobs);
     return st->status;
 }

@@ -3864,6 +3864,32 @@ size_t qed_abi_struct_size(const char* name) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// The remaining-time arithmetic of the event kernels, exposed for validation
+// ---------------------------------------------------------------------------
+__global__ void k_time_split(const float* __restrict__ t_hi, const float* __restrict__ t_lo,
+                             const uint32_t* __restrict__ N, const uint32_t* __restrict__ m,
+                             long long n, double* __restrict__ h_out, double* __restrict__ t_out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const ftime t{t_hi[i], t_lo[i]};
+        const ftime h = time_div(t, N[i]);
+        const ftime r = m[i] >= N[i] ? ftime{0.0f, 0.0f} : time_sub_mul(t, m[i], h);
+        h_out[i] = (double)h.hi + (double)h.lo;
+        t_out[i] = (double)r.hi + (double)r.lo;
+    }
+}
+
+extern "C" qed_status qed_time_split(const float* t_hi, const float* t_lo, const uint32_t* N,
+                                     const uint32_t* m, int64_t n, double* h, double* t_after,
+                                     void* stream) {
+    if (n < 0 || (n > 0 && (!t_hi || !t_lo || !N || !m || !h || !t_after))) return QED_ERR_ARG;
+    if (n == 0) return QED_OK;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    k_time_split<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(t_hi, t_lo, N, m, n, h, t_after);
+    return cudaGetLastError() == cudaSuccess ? QED_OK : QED_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
 // Event step without allocation.
 //
 // For callers that may not allocate device memory: hosts that hand each

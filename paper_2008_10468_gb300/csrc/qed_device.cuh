@@ -155,14 +155,16 @@ __device__ __forceinline__ float chi_ff(bool photon, float px, float py, float p
 }
 
 // chi in binary32 (Sec. 2.2).  Sets *well_conditioned when the rounding
-// error of chi is certainly below 8e-7 relative: the error of the computed
-// chi^2 is at most ~13 u M^2 (u = 2^-24) with M = eps|E| + |p||B| (a bound on
-// |eps E + p x B| and |p.E|), so kappa = 2 (eps^2 E^2 + p^2 B^2) / chi^2 >=
-// M^2 / chi^2 below 2 keeps the error of chi below 13 u = 7.8e-7 (sqrt and
-// the scaling add ~1 u).  Otherwise use chi_ff.
+// error of chi is certainly below 7.5 u kappa_max relative (u = 2^-24): the
+// error of the computed chi^2 is at most ~15 u M^2 with M = eps|E| + |p||B|
+// (a bound on |eps E + p x B| and |p.E|), and kappa = 2 (eps^2 E^2 + p^2 B^2)
+// / chi^2 >= M^2 / chi^2 (*kappa_out, if asked).  Both the planner and the
+// push mode's chi of each sub-step accept kappa < 8 (3.6e-6); the planner
+// widens its count's safety band with kappa.  Otherwise use chi_ff.
 __device__ __forceinline__ float chi_f32(bool photon, float px, float py, float pz, float Ex,
                                          float Ey, float Ez, float Bx, float By, float Bz,
-                                         float inv_Es, float* eps_out, bool* well_conditioned) {
+                                         float inv_Es, float* eps_out, bool* well_conditioned,
+                                         float kappa_max = 8.0f, float* kappa_out = nullptr) {
     const float p2 = fmaf(px, px, fmaf(py, py, pz * pz));
     const float eps = photon ? sqrtf(p2) : sqrtf(1.0f + p2);
     const float cx = fmaf(py, Bz, -pz * By);
@@ -175,11 +177,13 @@ __device__ __forceinline__ float chi_f32(bool photon, float px, float py, float 
     const float B2 = fmaf(Bx, Bx, fmaf(By, By, Bz * Bz));
     const float M2 = 2.0f * fmaf(eps * eps, E2, p2 * B2);
     *eps_out = eps;
-    *well_conditioned = q > 0.5f * M2;
+    *well_conditioned = q * kappa_max > M2;
+    if (kappa_out) *kappa_out = __fdividef(M2, q);
     return q > 0.0f ? sqrtf(q) * inv_Es : 0.0f;
 }
 
-// chi and eps of a momentum: binary32 when well conditioned, else float-float.
+// chi and eps of a momentum: binary32 when well conditioned (kappa < 8),
+// else float-float.
 __device__ __forceinline__ float chi_any(bool photon, float px, float py, float pz, float Ex,
                                          float Ey, float Ez, float Bx, float By, float Bz,
                                          float inv_Es, float* eps_out) {
@@ -319,23 +323,36 @@ struct ftime {
 
 __device__ __forceinline__ bool time_positive(ftime t) { return t.hi > 0.0f; }
 
+// An integer below 2^31 as the exact sum of two binary32 numbers: the
+// rounded value and the (signed, small) rest.
+__device__ __forceinline__ ff int_ff(uint32_t n) {
+    const float hi = (float)n;   // exact up to 2^24
+    const float lo = (float)(int)(n - (uint32_t)hi);
+    return {hi, lo};
+}
+
 // t / N for an integer N >= 1, to float-float precision: an approximate
-// reciprocal, one exact-residual correction of the leading part, then the
-// trailing part from the exact remainder (error-free products via FMA).
+// reciprocal of N's leading part, one exact-residual correction of the
+// leading part of the quotient, then the trailing part from the remainder
+// t - q N (the product with N's leading part error-free via FMA; N's rest,
+// nonzero only above 2^24, times q as a small correction).
 __device__ __forceinline__ ftime time_div(ftime t, uint32_t N) {
-    const float n = (float)N;                 // exact for N <= 2^24; N <= 2^30 rounds
-    const float r = __fdividef(1.0f, n);
+    const ff n = int_ff(N);
+    const float r = __fdividef(1.0f, n.hi);
     float q = t.hi * r;
-    q = __fmaf_rn(__fmaf_rn(-q, n, t.hi), r, q);
-    const ff qn = two_prod(q, n);
-    const float rem = __fadd_rn(__fsub_rn(__fsub_rn(t.hi, qn.hi), qn.lo), t.lo);
+    q = __fmaf_rn(__fmaf_rn(-q, n.hi, t.hi), r, q);
+    const ff qn = two_prod(q, n.hi);
+    const float rem = __fadd_rn(
+        __fsub_rn(__fsub_rn(__fsub_rn(t.hi, qn.hi), qn.lo), __fmul_rn(q, n.lo)), t.lo);
     const ff out = fast_two_sum(q, rem * r);
     return {out.hi, out.lo};
 }
 
-// t - m h for an integer m.
+// t - m h for an integer m (exact as a float-float pair up to 2^31).
 __device__ __forceinline__ ftime time_sub_mul(ftime t, uint32_t m, ftime h) {
-    const ff mh = ff_add(two_prod(h.hi, (float)m), ff{__fmul_rn(h.lo, (float)m), 0.0f});
+    const ff mf = int_ff(m);
+    const ff mh = ff_add(two_prod(h.hi, mf.hi),
+                         ff{__fmaf_rn(h.hi, mf.lo, __fmul_rn(h.lo, mf.hi)), 0.0f});
     const ff d = ff_add(ff{t.hi, t.lo}, ff_neg(mh));
     return {d.hi, d.lo};
 }
@@ -450,21 +467,23 @@ __device__ __forceinline__ float log2_split(float b) {
 
 // Plan the sub-steps of the remaining time T (Algorithms 1/2, planning).
 // `safe` reports whether N is certain.  The binary32 q = f / P_max carries a
-// relative error below 2.1e-6: chi 8.8e-7 (well-conditioned, see chi_f32;
-// every f(b) piece grows at most linearly in b), c 3.6e-7 (1/eps by the fast
-// divide, K and t rounded, two products), b^e 2.6e-7 (log2_split) plus 2.9e-7
-// (exp2f and the product in its argument), the constants A pi and 0.1 in
-// binary32 1.2e-7, the last three roundings 1.5e-7.  So N = max(1, ceil(q),
-// ceil(g)) is certain when it is the same at q (1 -+ 3e-6) and g (1 -+ 3e-6)
-// and b stays in its f piece within 2e-6; otherwise plan_slow recomputes it.
+// relative error below 1.2e-6 + e_chi: c 3.6e-7 (1/eps by the fast divide, K
+// and t rounded, two products), b^e 2.6e-7 (log2_split) plus 2.9e-7 (exp2f and
+// the product in its argument), the constants A pi and 0.1 in binary32
+// 1.2e-7, the last three roundings 1.5e-7; and chi's error e_chi passes on at
+// most linearly (every f(b) piece grows at most linearly in b).  With chi in
+// binary32, e_chi <= 7.5 u kappa + u (chi_f32), so the band is
+// d = 1.5e-6 + 5e-7 kappa; with chi from float-float, d = 1.5e-6.  N =
+// max(1, ceil(q), ceil(g)) is certain when it is the same at q (1 -+ d) and
+// g (1 -+ d) and b stays in its f piece within d; otherwise plan_slow
+// recomputes it.
 __device__ __forceinline__ PlanConst plan_const(const StepParams& P) {
     return PlanConst{P.K, P.inv_Es, P.inv_p_max, P.pair_coeff, P.p_max, P.lambda_m};
 }
 
 __device__ __forceinline__ Plan make_plan(const PlanConst& P, const float* __restrict__ sqz_e,
                                           const float* __restrict__ sqz_p, bool photon, float chi,
-                                          float eps, ftime T) {
-    constexpr float d = 3e-6f;
+                                          float eps, ftime T, float d) {
     Plan pl;
     pl.chi = chi;
     pl.eps = eps;
@@ -492,7 +511,7 @@ __device__ __forceinline__ Plan make_plan(const PlanConst& P, const float* __res
     const float n_hi = fmaxf(1.0f, fmaxf(ceilf(q * (1.0f + d)), ceilf(graw * (1.0f + d))));
     bool safe = n_lo == n_hi;
     if (!photon)
-        safe = safe && emission_piece(b * (1.0f - 2e-6f)) == emission_piece(b * (1.0f + 2e-6f));
+        safe = safe && emission_piece(b * (1.0f - d)) == emission_piece(b * (1.0f + d));
     N = fminf(N, 1073741824.0f);  // 2^30: keeps the 32-bit sub-step counter from wrapping
     pl.N = (uint32_t)N;
     pl.safe = safe;
@@ -515,10 +534,11 @@ __device__ __forceinline__ double bound_emission64(double b, double c) {
 
 // Slow path of plan_particle, for plans whose binary32 count is not certain
 // (chi ill-conditioned, or f / P_max within 3e-6 of an integer, or b at a
-// piece edge): chi in float-float, then the count N = max(1, ceil(f/P_max),
-// guard) in binary64, so that N is the exact count unless f / P_max lies
-// within ~1e-13 of an integer.  Rare (0.6% of the longest plans, fewer of
-// the others), so its binary64 arithmetic stays off the sub-step path.  Kept out of line
+// piece edge): chi in float-float and the binary32 plan from it; if its count
+// is still not certain, the count N = max(1, ceil(f/P_max), guard) in
+// binary64, so that N is the exact count unless f / P_max lies within ~1e-13
+// of an integer.  The binary64 step is rare (0.6% of the longest plans,
+// fewer of the others), so it stays off the sub-step path.  Kept out of line
 // so that the common path does not carry its registers.
 __device__ __noinline__ Plan plan_slow(PlanConst P, const float* __restrict__ sqz_e,
                                        const float* __restrict__ sqz_p, bool photon, float px,
@@ -536,6 +556,11 @@ __device__ __noinline__ Plan plan_slow(PlanConst P, const float* __restrict__ sq
         pl.N = 0;
         return pl;
     }
+    // the binary32 plan from the float-float chi (chi now within 1 ulp): when
+    // its count is certain, that is the plan (an ill-conditioned chi, the
+    // common reason to be here, needs no binary64)
+    pl = make_plan(P, sqz_e, sqz_p, photon, pl.chi, pl.eps, T, 1.5e-6f);
+    if (pl.safe) return pl;
     const double b = 1.5 * chi_d;
     const double c_rem = rate_K64(P.lambda_m) * ((double)T.hi + (double)T.lo) / eps_d;  // hi + lo exact
     const double f = photon ? (double)P.pair_coeff * c_rem * b
@@ -566,10 +591,12 @@ __device__ __forceinline__ Plan plan_particle(const StepParams& SP, const float*
                                               float* chi_out, float* eps_out) {
     const PlanConst P = plan_const(SP);
     bool wc;
-    float eps;
-    const float chi = chi_f32(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps, &wc);
+    float eps, kappa;
+    const float chi = chi_f32(photon, px, py, pz, Ex, Ey, Ez, Bx, By, Bz, P.inv_Es, &eps, &wc,
+                              8.0f, &kappa);
     if (wc && eps > 0.0f) {
-        const Plan pl = make_plan(P, sqz_e, sqz_p, photon, chi, eps, T);
+        const Plan pl =
+            make_plan(P, sqz_e, sqz_p, photon, chi, eps, T, fmaf(5e-7f, kappa, 1.5e-6f));
         if (pl.safe) {
             *chi_out = chi;
             *eps_out = eps;

@@ -151,6 +151,23 @@ def stats_dict(s):
     return {k: int(getattr(s, k)) for k, _ in StepStats._fields_}
 
 
+PROBE_MUL32, PROBE_FMA32, PROBE_EX2, PROBE_ALU = 0, 1, 2, 3
+
+
+def peak_probe(kind, iters=1 << 16, stream=None):
+    """(operations per second, ms) of one peak probe (qed_peak_probe)."""
+    L = lib()
+    L.qed_peak_probe.argtypes = [C.c_int, C.c_int64, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.c_void_p]
+    L.qed_peak_probe.restype = C.c_int
+    r, ms = C.c_double(), C.c_double()
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    st = L.qed_peak_probe(int(kind), int(iters), C.byref(r), C.byref(ms), C.c_void_p(s))
+    if st != QED_OK:
+        raise QEDError(st, "qed_peak_probe failed")
+    return r.value, ms.value
+
+
 def synchrotron_F1F2_f64(y, F1=None, F2=None, stream=None):
     """F and G in binary64 (float64 CUDA tensors) on `stream` (default: the
     current torch stream); no context needed."""

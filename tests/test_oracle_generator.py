@@ -157,3 +157,32 @@ def test_threaded_oracle_matches_sequential():
     o4 = np.argsort(r4["id"])
     for f in ("px", "py", "pz", "type", "id", "w"):
         np.testing.assert_array_equal(r1[f][o1], r4[f][o4])
+
+
+def test_memoised_synchrotron_table_matches_quadrature():
+    # the CPU baseline's table form of F and G: within 1e-10 of the
+    # quadrature over its whole range (ln F interpolated between nodes)
+    x = np.exp(np.random.default_rng(8).uniform(np.log(1e-8), np.log(700.0), 20000))
+    q1, q2 = O.F1F2(x)
+    with O.memoised_F1F2():
+        t1, t2 = O.F1F2(x)
+    assert np.max(np.abs(t1 / q1 - 1)) < 1e-10 and np.max(np.abs(t2 / q2 - 1)) < 1e-10
+    # outside the table range the quadrature is used
+    with O.memoised_F1F2():
+        e1, e2 = O.F1F2(np.array([1e-9, 710.0]))
+    r1, r2 = O.F1F2(np.array([1e-9, 710.0]))
+    np.testing.assert_array_equal(e1, r1)
+    np.testing.assert_array_equal(e2, r2)
+
+
+def test_memoised_event_step_equals_quadrature_step():
+    arr = I.clumped_mixed(600, 17, hot_fraction=0.05)
+    cf = O.make_config(5, process_mask=3, cascade=1, threads=4)
+    a, sa = O.event_step_mt(cf, arr, 3, capacity=600 * 60)
+    with O.memoised_F1F2(threads=4):
+        b, sb = O.event_step_mt(cf, arr, 3, capacity=600 * 60)
+    for k in ("substeps", "emissions", "pairs", "children", "plans"):
+        assert sa[k] == sb[k], k
+    oa, ob = np.argsort(a["id"]), np.argsort(b["id"])
+    for k in a:
+        np.testing.assert_array_equal(a[k][oa], b[k][ob])
