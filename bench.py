@@ -603,69 +603,73 @@ def run_uniform(dev, args):
 def run_push(store, dev, args, restore, plain_value):
     """The clumped step with the Boris push of Algorithm 1 before every e+-
     draw (qed_event_step_push): one lane per particle through its sub-steps
-    in order, the generations launched one by one."""
+    in order, the whole cascade in one persistent launch that takes children
+    as they come; beside it the same step generation by generation
+    (tail_rows 0) and with one sub-step per cell."""
     import torch
     from paper_2008_10468_gb300 import qed
-    ctx = qed.Context(seed=SEED_CLUMPED, process_mask=3, cascade=True)
     stream = torch.cuda.current_stream()
-    for w in range(2):
-        restore()
-        ctx.event_step(store, 4000 + w, push=True)
     steps = max(3, min(args.steps, 5))
-    total_ms, subs, agg = 0.0, 0, {"emissions": 0, "pairs": 0, "children": 0, "passes": 0}
+
+    def timed(ctx, call):
+        for w in range(2):
+            restore()
+            call(ctx, 4000 + w)
+        ms, subs, agg = 0.0, 0, {"emissions": 0, "pairs": 0, "children": 0, "passes": 0}
+        for k in range(steps):
+            restore()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = call(ctx, 2000 + k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            subs += st["substeps"]
+            for key in agg:
+                agg[key] += st[key]
+            if st["status"] != 0:
+                raise SystemExit("push step failed with status %d" % st["status"])
+        return ms, subs, agg
+
+    def plain_push(ctx, step):
+        return ctx.event_step(store, step, push=True)
+
+    ctx = qed.Context(seed=SEED_CLUMPED, process_mask=3, cascade=True)
+    total_ms, subs, agg = timed(ctx, plain_push)
+    value = subs / (total_ms / 1e3)
+    # one profiled step: the persistent kernel's share
+    restore()
     ctx.profile_read()
     ctx.profile(True)
-    kern = {}
-    for k in range(steps):
-        restore()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = ctx.event_step(store, 2000 + k, push=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        subs += st["substeps"]
-        for key in agg:
-            agg[key] += st[key]
-        if st["status"] != 0:
-            raise SystemExit("push step failed with status %d" % st["status"])
-        for name, (ms, nl) in ctx.profile_read().items():
-            a = kern.setdefault(name, [0.0, 0])
-            a[0] += ms
-            a[1] += nl
+    plain_push(ctx, 2000)
+    kern = ctx.profile_read()
     ctx.profile(False)
-    value = subs / (total_ms / 1e3)
+    # the generation loop (one launch per cascade generation, the host
+    # checking each), for comparison
+    gen_ctx = qed.Context(seed=SEED_CLUMPED, process_mask=3, cascade=True)
+    gen_ctx.set_tail(0)
+    g_ms, g_subs, g_agg = timed(gen_ctx, plain_push)
     # one sub-step per cell (64 consecutive rows per cell), Algorithm 1 as printed
     restore()
     n = int(store.count.item())
     cell = (torch.arange(n, device=store.device, dtype=torch.int64) // 64).to(torch.int32)
     ncells = (n + 63) // 64
-    c_ms, c_subs = 0.0, 0
-    for k in range(steps):
-        restore()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = ctx.event_step_push_cells(store, 2000 + k, cell, ncells)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        c_ms += e0.elapsed_time(e1)
-        c_subs += st["substeps"]
-        if st["status"] != 0:
-            raise SystemExit("push step with cells failed with status %d" % st["status"])
+    c_ms, c_subs, _ = timed(ctx, lambda c, step: c.event_step_push_cells(store, step, cell,
+                                                                           ncells))
     cells = {"rows_per_cell": 64, "ms_per_step": c_ms / steps, "substeps_per_step": c_subs / steps,
              "substeps_per_s": c_subs / (c_ms / 1e3)}
     return {"substeps_per_s": value, "ms_per_step": total_ms / steps, "steps": steps,
             "with_cells": cells,
             "per_step": {k: v / steps for k, v in agg.items()},
             "substeps_per_step": subs / steps,
-            "k_push_ms_per_step": kern.get("hot", [0.0])[0] / steps,
+            "k_push_ms_one_step": kern.get("hot", (0.0, 0))[0],
             "relative_to_step_without_push": value / plain_value,
-            "note": "generations launched one by one with CUDA events around each "
-                    "launch; no tail pass, no graph"}
+            "generations": {"ms_per_step": g_ms / steps, "substeps_per_s": g_subs / (g_ms / 1e3),
+                            "passes_per_step": g_agg["passes"] / steps},
+            "note": "the whole cascade in one persistent launch (children taken as they are "
+                    "reserved); 'generations' is the same step one launch per generation"}
 
 
 def run_plan_cells(ctx, store, n, dev, hbm_peak, peak_kind):

@@ -69,7 +69,9 @@ typedef struct {
                                   (geometric), with no per-sub-step draws; its
                                   particles run one per lane and each warp's
                                   events go through the network together on
-                                  the tensor cores (no tail pass in this mode) */
+                                  the tensor cores; in the tail pass of the
+                                  cascade they are stepped a warp each and go
+                                  through the network one at a time          */
     float sampler_max_err;     /* a chi bin is usable if its max CDF error <= this
                                   (1e-3)                                        */
 } qed_config;
@@ -179,8 +181,8 @@ qed_status qed_synchrotron_generate(qed_ctx* ctx, uint64_t seed, int64_t n, floa
  * whose process is disabled, get N = 0.  Errors: QED_ERR_ARG. */
 qed_status qed_plan(qed_ctx* ctx, const qed_particles* p, int64_t n, float* chi, uint32_t* N);
 
-/* Per-cell planning (Sec. 2.2: the first line of Algorithms 1 and 2 plans
- * one sub-step per cell): N_cell[c] = the largest sub-step count N of
+/* Per-cell planning (Sec. 2.2: Algorithms 1 and 2 start by fixing one
+ * sub-step per cell): N_cell[c] = the largest sub-step count N of
  * qed_plan over the rows i < n with cell[i] == c (0 for a cell without an
  * active row), so that sub_t = dt / N_cell[c] keeps every particle of the
  * cell within P_max per sub-step.  cell: device array of n cell indices;
@@ -220,8 +222,11 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
  * the Boris formulas (the store's precision).  Positions are not stored, so
  * only momenta move.  On return every processed e+- row holds its momentum
  * after the step.  Same arguments, statistics, capacity rule and errors as
- * qed_event_step; the learned sampler is not used, and the generations run
- * one launch each (no tail pass, no graph). */
+ * qed_event_step; the learned sampler is not used.  With the cascade, the
+ * whole step runs as one persistent pass that takes each child as soon as it
+ * is reserved (the generations do not wait for the longest push chain of the
+ * one before), unless qed_set_tail(ctx, 0) asks for one launch per
+ * generation; both give the same result. */
 qed_status qed_event_step_push(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
                                qed_step_stats* out);
 
@@ -315,9 +320,11 @@ qed_status qed_graph_read_stats(qed_ctx* ctx, qed_step_stats* out, int nsteps);
 qed_status qed_sampler_process(qed_ctx* ctx, uint32_t process);
 
 /* Train with Adam (cosine-decayed step `lr`) on `samples` pairs drawn in
- * batches of `batch` (64 <= batch <= 2^20): log10 chi and u uniform, target x
- * from the exact CDF of the emission spectrum, tabulated on the GPU from the
- * acceptance function of Algorithm 1 (1024 chi rows x 4096 x intervals).
+ * batches of `batch` (64 <= batch <= 2^20): log10 chi and u uniform (chi in
+ * [1e-2, 1e2) for the emission network, [0.25, 1e2) for the pair network,
+ * whose spectrum underflows binary32 below), target x from the exact CDF of
+ * the network's spectrum, tabulated on the GPU from the acceptance function
+ * of Algorithm 1 or 2 (1024 chi rows x 4096 x intervals).
  * Loss: mean of (CDF(chi, x_net) - u)^2, the squared CDF error of the
  * sampler, with CDF and density from the same tables; the forward pass uses
  * the BF16-rounded weights the event kernels use, its gradient updating the
@@ -379,11 +386,12 @@ qed_status qed_set_launch(qed_ctx* ctx, uint32_t hot_min, uint32_t long_min,
  * Errors: QED_ERR_ARG (ctx null, tail_rows < 0). */
 qed_status qed_set_tail(qed_ctx* ctx, int64_t tail_rows);
 
-/* Longest bounded wait of the tail pass, in nanoseconds (0: the default,
- * 1 s).  The persistent kernel of the tail pass waits for child rows that
- * another warp is still writing and for queue entries not yet pushed, and
- * its idle warps wait for new work; a warp that has waited this long in
- * total without progress gives up, and the step ends with QED_ERR_TIMEOUT
+/* Longest bounded wait of the persistent passes (the tail pass, the push
+ * step's pass), in nanoseconds (0: the default, 1 s).  Their kernels wait
+ * for child rows that another warp is still writing and for queue entries
+ * not yet pushed, and their idle warps wait for new work; a warp that has
+ * waited this long without progress anywhere (rows stored or completed,
+ * beats of long chains) gives up, and the step ends with QED_ERR_TIMEOUT
  * (in the statistics and as the return value when they are read) instead of
  * hanging; the context stays usable.  A short limit makes idle warps give
  * up early, so it is for tests of that path.  Applies to later steps and

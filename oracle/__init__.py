@@ -18,8 +18,8 @@ What it computes (each function cites the passage it follows):
   P_p (Eq. 2 with the bracket sign corrected, Algorithm 2).
 * ``total_per_c``: the per-sub-step event probability divided by c
   (the integral bounded by f(b) in Sec. 3.1.1).
-* ``plan_cells``: the sub-step count per cell of the first line of Algorithms
-  1 and 2 (the largest count of the cell's particles).
+* ``plan_cells``: the sub-step count per cell with which Algorithms 1 and 2
+  start (the largest count of the cell's particles).
 * ``event_step``: Algorithms 1 and 2 for a particle store over one global step,
   optionally with the Boris push of Algorithm 1 before every e+- draw.
 * ``boris64``/``boris32``: that push (the Lorentz force in code units), in
@@ -316,7 +316,7 @@ def plan(cf, p, E, B, t_rem, photon=False):
 
 
 def plan_cells(cf, arrs, cell, ncells):
-    """Per-cell sub-step counts (the first line of Algorithms 1 and 2 plans one
+    """Per-cell sub-step counts (Algorithms 1 and 2 start by fixing one
     sub-step per cell): for each cell the largest planned N
     (``plan`` over a full global step) of its rows whose process is enabled
     (0 for a cell without one).  Rows with a cell index >= ncells are left out."""

@@ -18,7 +18,7 @@
  *   - the sub-step planner from the rate bounds f(b) of Sec. 3.1.1;
  *   - Algorithms 1 and 2 with local sub-stepping, recoil and children;
  *   - Philox4x32-10 (Salmon et al., SC'11) for the per-sub-step draws;
- *   - optionally, the Boris push of Algorithm 1 (line 3 of its loop): every
+ *   - optionally, the Boris push of Algorithm 1 (inside its loop): every
  *     sub-step of an electron or positron first moves its momentum by the
  *     Lorentz force, then chi is recomputed for the draw.
  *
@@ -588,7 +588,7 @@ static void process_particle(const orc_config* cf, orc_particles* P, int64_t i, 
             uint32_t hi2 = plan_count(cf, is_photon, b, c_rem, 1.0 - eps, 1.0 + eps, NULL);
             if (lo != N || hi != N || lo2 != N || hi2 != N) { tied = 1; log_tie(L, id, s, 2); }
         }
-        /* one sub-step per cell (first line of Algorithms 1/2): an initial
+        /* one sub-step per cell (as Algorithms 1/2 start): an initial
          * row's first plan takes its cell's count when that is larger (a
          * near-tie of the cell's count is the caller's to flag) */
         if (cf->first_N && s == 0 && i < cf->first_N_rows && cf->first_N[i] > N)

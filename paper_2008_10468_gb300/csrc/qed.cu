@@ -91,6 +91,8 @@ struct DevCtl {
     unsigned long long push_head;   // push mode: next row of the generation to take
     unsigned int samp_tail, samp_head;   // event-driven sampler: its queue of this generation
     long long n_init;               // rows at the start of the step (the rest are children)
+    unsigned long long beat;        // persistent passes: progress of long chains, so that
+                                    // idle warps tell a long chain from a stalled step
 };
 
 // Type byte of a child row that has been reserved but not yet written: in the
@@ -252,8 +254,8 @@ __global__ void __launch_bounds__(kSweepThreads) k_generate(uint32_t k0, uint32_
 // ---------------------------------------------------------------------------
 // Planner
 // ---------------------------------------------------------------------------
-// cell / N_cell (optional): per-cell planning, Algorithm 1's sub-step "for
-// the current cell": N_cell[c] becomes the largest N of the rows of cell c
+// cell / N_cell (optional): per-cell planning (Algorithm 1 and 2 fix one
+// sub-step per cell): N_cell[c] becomes the largest N of the rows of cell c
 // (N_cell zeroed by the caller; rows whose cell index is >= ncells are left
 // out of it).
 __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParams SP, long long n,
@@ -295,6 +297,12 @@ __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParam
 struct PState {
     float px, py, pz;
 };
+
+// Rows stored so far (the count, capped at the capacity), read afresh.
+__device__ __forceinline__ unsigned long long stored_rows(const DevParticles& P) {
+    const long long c = *reinterpret_cast<volatile long long*>(P.count);
+    return (unsigned long long)min(c, P.capacity);
+}
 
 // Reserve n rows for children.  `aggregate`: the lanes of the warp that reach
 // this call together share one atomic (ballots of the active lanes give each
@@ -737,16 +745,31 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
 // Push mode: Algorithm 1 with the Boris push before every e+- draw
 // ---------------------------------------------------------------------------
 constexpr int kPushGroupMax = 16;   // busy lanes of a drained warp that switch to group mode
-// One generation of a push-mode step.  The push makes every sub-step depend
-// on the one before, so a lane steps one particle through its sub-steps in
-// order; a lane whose particle is done takes the next row of the generation
-// (the idle lanes of a warp share one atomic on ctl->push_head, which the
-// host clears before the launch).  Per sub-step of an e+-: the push over h,
-// chi and eps of the new momentum, the squeeze bound for that chi, the draw
-// of sub-step s and the test.  A photon flies straight: its momentum, chi and
-// plan stay, as in the other kernels.  After an event the particle is
-// re-planned over the time that remains, from its state after the push and
-// the recoil.
+// A push-mode step.  The push makes every sub-step depend on the one before,
+// so a lane steps one particle through its sub-steps in order; a lane whose
+// particle is done takes the next row (the idle lanes of a warp share one
+// atomic on ctl->push_head, which starts at 0).  Per sub-step of an e+-: the
+// push over h, chi and eps of the new momentum, the squeeze bound for that
+// chi, the draw of sub-step s and the test.  A photon flies straight: its
+// momentum, chi and plan stay, as in the other kernels.  After an event the
+// particle is re-planned over the time that remains, from its state after
+// the push and the recoil.
+//
+// kStream = false: one cascade generation, the rows [pass_begin, pass_end).
+// kStream = true: the whole step in one launch.  Rows are taken in store
+// order as they come: the step's initial rows, then every child as soon as
+// it is reserved, so that a generation does not wait for the longest push
+// chain of the one before.  The rows past the initial ones start "not
+// written" (k_push_begin); a child's writer stores the row, fences, then its
+// type byte, and a lane that took the row waits for that byte.  Each warp
+// takes child indices into a pending range with one atomic and hands a lane
+// only an index whose row is reserved already (indices never reserved are
+// void at the end).  The step ends when the rows completed equal the rows
+// stored.  Every wait is bounded: a warp that sees no progress anywhere
+// (rows stored, rows completed, the beats of long chains) for SP.wait_ns
+// records QED_ERR_TIMEOUT and returns.
+constexpr unsigned int kBeatRounds = 1024;   // rounds of a warp between two beats
+template <bool kStream>
 __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParams SP, Scratch S,
                                                        DevCtl* ctl) {
     const uint32_t step = step_index(SP);
@@ -754,16 +777,23 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
     stage_tables(sm);
     __syncthreads();
     if (ctl->status == (int)QED_ERR_TIMEOUT) return;
-    const bool first_pass = ctl->first_pass != 0;
-    const long long begin = first_pass ? 0 : ctl->pass_begin;
-    const long long n = ctl->pass_end - begin;
+    const bool first_pass = kStream || ctl->first_pass != 0;
+    const long long begin = kStream ? 0 : (first_pass ? 0 : ctl->pass_begin);
+    const long long n = kStream ? 0 : ctl->pass_end - begin;
     const long long n_init = ctl->n_init;
+    const bool cascade = SP.cascade != 0;
     constexpr unsigned int kAll = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const PlanConst PC = plan_const(SP);
     Stats stats;
-    bool busy = false, drained = n <= 0, photon = false, electron = false, need_plan = false;
-    bool removed = false;
+    bool busy = false, drained = kStream ? false : n <= 0, photon = false, electron = false;
+    bool need_plan = false, removed = false;
+    bool waiting = false;                          // kStream: the lane's row is still being written
+    unsigned int units = 0;                        // kStream: rows this lane completed, not yet added
+    unsigned long long pend_lo = 0, pend_hi = 0;   // kStream: the warp's pending child indices
+    unsigned long long idle_ns = 0, seen = 0;      // kStream: bounded wait
+    unsigned int idle = 0, rounds = 0;
+    bool timed_out = false;
     long long i = 0;
     uint64_t id = 0;
     PState st{0.0f, 0.0f, 0.0f};
@@ -777,41 +807,136 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
     float chi = 0.0f, eps = 0.0f, a = 0.0f;
     uint32_t k = 0, s = 0, blk = kNoEvent;
     uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    // a row the lane holds: start its particle, or count the row as done
+    auto take_row = [&](long long row) {
+        const uint8_t type = P.type[row];
+        photon = type == QED_PHOTON;
+        if (type <= QED_PHOTON && process_enabled(SP, photon)) {
+            t_rem = (kStream ? row < n_init : first_pass) ? SP.t_step : S.t_rem[row];
+            if (time_positive(t_rem)) {
+                busy = true;
+                need_plan = true;
+                removed = false;
+                electron = type == QED_ELECTRON;
+                id = P.id[row];
+                st = PState{P.px[row], P.py[row], P.pz[row]};
+                F = Fields{P.Ex[row], P.Ey[row], P.Ez[row], P.Bx[row], P.By[row], P.Bz[row]};
+                s = 0;
+                blk = kNoEvent;
+                return;
+            }
+        }
+        if (kStream) ++units;
+    };
     while (true) {
-        const unsigned int idle = __ballot_sync(kAll, !busy);
-        if (idle && !drained) {
-            const int leader = __ffs(idle) - 1;
+        const unsigned int free_lanes = __ballot_sync(kAll, !busy && !waiting);
+        if (kStream) {
+            // rows for the free lanes: indices below the rows stored now
+            int got = 0;
             unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(&ctl->push_head, (unsigned long long)__popc(idle));
-            base = __shfl_sync(kAll, base, leader);
-            if ((long long)base + __popc(idle) >= n) drained = true;
-            if (!busy) {
-                const long long row = (long long)base + __popc(idle & ((1u << lane) - 1u));
-                if (row < n) {
-                    i = begin + row;
-                    const uint8_t type = P.type[i];
-                    photon = type == QED_PHOTON;
-                    if (type <= QED_PHOTON && process_enabled(SP, photon)) {
-                        t_rem = first_pass ? SP.t_step : S.t_rem[i];
-                        if (time_positive(t_rem)) {
-                            busy = true;
-                            need_plan = true;
-                            removed = false;
-                            electron = type == QED_ELECTRON;
-                            id = P.id[i];
-                            st = PState{P.px[i], P.py[i], P.pz[i]};
-                            F = Fields{P.Ex[i], P.Ey[i], P.Ez[i], P.Bx[i], P.By[i], P.Bz[i]};
-                            s = 0;
-                            blk = kNoEvent;
+            if (free_lanes) {
+                const int want = __popc(free_lanes);
+                if (lane == 0) {
+                    const unsigned long long lim =
+                        cascade ? stored_rows(P) : (unsigned long long)n_init;
+                    if (pend_lo == pend_hi) {
+                        const unsigned long long h =
+                            *reinterpret_cast<volatile unsigned long long*>(&ctl->push_head);
+                        if (h < lim) {
+                            const unsigned long long kk = min((unsigned long long)want, lim - h);
+                            pend_lo = atomicAdd(&ctl->push_head, kk);
+                            pend_hi = pend_lo + kk;
                         }
                     }
+                    if (pend_lo < pend_hi && pend_lo < lim) {
+                        got = (int)min((unsigned long long)want, min(pend_hi, lim) - pend_lo);
+                        base = pend_lo;
+                        pend_lo += (unsigned long long)got;
+                    }
+                }
+                got = __shfl_sync(kAll, got, 0);
+                base = __shfl_sync(kAll, base, 0);
+                const int rank = __popc(free_lanes & ((1u << lane) - 1u));
+                if (!busy && !waiting && rank < got) {
+                    i = (long long)(base + (unsigned long long)rank);
+                    waiting = true;
+                }
+            }
+            // no free lane left wanting a row: the warp is not starved
+            drained = free_lanes != 0 && got < __popc(free_lanes);
+            if (waiting) {
+                const uint8_t ty = *reinterpret_cast<volatile uint8_t*>(P.type + i);
+                if (ty != kNotReady) {
+                    __threadfence();   // the row was stored before its type byte
+                    waiting = false;
+                    take_row(i);
+                }
+            }
+        } else if (free_lanes && !drained) {
+            const int leader = __ffs(free_lanes) - 1;
+            unsigned long long base = 0;
+            if (lane == leader)
+                base = atomicAdd(&ctl->push_head, (unsigned long long)__popc(free_lanes));
+            base = __shfl_sync(kAll, base, leader);
+            if ((long long)base + __popc(free_lanes) >= n) drained = true;
+            if (!busy) {
+                const long long row = (long long)base + __popc(free_lanes & ((1u << lane) - 1u));
+                if (row < n) {
+                    i = begin + row;
+                    take_row(i);
                 }
             }
         }
         const unsigned int bm = __ballot_sync(kAll, busy);
         if (!bm) {
-            if (drained) break;
+            if (!kStream) {
+                if (drained) break;
+                continue;
+            }
+            // nothing to step: wait for rows, or finish
+            const bool hold = __any_sync(kAll, waiting);
+            bool finish = false;
+            unsigned long long progress = 0;
+            if (!hold) {
+                const unsigned long long sum = warp_sum(units);
+                units = 0;
+                if (lane == 0) {
+                    __threadfence();   // this warp's reservations before its completions
+                    if (sum) atomicAdd(&ctl->finished, sum);
+                    const unsigned long long c1 = cascade ? stored_rows(P) : (unsigned long long)n_init;
+                    const unsigned long long f =
+                        *reinterpret_cast<volatile unsigned long long*>(&ctl->finished);
+                    const unsigned long long c2 = cascade ? stored_rows(P) : (unsigned long long)n_init;
+                    finish = f == c1 && c1 == c2;
+                    progress = f + c2 + *reinterpret_cast<volatile unsigned long long*>(&ctl->beat);
+                }
+                finish = __shfl_sync(kAll, finish ? 1 : 0, 0) != 0;
+                progress = __shfl_sync(kAll, progress, 0);
+            }
+            if (finish) break;
+            // idle: back off from 256 ns to 4 us (64 ns while a row is being
+            // written); the idle time counts from the last progress seen
+            if (!hold && progress != seen) {
+                seen = progress;
+                idle_ns = 0;
+            }
+            const unsigned int nap = hold ? 64u : 256u << min(idle, 4u);
+            ++idle;
+            idle_ns += nap;
+            if (idle_ns > SP.wait_ns) {
+                timed_out = true;
+                break;
+            }
+            __nanosleep(nap);
             continue;
+        }
+        if (kStream) {
+            idle = 0;
+            idle_ns = 0;
+            if (++rounds == kBeatRounds) {   // a long chain shows its progress
+                rounds = 0;
+                if (lane == 0) atomicAdd(&ctl->beat, 1ull);
+            }
         }
         // plan the lane's particle (Algorithms 1/2, planning); true if it is done
         auto plan_now = [&]() -> bool {
@@ -939,7 +1064,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
                                                        : time_sub_mul(t_rem, kk, pl.h);
                     removed = apply_event(P, S, SP, ctl, i, id, photon, nxd, neps, nchi, step,
                                           s + (uint32_t)jstar_o, t_after, st, stats, true, false, F,
-                                          false);
+                                          kStream);
                     s += used_o;
                     t_rem = t_after;
                     if (removed || !time_positive(t_rem)) done = true;
@@ -981,7 +1106,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
                 const ftime t_after = (k + 1u == pl.N) ? ftime{0.0f, 0.0f}
                                                        : time_sub_mul(t_rem, k + 1u, pl.h);
                 removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps_k, chi_k, step, s,
-                                      t_after, st, stats, true, false, F, false);
+                                      t_after, st, stats, true, false, F, kStream);
                 ++s;
                 t_rem = t_after;
                 if (removed || !time_positive(t_rem)) done = true;
@@ -1000,6 +1125,15 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
                 P.py[i] = st.py;
                 P.pz[i] = st.pz;
             }
+            if (kStream) ++units;
+        }
+    }
+    if (kStream) {
+        if (timed_out && lane == 0) atomicExch(&ctl->status, (int)QED_ERR_TIMEOUT);
+        const unsigned long long sum = warp_sum(units);
+        if (lane == 0 && sum) {
+            __threadfence();
+            atomicAdd(&ctl->finished, sum);
         }
     }
     flush_stats(stats, ctl);
@@ -1031,6 +1165,7 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
     uint32_t s = it.s;
     ftime t_rem = it.t_rem;
     bool removed = false, changed = false;
+    unsigned int rounds = 0;   // publish (persistent pass): beats of a long chain
     while (time_positive(t_rem)) {
         float eps, chi;
         const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
@@ -1136,6 +1271,10 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
                 if (lane == 0) stats.substeps += chunk_end - sb;
                 kdone += chunk_end - sb;
                 s = chunk_end;
+                if (publish && ++rounds == kBeatRounds) {
+                    rounds = 0;
+                    if (lane == 0) atomicAdd(&ctl->beat, 1ull);
+                }
                 continue;
             }
             const int p0 = m0 ? 2 * (__ffs(m0) - 1) : 1 << 30;
@@ -1552,16 +1691,13 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
 // when they run out of work, so the count is exact whenever the test can
 // succeed.  Idle warps back off (256 ns doubling to 4 us), so that their
 // polls of the control words do not slow the atomics of the busy ones.  Every
-// wait is bounded: past SP.wait_ns idle (1 s unless qed_set_wait_limit says
-// otherwise), or as many 64 ns polls for a queue entry, the kernel records
-// QED_ERR_TIMEOUT and returns.
+// wait is bounded: past SP.wait_ns (1 s unless qed_set_wait_limit says
+// otherwise) without progress anywhere (rows stored or completed, or a beat:
+// warps stepping a long chain add one every kBeatRounds rounds), or as many
+// 64 ns polls for a queue entry, the kernel records QED_ERR_TIMEOUT and
+// returns.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long kWaitNsDefault = 1000000000ull;   // idle time before giving up: 1 s
-
-__device__ __forceinline__ unsigned long long stored_rows(const DevParticles& P) {
-    const long long c = *reinterpret_cast<volatile long long*>(P.count);
-    return (unsigned long long)min(c, P.capacity);
-}
 
 // Queue a long plan: the entry's row index is written last (readers wait for it).
 __device__ __forceinline__ void push_long(const Scratch& S, DevCtl* ctl, unsigned int cold_long,
@@ -1620,8 +1756,8 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
     pl.T = 0;
     pl.b = pl.c_h = 0.0f;
     float chi = 0.0f, eps = 0.0f;
-    unsigned int idle = 0;
-    unsigned long long idle_ns = 0;
+    unsigned int idle = 0, rounds = 0;
+    unsigned long long idle_ns = 0, seen = 0;
     unsigned int ticket = kNoItem;   // lane 0: long-queue entry taken, not yet pushed
     unsigned long long pend_lo = 0, pend_hi = 0;   // lane 0: child indices taken, not handed out
     bool timed_out = false;
@@ -1792,11 +1928,13 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
             // lanes waiting for a row still being written hold the warp
             const bool hold = __any_sync(kAll, waiting);
             bool finish = false;
+            unsigned long long progress = 0;
             if (!hold) {
                 // add this warp's finished rows, then test for the end of the step
                 const unsigned long long sum = warp_sum(done);
                 done = 0;
                 if (lane == 0) {
+                    __threadfence();   // this warp's reservations before its completions
                     if (sum) atomicAdd(&ctl->finished, sum);
                     // units to complete: the thread pass's queue, and every child
                     // reserved so far when children are stepped within the step
@@ -1805,12 +1943,19 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
                         *reinterpret_cast<volatile unsigned long long*>(&ctl->finished);
                     const unsigned long long c2 = units0 + (cascade ? stored_rows(P) - n0 : 0ull);
                     finish = f == c1 && c1 == c2;
+                    progress = f + c2 + *reinterpret_cast<volatile unsigned long long*>(&ctl->beat);
                 }
                 finish = __shfl_sync(kAll, finish ? 1 : 0, 0) != 0;
+                progress = __shfl_sync(kAll, progress, 0);
             }
             if (finish) break;
             // idle: back off from 256 ns to 4 us (64 ns while a row is being
-            // written); the wait is bounded by the time spent idle
+            // written); the idle time counts from the last progress seen
+            // (rows stored or completed, beats of long chains)
+            if (!hold && progress != seen) {
+                seen = progress;
+                idle_ns = 0;
+            }
             const unsigned int nap = hold ? 64u : 256u << min(idle, 4u);
             ++idle;
             idle_ns += nap;
@@ -1823,6 +1968,10 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(Dev
         }
         idle = 0;
         idle_ns = 0;
+        if (++rounds == kBeatRounds) {
+            rounds = 0;
+            if (lane == 0) atomicAdd(&ctl->beat, 1ull);
+        }
         // ---- 5. one round of warp-shared draws for the active lanes
         const uint32_t n_win = active ? min(kWindow, pl.N - k_done) : 0u;
         const uint32_t s_end = s + n_win;
@@ -1998,6 +2147,18 @@ __global__ void k_tail_begin(DevParticles P, Scratch S, DevCtl* ctl) {
     for (long long r = n0 + t0; r < P.capacity; r += stride) P.type[r] = kNotReady;
     const long long used = min((long long)ctl->hot_hw, S.hot_cap);
     for (long long q = t0; q < used; q += stride) S.hot[q].idx = kNoItem;
+}
+
+// Start of a push step run as one persistent pass (k_push<true>): the rows
+// past the initial ones are marked not written, so that a lane taking a child
+// row waits for its writer, and the step is marked as a tail pass (k_tail_end
+// then caps the count and clears the rows past it).
+__global__ void k_push_begin(DevParticles P, DevCtl* ctl) {
+    const long long n0 = ctl->n_init;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0) ctl->tail = 1;
+    for (long long r = n0 + t0; r < P.capacity; r += stride) P.type[r] = kNotReady;
 }
 
 // End of the step: after a tail pass the count is capped at the capacity
@@ -2582,7 +2743,7 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
                                                       kNetSmemBytes);
         ctx->step_net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push, kLaneThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push<true>, kLaneThreads, 0);
         ctx->push_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
         cudaFuncSetAttribute(k_samp, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2830,6 +2991,7 @@ static qed_status push_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_
     qed_status st = ensure_scratch(ctx, p->capacity);
     if (st != QED_OK) return st;
     StepParams SP = make_params(ctx->cfg, step_index);   // the sampler is not used
+    SP.wait_ns = ctx->wait_ns;
     const DevParticles D = to_dev(p);
     const Scratch S = make_scratch(ctx);
     const bool cascade = cascade_enabled(ctx->cfg);
@@ -2861,16 +3023,35 @@ static qed_status push_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_
         LaunchScope ls(ctx, QED_KERNEL_CONTROL);
         k_step_init<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, 0);
     }
+    if (cascade && ctx->tail_rows > 0) {
+        // the whole step as one persistent pass: children are taken as they
+        // are appended (no generation waits for the one before)
+        {
+            LaunchScope ls(ctx, QED_KERNEL_CONTROL);
+            k_push_begin<<<ctx->sms * 8, 256, 0, ctx->stream>>>(D, ctx->d_ctl);
+        }
+        {
+            LaunchScope ls(ctx, QED_KERNEL_HOT);
+            k_push<true><<<ctx->push_blocks, kLaneThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+        }
+        {
+            LaunchScope ls(ctx, QED_KERNEL_CONTROL);
+            k_tail_end<<<ctx->sms * 8, 256, 0, ctx->stream>>>(D, S, ctx->d_ctl);
+        }
+        QED_CUDA(ctx, cudaGetLastError());
+        if (out) return qed_read_stats(ctx, out);
+        return QED_OK;
+    }
     for (int pass = 0; pass < ctx->cfg.max_passes; ++pass) {
         QED_CUDA(ctx, cudaMemsetAsync(&ctx->d_ctl->push_head, 0, sizeof(unsigned long long),
                                       ctx->stream));
         {
             LaunchScope ls(ctx, QED_KERNEL_HOT);
-            k_push<<<ctx->push_blocks, kLaneThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+            k_push<false><<<ctx->push_blocks, kLaneThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
         }
         {
             LaunchScope ls(ctx, QED_KERNEL_CONTROL);
-            // no tail pass: every generation runs k_push
+            // generation by generation (tail_rows 0, or no cascade)
             k_advance<<<1, 1, 0, ctx->stream>>>(ctx->d_ctl, D.count, D.capacity, cascade ? 1 : 0,
                                                 ctx->cfg.max_passes, 0ll, 0ull, 0);
         }

@@ -63,7 +63,8 @@ def test_push_uniform_field_emission():
 def test_push_clumped_cascade():
     arr = I.clumped_mixed(4133, 20081049, hot_fraction=0.02)
     rep, g_st, _, _ = _check(arr, 3, 4133 * 20, 20081049, mask=3, cascade=True)
-    assert g_st["pairs"] > 0 and g_st["passes"] > 1
+    # the cascade runs as one persistent pass that takes children as they come
+    assert g_st["pairs"] > 0 and g_st["tail"] == 1 and g_st["passes"] == 1
 
 
 def test_push_without_recoil():
@@ -153,7 +154,7 @@ def test_push_capacity_overflow_reports_required_rows():
     assert st["status"] == qed.QED_ERR_CAPACITY
     assert st["required_capacity"] > 2100
     assert store.n() == 2100
-    # with the cascade on, the generations stop at the overflow
+    # with the cascade on (one persistent pass) the step reports the overflow too
     store = qed.ParticleStore.from_numpy(arr, capacity=2100)
     ctx2 = qed.Context(process_mask=3, cascade=True)
     st = ctx2.event_step(store, 0, push=True)
@@ -232,3 +233,68 @@ def test_push_one_row_per_cell_is_the_push_step():
         assert np.array_equal(A[k][n:][ia], B[k][n:][ib]), k
     with pytest.raises(qed.QEDError):
         b_ctx.event_step_push_cells(b, 1, cd, 0)
+
+
+def _by_id(d):
+    o = np.argsort(d["id"])
+    return {k: v[o] for k, v in d.items()}
+
+
+@pytest.mark.parametrize("cells", [False, True])
+def test_push_persistent_pass_equals_generations(cells):
+    # the whole step in one persistent launch (children taken as soon as they
+    # are reserved) against the generation loop (tail_rows 0): the draws are
+    # keyed by (id, step, sub-step) and the push is a fixed sequence of
+    # binary32 operations, so statistics and store (by id) are equal bit for
+    # bit whatever the order in which the lanes take the rows
+    n = 30011
+    arr = I.clumped_mixed(n, 20081049, hot_fraction=0.01)
+    cell = torch.from_numpy((np.arange(n) // 16).astype(np.int32)).cuda()
+    out = []
+    for tail in (0, None):
+        ctx = qed.Context(seed=41, process_mask=3, cascade=True)
+        if tail is not None:
+            ctx.set_tail(tail)
+        store = qed.ParticleStore.from_numpy(arr, capacity=n * 40)
+        if cells:
+            st = ctx.event_step_push_cells(store, 6, cell, (n + 15) // 16)
+        else:
+            st = ctx.event_step(store, 6, push=True)
+        out.append((st, store.to_numpy()))
+    (g, a), (t, b) = out
+    assert g["status"] == 0 and t["status"] == 0
+    assert g["tail"] == 0 and g["passes"] > 2 and t["tail"] == 1 and t["passes"] == 1
+    for k in ("substeps", "emissions", "pairs", "children", "plans", "candidates", "max_N",
+              "guard_hits", "count"):
+        assert g[k] == t[k], (k, g[k], t[k])
+    for k in a:   # initial rows in place, then the children by id
+        np.testing.assert_array_equal(a[k][:n], b[k][:n], err_msg=k)
+    A, B = _by_id({k: v[n:] for k, v in a.items()}), _by_id({k: v[n:] for k, v in b.items()})
+    for k in A:
+        np.testing.assert_array_equal(A[k], B[k], err_msg=k)
+
+
+def test_push_persistent_pass_wait_limit_ends_the_step_with_timeout():
+    # failure detection without a fault: with a wait limit of 1 ns the
+    # persistent pass's warps give up at their first idle poll (more lanes
+    # than rows), the step ends with QED_ERR_TIMEOUT, and at the default limit
+    # the context steps as a fresh one does
+    n = 3000
+    arr = I.clumped_mixed(n, 52, hot_fraction=0.05)
+    ctx = qed.Context(seed=8, process_mask=3, cascade=True)
+    ctx.set_wait_limit(1)
+    store = qed.ParticleStore.from_numpy(arr, capacity=n * 40)
+    st = ctx.event_step(store, 2, push=True)
+    assert st["status"] == qed.QED_ERR_TIMEOUT and st["tail"] == 1, st
+    ctx.set_wait_limit(0)
+    again = qed.ParticleStore.from_numpy(arr, capacity=n * 40)
+    st = ctx.event_step(again, 2, push=True)
+    ref_ctx = qed.Context(seed=8, process_mask=3, cascade=True)
+    ref = qed.ParticleStore.from_numpy(arr, capacity=n * 40)
+    st_ref = ref_ctx.event_step(ref, 2, push=True)
+    assert st["status"] == 0 and st_ref["status"] == 0
+    for k in ("substeps", "emissions", "pairs", "children", "plans", "count"):
+        assert st[k] == st_ref[k], (k, st[k], st_ref[k])
+    a, b = _by_id(again.to_numpy()), _by_id(ref.to_numpy())
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)

@@ -1,5 +1,5 @@
-"""Pins of the oracle's per-cell planning (one sub-step per cell, as the
-first line of Algorithms 1 and 2 plans it).  CPU only.
+"""Pins of the oracle's per-cell planning (one sub-step per cell, with which
+Algorithms 1 and 2 start).  CPU only.
 
 A cell's count must be the largest per-particle count of its members: equal
 to a lone member's plan, at least every member's, and attained by one of
