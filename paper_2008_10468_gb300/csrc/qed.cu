@@ -745,6 +745,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
 // Push mode: Algorithm 1 with the Boris push before every e+- draw
 // ---------------------------------------------------------------------------
 constexpr int kPushGroupMax = 16;   // busy lanes of a drained warp that switch to group mode
+constexpr int kPushPlanBatch = 8;   // lanes wanting a plan before the warp plans
 // A push-mode step.  The push makes every sub-step depend on the one before,
 // so a lane steps one particle through its sub-steps in order; a lane whose
 // particle is done takes the next row (the idle lanes of a warp share one
@@ -789,6 +790,8 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
     bool busy = false, drained = kStream ? false : n <= 0, photon = false, electron = false;
     bool need_plan = false, removed = false;
     bool waiting = false;                          // kStream: the lane's row is still being written
+    bool ev = false;                               // an accepted event not yet applied
+    float ev_x = 0.0f, ev_eps = 0.0f, ev_chi = 0.0f;
     unsigned int units = 0;                        // kStream: rows this lane completed, not yet added
     unsigned long long pend_lo = 0, pend_hi = 0;   // kStream: the warp's pending child indices
     unsigned long long idle_ns = 0, seen = 0;      // kStream: bounded wait
@@ -938,9 +941,19 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
                 if (lane == 0) atomicAdd(&ctl->beat, 1ull);
             }
         }
-        // plan the lane's particle (Algorithms 1/2, planning); true if it is done
+        // plan the lane's particle (Algorithms 1/2, planning); true if it is
+        // done.  An accepted event of the lane's last sub-step is applied
+        // first (recoil or decay, children), so that the lanes of a warp
+        // apply their events together with their plans.
         auto plan_now = [&]() -> bool {
             need_plan = false;
+            if (ev) {
+                ev = false;
+                removed = apply_event(P, S, SP, ctl, i, id, photon, ev_x, ev_eps, ev_chi, step, s,
+                                      t_rem, st, stats, true, false, F, kStream);
+                ++s;
+                if (removed || !time_positive(t_rem)) return true;
+            }
             pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, F.Ex, F.Ey,
                                F.Ez, F.Bx, F.By, F.Bz, t_rem, &chi, &eps);
             if (!(eps > 0.0f)) return true;
@@ -1075,9 +1088,16 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
                     if (k == pl.N) done = true;
                 }
             }
-        } else if (busy && need_plan) {
-            done = plan_now();
-        } else if (busy) {
+        } else {
+            // A plan taken by one or two lanes at a time would make the warp
+            // run the planner in most rounds while the others wait: a lane
+            // that wants a plan waits until kPushPlanBatch lanes want one, or
+            // until no busy lane is left to step, and then steps its first
+            // sub-step in the same round.
+            const unsigned int pm = __ballot_sync(kAll, busy && need_plan);
+            if ((__popc(pm) >= kPushPlanBatch || pm == bm) && busy && need_plan) done = plan_now();
+        }
+        if (!(drained && m <= kPushGroupMax) && busy && !need_plan && !done) {
             float b = pl.b, c_h = pl.c_h, chi_k = chi, eps_k = eps;
             uint32_t T = pl.T;
             if (!photon) {
@@ -1103,14 +1123,14 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
                 acc = u01(yw) < acceptance(sm.syn, photon, b, c_h, x, &dtmp);
             }
             if (acc) {
-                const ftime t_after = (k + 1u == pl.N) ? ftime{0.0f, 0.0f}
-                                                       : time_sub_mul(t_rem, k + 1u, pl.h);
-                removed = apply_event(P, S, SP, ctl, i, id, photon, x, eps_k, chi_k, step, s,
-                                      t_after, st, stats, true, false, F, kStream);
-                ++s;
-                t_rem = t_after;
-                if (removed || !time_positive(t_rem)) done = true;
-                else need_plan = true;
+                // the event is applied with the next plan (plan_now), s and
+                // the pushed state stay until then
+                t_rem = (k + 1u == pl.N) ? ftime{0.0f, 0.0f} : time_sub_mul(t_rem, k + 1u, pl.h);
+                ev = true;
+                ev_x = x;
+                ev_eps = eps_k;
+                ev_chi = chi_k;
+                need_plan = true;
             } else {
                 ++s;
                 if (++k == pl.N) done = true;
