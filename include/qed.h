@@ -464,8 +464,7 @@ qed_status qed_time_split(const float* t_hi, const float* t_lo, const uint32_t* 
  * the legacy default stream); with cfg->cascade_in_step it synchronises that
  * stream after every cascade generation, and if out != NULL at the end.
  * The first call on a device looks up the array and the launch geometry with
- * that device current (make that first call before any stream capture);
- * later calls on the device reuse them.  The array is shared by every call
+ * that device current; later calls on the device reuse them.  The array is shared by every call
  * and keeps the contents of the last one: each step starts by resetting what
  * it reads, but calls whose work overlaps on the GPU (other streams, other
  * host threads) race with each other; serialise them.
