@@ -801,57 +801,46 @@ def run_sampler(arr, pristine, store, cap, n, dev, args, restore, plain_value):
 
 
 def run_e2e(ctx, arr, cap, dev, args):
-    """Same metric through the API with host buffers: per step copy the
-    population from pinned host memory, step, and copy the result back: the
-    momenta and types of the original rows (the only fields a step changes
-    there) and every field of the appended children, so that the host holds
-    the whole updated store."""
+    """Same metric through the API with host buffers: qed_event_step_host on a
+    page-locked host store, which copies the population to the device, steps
+    it and copies back what the step changed (momenta and types of the
+    original rows, every field of the appended children), so that the host
+    holds the whole updated store.  Timed with CUDA events around the call;
+    the host store is restored between steps outside the timed region."""
     import torch
     from paper_2008_10468_gb300 import qed
     n = len(arr["px"])
-    host = {}
-    for k in qed.FLOAT_FIELDS:
-        host[k] = torch.from_numpy(arr[k]).pin_memory()
-    host["id"] = torch.from_numpy(arr["id"].view(np.int64)).pin_memory()
-    host["type"] = torch.from_numpy(arr["type"]).pin_memory()
-    out = {k: torch.empty(cap, dtype=v.dtype).pin_memory() for k, v in host.items()}
-    for k, v in host.items():   # fields the step leaves unchanged on the original rows
-        out[k][:n].copy_(v)
-    store = qed.ParticleStore(cap, device=dev)
+    h = qed.HostStore.from_numpy(arr, capacity=cap)
+    keep = {k: getattr(h, k)[:n].clone() for k in ("px", "py", "pz", "type")}
     stream = torch.cuda.current_stream()
     steps = max(2, min(args.steps, 5))
     total = 0.0
     subs = 0
     h2d = d2h = 0
-    for k in range(steps + 1):
+    parts = []
+    for k in range(steps + 2):
+        for key, v in keep.items():
+            getattr(h, key)[:n].copy_(v)
+        h.count = n
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        b_in = 0
-        for key, t in host.items():
-            getattr(store, key)[:n].copy_(t, non_blocking=True)
-            b_in += t.numel() * t.element_size()
-        store.type[n:].fill_(qed.REMOVED)
-        store.count.fill_(n)
-        st = ctx.event_step(store, 3000 + k)
-        m = st["count"]
-        b_out = 0
-        for key in host:
-            lo = 0 if key in ("px", "py", "pz", "type") else n
-            src = getattr(store, key)[lo:m]
-            out[key][lo:m].copy_(src, non_blocking=True)
-            b_out += src.numel() * src.element_size()
+        st = ctx.event_step_host(h, 3000 + k)
         e1.record(stream)
         torch.cuda.synchronize()
-        if k == 0:
-            continue  # first one warms the pinned paths
+        if st["status"] != 0:
+            raise SystemExit("host-store step failed with status %d" % st["status"])
+        if k < 2:
+            continue  # the first calls allocate the device copy and warm the host link
+        m = st["count"]
         total += e0.elapsed_time(e1)
         subs += st["substeps"]
-        h2d += b_in
-        d2h += b_out
+        h2d += 49 * n
+        d2h += 13 * m + 36 * (m - n)
     return {"value": subs / (total / 1e3), "unit": UNIT,
-            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps}
+            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
+            "ms_per_step": total / steps, "api": "qed_event_step_host (page-locked host store)"}
 
 
 # --------------------------------------------------------------------------

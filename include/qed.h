@@ -94,6 +94,17 @@ typedef struct {
     int64_t capacity;          /* rows allocated in every array                 */
 } qed_particles;
 
+/* Particle store in host memory (host pointers, caller-owned), for
+ * qed_event_step_host: the fields of qed_particles, with the row count on
+ * the host. */
+typedef struct {
+    float *px, *py, *pz, *Ex, *Ey, *Ez, *Bx, *By, *Bz, *w;
+    uint64_t *id;
+    uint8_t *type;
+    int64_t count;             /* rows in use: read before the step, written after */
+    int64_t capacity;          /* rows every array holds                        */
+} qed_host_particles;
+
 /* Statistics of the last step (host struct). */
 typedef struct {
     uint64_t substeps;         /* sub-steps executed (loop iterations of Alg. 1/2) */
@@ -209,6 +220,24 @@ qed_status qed_plan_cells(qed_ctx* ctx, const qed_particles* p, int64_t n, const
  * Errors: QED_ERR_ARG, QED_ERR_CUDA, QED_ERR_CAPACITY, QED_ERR_TIMEOUT. */
 qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
                           qed_step_stats* out);
+
+/* qed_event_step on a store in host memory (the same step: Sec. 2,
+ * Algorithms 1 and 2).  The context keeps a device copy of the store's
+ * layout (capacity rows; allocated on first use and when the capacity
+ * changes).  Rows [0, h->count) of every field are copied to it, the step
+ * runs there, and what the step changed is copied back: momenta and types
+ * of the rows it was given, every field of the rows it appended; h->count
+ * becomes the rows in use after the step.  Copies are cudaMemcpyAsync on the
+ * context stream: page-locked host arrays (cudaHostAlloc, cudaHostRegister)
+ * copy at the host link's rate, pageable ones are staged by the driver.
+ * Synchronises.  *out (nullable) receives the step's statistics.  If the
+ * step does not succeed (QED_ERR_CAPACITY with the rows required,
+ * QED_ERR_TIMEOUT, ...) nothing is copied back: the host store is left as it
+ * was.  Errors: QED_ERR_ARG (a null array, capacity outside [1, 2^32),
+ * count outside [0, capacity]), QED_ERR_CUDA, and the statuses of
+ * qed_event_step. */
+qed_status qed_event_step_host(qed_ctx* ctx, qed_host_particles* h, uint64_t step_index,
+                               qed_step_stats* out);
 
 /* The same step with the Boris push of Algorithm 1 (Sec. 2.2: the particle is
  * moved by a Boris step of one sub-step, then chi is recomputed and
@@ -492,7 +521,8 @@ enum { QED_PROBE_MUL32 = 0, QED_PROBE_FMA32 = 1, QED_PROBE_EX2 = 2, QED_PROBE_AL
 qed_status qed_peak_probe(int kind, int64_t iters, double* ops_per_s, double* ms, void* stream);
 
 /* sizeof of a public struct by name ("qed_config", "qed_particles",
- * "qed_step_stats", "qed_event_record"), or 0 for an unknown name.  Host
+ * "qed_host_particles", "qed_step_stats", "qed_event_record"), or 0 for an
+ * unknown name.  Host
  * only; lets bindings check their struct mirrors without a GPU. */
 size_t qed_abi_struct_size(const char* name);
 

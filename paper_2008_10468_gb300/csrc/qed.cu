@@ -2440,6 +2440,8 @@ struct qed_ctx {
     int push_blocks;            // resident blocks of the push-mode kernel
     unsigned int* d_Ncell;      // per-cell counts of the push mode with cells
     long long ncell_cap;
+    unsigned char* d_hstore;    // device copy of a host store (qed_event_step_host)
+    long long hstore_cap;
     // compaction
     Mirror mirror;
     long long mirror_cap;
@@ -2798,6 +2800,7 @@ qed_status qed_destroy(qed_ctx* ctx) {
     if (ctx->d_hot) cudaFree(ctx->d_hot);
     if (ctx->d_Ncell) cudaFree(ctx->d_Ncell);
     if (ctx->d_samp) cudaFree(ctx->d_samp);
+    if (ctx->d_hstore) cudaFree(ctx->d_hstore);
     free_graph(ctx);
     float* f[] = {ctx->mirror.px, ctx->mirror.py, ctx->mirror.pz, ctx->mirror.Ex, ctx->mirror.Ey,
                   ctx->mirror.Ez, ctx->mirror.Bx, ctx->mirror.By, ctx->mirror.Bz, ctx->mirror.w};
@@ -3102,6 +3105,75 @@ qed_status qed_event_step_push_cells(qed_ctx* ctx, const qed_particles* p, uint6
         ncells > 0xffffffffll)
         return set_err(ctx, QED_ERR_ARG, "qed_event_step_push_cells: bad argument");
     return push_step(ctx, p, step_index, out, cell, ncells);
+}
+
+}  // extern "C"
+__global__ void k_set_count(long long* count, long long n) { *count = n; }
+extern "C" {
+
+// The store in host memory: its rows go to a device copy owned by the
+// context (SoA, capacity rows: ten float arrays, the ids, the types, the
+// count), the step runs there, and what the step changed comes back.
+qed_status qed_event_step_host(qed_ctx* ctx, qed_host_particles* h, uint64_t step_index,
+                               qed_step_stats* out) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!h || !h->px || !h->py || !h->pz || !h->Ex || !h->Ey || !h->Ez || !h->Bx || !h->By ||
+        !h->Bz || !h->w || !h->id || !h->type || h->capacity <= 0 || h->capacity >= (1ll << 32) ||
+        h->count < 0 || h->count > h->capacity || step_index > 0xffffffffull)
+        return set_err(ctx, QED_ERR_ARG, "qed_event_step_host: bad argument");
+    const long long cap = h->capacity, n = h->count;
+    const size_t f4 = sizeof(float) * (size_t)cap;
+    const size_t id_off = 10 * f4, type_off = id_off + sizeof(uint64_t) * (size_t)cap;
+    const size_t count_off = (type_off + (size_t)cap + 15) / 16 * 16;
+    if (ctx->hstore_cap != cap) {
+        if (ctx->d_hstore) cudaFree(ctx->d_hstore);
+        ctx->d_hstore = nullptr;
+        ctx->hstore_cap = 0;
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_hstore, count_off + sizeof(long long)));
+        ctx->hstore_cap = cap;
+    }
+    unsigned char* base = ctx->d_hstore;
+    float* dev_f[10];
+    for (int k = 0; k < 10; ++k) dev_f[k] = reinterpret_cast<float*>(base + (size_t)k * f4);
+    float* host_f[10] = {h->px, h->py, h->pz, h->Ex, h->Ey, h->Ez, h->Bx, h->By, h->Bz, h->w};
+    qed_particles d;
+    d.px = dev_f[0]; d.py = dev_f[1]; d.pz = dev_f[2];
+    d.Ex = dev_f[3]; d.Ey = dev_f[4]; d.Ez = dev_f[5];
+    d.Bx = dev_f[6]; d.By = dev_f[7]; d.Bz = dev_f[8];
+    d.w = dev_f[9];
+    d.id = reinterpret_cast<uint64_t*>(base + id_off);
+    d.type = base + type_off;
+    d.count = reinterpret_cast<int64_t*>(base + count_off);
+    d.capacity = cap;
+    cudaStream_t s = ctx->stream;
+    const auto h2d = [&](void* dst, const void* src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    for (int k = 0; k < 10; ++k) QED_CUDA(ctx, h2d(dev_f[k], host_f[k], sizeof(float) * (size_t)n));
+    QED_CUDA(ctx, h2d(d.id, h->id, sizeof(uint64_t) * (size_t)n));
+    QED_CUDA(ctx, h2d(d.type, h->type, (size_t)n));
+    QED_CUDA(ctx, cudaMemsetAsync(d.type + n, QED_REMOVED, (size_t)(cap - n), s));
+    k_set_count<<<1, 1, 0, s>>>(reinterpret_cast<long long*>(d.count), n);
+    QED_CUDA(ctx, cudaGetLastError());
+    qed_step_stats st{};
+    const qed_status r = qed_event_step(ctx, &d, step_index, &st);
+    if (out) *out = st;
+    if (r != QED_OK) return r;   // the host store is left as it was
+    const long long m = st.count;
+    const auto d2h = [&](void* dst, const void* src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+    };
+    // the step changes momenta and types of the rows it was given, and
+    // writes every field of the rows it appends
+    for (int k = 0; k < 10; ++k) {
+        const long long lo = k < 3 ? 0 : n;
+        QED_CUDA(ctx, d2h(host_f[k] + lo, dev_f[k] + lo, sizeof(float) * (size_t)(m - lo)));
+    }
+    QED_CUDA(ctx, d2h(h->id + n, d.id + n, sizeof(uint64_t) * (size_t)(m - n)));
+    QED_CUDA(ctx, d2h(h->type, d.type, (size_t)m));
+    QED_CUDA(ctx, cudaStreamSynchronize(s));
+    h->count = m;
+    return QED_OK;
 }
 
 qed_status qed_read_stats(qed_ctx* ctx, qed_step_stats* out) {
@@ -4059,6 +4131,7 @@ size_t qed_abi_struct_size(const char* name) {
     if (!strcmp(name, "qed_particles")) return sizeof(qed_particles);
     if (!strcmp(name, "qed_step_stats")) return sizeof(qed_step_stats);
     if (!strcmp(name, "qed_event_record")) return sizeof(qed_event_record);
+    if (!strcmp(name, "qed_host_particles")) return sizeof(qed_host_particles);
     return 0;
 }
 

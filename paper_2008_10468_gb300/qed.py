@@ -43,6 +43,11 @@ class Particles(C.Structure):
         ("id", C.c_void_p), ("type", C.c_void_p), ("count", C.c_void_p), ("capacity", C.c_int64)]
 
 
+class HostParticles(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in FLOAT_FIELDS] + [
+        ("id", C.c_void_p), ("type", C.c_void_p), ("count", C.c_int64), ("capacity", C.c_int64)]
+
+
 class StepStats(C.Structure):
     _fields_ = [("substeps", C.c_uint64), ("emissions", C.c_uint64), ("pairs", C.c_uint64),
                 ("children", C.c_uint64), ("guard_hits", C.c_uint64), ("plans", C.c_uint64),
@@ -87,6 +92,8 @@ def lib():
         L.qed_event_step.restype = st
         L.qed_event_step_push.argtypes = [vp, C.POINTER(Particles), u64, C.POINTER(StepStats)]
         L.qed_event_step_push.restype = st
+        L.qed_event_step_host.argtypes = [vp, C.POINTER(HostParticles), u64, C.POINTER(StepStats)]
+        L.qed_event_step_host.restype = st
         L.qed_plan_cells.argtypes = [vp, C.POINTER(Particles), i64, vp, i64, vp]
         L.qed_plan_cells.restype = st
         L.qed_event_step_push_cells.argtypes = [vp, C.POINTER(Particles), u64, vp, i64,
@@ -236,6 +243,58 @@ class ParticleStore:
         return p
 
 
+class HostStore:
+    """Caller-owned SoA particle arrays in host memory (see qed_host_particles),
+    page-locked by default."""
+
+    def __init__(self, capacity, pinned=True):
+        self.capacity = int(capacity)
+        kw = dict(pin_memory=bool(pinned))
+        for k in FLOAT_FIELDS:
+            setattr(self, k, torch.zeros(self.capacity, dtype=torch.float32, **kw))
+        self.id = torch.zeros(self.capacity, dtype=torch.int64, **kw)
+        self.type = torch.full((self.capacity,), REMOVED, dtype=torch.uint8, **kw)
+        self.count = 0
+
+    @classmethod
+    def from_numpy(cls, arrs, capacity=None, pinned=True):
+        n = int(arrs["px"].shape[0])
+        s = cls(capacity if capacity is not None else max(n, 1), pinned)
+        s.load(arrs)
+        return s
+
+    def load(self, arrs):
+        n = int(arrs["px"].shape[0])
+        if n > self.capacity:
+            raise QEDError(QED_ERR_ARG, "more rows than capacity")
+        for k in FLOAT_FIELDS:
+            getattr(self, k)[:n].copy_(torch.from_numpy(np.ascontiguousarray(arrs[k], np.float32)))
+        self.id[:n].copy_(torch.from_numpy(np.ascontiguousarray(arrs["id"]).view(np.int64)))
+        self.type[:n].copy_(torch.from_numpy(np.ascontiguousarray(arrs["type"], np.uint8)))
+        self.type[n:].fill_(REMOVED)
+        self.count = n
+
+    def n(self):
+        return self.count
+
+    def to_numpy(self):
+        n = self.count
+        out = {k: getattr(self, k)[:n].numpy().copy() for k in FLOAT_FIELDS}
+        out["id"] = self.id[:n].numpy().view(np.uint64).copy()
+        out["type"] = self.type[:n].numpy().copy()
+        return out
+
+    def struct(self):
+        p = HostParticles()
+        for k in FLOAT_FIELDS:
+            setattr(p, k, getattr(self, k).data_ptr())
+        p.id = self.id.data_ptr()
+        p.type = self.type.data_ptr()
+        p.count = self.count
+        p.capacity = self.capacity
+        return p
+
+
 class Context:
     """A library context bound to a CUDA stream (default: torch's current stream)."""
 
@@ -338,6 +397,18 @@ class Context:
             return stats_dict(s)
         self._check(fn(self._h, C.byref(p), int(step), None))
         return None
+
+    def event_step_host(self, hstore, step):
+        """One global step on a HostStore (qed_event_step_host): its rows go to
+        the device, the step runs, the changes come back; returns the
+        statistics dict.  On an unsuccessful step the host store is unchanged."""
+        p = hstore.struct()
+        s = StepStats()
+        st = lib().qed_event_step_host(self._h, C.byref(p), int(step), C.byref(s))
+        if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_TIMEOUT):   # step outcomes
+            self._check(st)
+        hstore.count = int(p.count)
+        return stats_dict(s)
 
     def event_step_push_cells(self, store, step, cell, ncells):
         """Push-mode step with one sub-step per cell (cell: int32 CUDA tensor of

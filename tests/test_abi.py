@@ -46,9 +46,11 @@ def test_struct_mirrors_match(libqed):
     libqed.qed_abi_struct_size.restype = C.c_size_t
     libqed.qed_abi_struct_size.argtypes = [C.c_char_p]
     sizes = {n: libqed.qed_abi_struct_size(n.encode()) for n in
-             ("qed_config", "qed_particles", "qed_step_stats", "qed_event_record")}
+             ("qed_config", "qed_particles", "qed_host_particles", "qed_step_stats",
+              "qed_event_record")}
     assert sizes["qed_config"] == C.sizeof(qed.Config)
     assert sizes["qed_particles"] == C.sizeof(qed.Particles)
+    assert sizes["qed_host_particles"] == C.sizeof(qed.HostParticles)
     assert sizes["qed_step_stats"] == C.sizeof(qed.StepStats)
     assert sizes["qed_event_record"] == qed.EVENT_DTYPE.itemsize
     assert libqed.qed_abi_struct_size(b"nope") == 0

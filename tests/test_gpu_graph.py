@@ -282,3 +282,62 @@ def test_tail_pass_wait_limit_ends_the_step_with_timeout(graph):
     a, b = _sorted(again.to_numpy()), _sorted(ref.to_numpy())
     for k in a:
         np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_host_store_step_equals_device_step():
+    # qed_event_step_host: the store in host memory, copied in, stepped and
+    # copied back by the library; the same kernels run on the same rows, so
+    # the result equals qed_event_step's bit for bit (initial rows in place,
+    # children by id), for page-locked and pageable host arrays
+    n = 5000
+    arr = I.clumped_mixed(n, 57, hot_fraction=0.03)
+    ref_ctx = qed.Context(seed=12)
+    ref = qed.ParticleStore.from_numpy(arr, capacity=n * 60)
+    st_ref = ref_ctx.event_step(ref, 4)
+    assert st_ref["children"] > 0
+    R = ref.to_numpy()
+    for pinned in (True, False):
+        ctx = qed.Context(seed=12)
+        h = qed.HostStore.from_numpy(arr, capacity=n * 60, pinned=pinned)
+        st = ctx.event_step_host(h, 4)
+        assert st["status"] == 0 and h.n() == st_ref["count"]
+        for k in ("substeps", "emissions", "pairs", "children", "plans", "count"):
+            assert st[k] == st_ref[k], (k, st[k], st_ref[k])
+        H = h.to_numpy()
+        for k in H:
+            np.testing.assert_array_equal(H[k][:n], R[k][:n], err_msg=k)
+        a, b = _sorted({k: v[n:] for k, v in H.items()}), _sorted({k: v[n:] for k, v in R.items()})
+        for k in a:
+            np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+        # a second step continues from the updated host store
+        st2 = ctx.event_step_host(h, 5)
+        st2_ref = ref_ctx.event_step(ref, 5)
+        for k in ("substeps", "emissions", "pairs", "children", "count"):
+            assert st2[k] == st2_ref[k], (k, st2[k], st2_ref[k])
+        ref = qed.ParticleStore.from_numpy(arr, capacity=n * 60)
+        ref_ctx.event_step(ref, 4)
+
+
+def test_host_store_step_leaves_the_store_on_failure():
+    n = 2000
+    arr = I.uniform_field_electrons(n, 20081047)
+    ctx = qed.Context(seed=3, process_mask=1, cascade=False)
+    h = qed.HostStore.from_numpy(arr, capacity=2100)
+    before = h.to_numpy()
+    st = ctx.event_step_host(h, 0)
+    assert st["status"] == qed.QED_ERR_CAPACITY and st["required_capacity"] > 2100
+    assert h.n() == n
+    after = h.to_numpy()
+    for k in before:
+        np.testing.assert_array_equal(before[k], after[k], err_msg=k)
+    # bad arguments
+    h.count = 2101
+    with pytest.raises(qed.QEDError):
+        ctx.event_step_host(h, 0)
+    h.count = n
+    with pytest.raises(qed.QEDError):
+        ctx.event_step_host(h, 1 << 33)
+    # empty store
+    e = qed.HostStore(16)
+    st = ctx.event_step_host(e, 0)
+    assert st["status"] == 0 and st["substeps"] == 0 and e.n() == 0
