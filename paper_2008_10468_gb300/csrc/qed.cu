@@ -2261,6 +2261,12 @@ __global__ void __launch_bounds__(kCompactThreads)
     k_compact_count(DevParticles P, StepParams SP, float drain_chi, double* hist,
                     unsigned int* block_live) {
     __shared__ unsigned int warp_tot[kCompactThreads / 32];
+    // the block's drained weight per bin, added to the spectrum once per bin:
+    // the drained photons crowd a few energy bins, and one global atomic per
+    // photon serialised on them
+    __shared__ double sh_hist[QED_SPECTRUM_BINS];
+    for (int b = threadIdx.x; b < QED_SPECTRUM_BINS; b += blockDim.x) sh_hist[b] = 0.0;
+    __syncthreads();
     const long long n = clamp_count(P);
     const long long base = (long long)blockIdx.x * kTile;
     unsigned int live = 0;
@@ -2281,7 +2287,7 @@ __global__ void __launch_bounds__(kCompactThreads)
                                               ((float)QED_SPECTRUM_BINS /
                                                (float)(QED_SPECTRUM_LOG10_MAX - QED_SPECTRUM_LOG10_MIN)));
                         bin = min(max(bin, 0), QED_SPECTRUM_BINS - 1);
-                        atomicAdd(&hist[bin], (double)P.w[i]);
+                        atomicAdd(&sh_hist[bin], (double)P.w[i]);
                     }
                     P.type[i] = QED_REMOVED;
                     t = QED_REMOVED;
@@ -2302,6 +2308,9 @@ __global__ void __launch_bounds__(kCompactThreads)
         for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
         if (threadIdx.x == 0) block_live[blockIdx.x] = w;
     }
+    if (hist)
+        for (int b = threadIdx.x; b < QED_SPECTRUM_BINS; b += blockDim.x)
+            if (sh_hist[b] != 0.0) atomicAdd(&hist[b], sh_hist[b]);
 }
 
 // Exclusive scan of the per-tile counts (one block); total -> ctl->live.
