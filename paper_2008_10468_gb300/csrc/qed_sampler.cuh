@@ -624,9 +624,12 @@ __device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f 
 
 // One hidden layer for one 16-row tile: C = W a + b from the A fragments
 // (hi, lo) of the layer below, then SiLU; the result replaces (hi, lo).
+// upper = false: rows 8..15 of the tile hold no sample; their activations are
+// left at 0 instead of going through SiLU (rows do not mix in the products, so
+// the other rows' results are unchanged).
 __device__ __forceinline__ void mma_hidden(const __nv_bfloat16* __restrict__ W,
                                            const float* __restrict__ bias, uint32_t (&Ah)[4][4],
-                                           uint32_t (&Al)[4][4]) {
+                                           uint32_t (&Al)[4][4], bool upper) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     float C[8][4];
 #pragma unroll
@@ -652,15 +655,27 @@ __device__ __forceinline__ void mma_hidden(const __nv_bfloat16* __restrict__ W,
     for (int nt = 0; nt < 8; ++nt) {
         const int kt = nt >> 1, q = (nt & 1) * 2;
         split_bf16x2(silu_fast(C[nt][0]), silu_fast(C[nt][1]), Ah[kt][q], Al[kt][q]);
-        split_bf16x2(silu_fast(C[nt][2]), silu_fast(C[nt][3]), Ah[kt][q + 1], Al[kt][q + 1]);
+    }
+    if (upper) {
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const int kt = nt >> 1, q = (nt & 1) * 2;
+            split_bf16x2(silu_fast(C[nt][2]), silu_fast(C[nt][3]), Ah[kt][q + 1], Al[kt][q + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+            Ah[kt][1] = Ah[kt][3] = 0u;
+            Al[kt][1] = Al[kt][3] = 0u;
+        }
     }
 }
 
 // The network's output logit (before b4 and the anchor) for rows g and g + 8
 // of one tile, whose inputs are (v0a, v1a) and (v0b, v1b); every lane of the
-// group g gets both.
+// group g gets both (upper = false: rows g + 8 hold no sample, ob is 0).
 __device__ __forceinline__ void mma_tile(const SamplerMma& S, float v0a, float v1a, float v0b,
-                                         float v1b, float& oa, float& ob) {
+                                         float v1b, float& oa, float& ob, bool upper = true) {
     const int lane = threadIdx.x & 31, t = lane & 3;
     uint32_t Ah[4][4], Al[4][4];
     // layer 1 (two inputs) on the CUDA cores, in the fragment layout
@@ -671,13 +686,16 @@ __device__ __forceinline__ void mma_tile(const SamplerMma& S, float v0a, float v
         const float w10 = S.W1[2 * n + 2], w11 = S.W1[2 * n + 3];
         const float za0 = fmaf(w00, v0a, fmaf(w01, v1a, S.b1[n]));
         const float za1 = fmaf(w10, v0a, fmaf(w11, v1a, S.b1[n + 1]));
-        const float zb0 = fmaf(w00, v0b, fmaf(w01, v1b, S.b1[n]));
-        const float zb1 = fmaf(w10, v0b, fmaf(w11, v1b, S.b1[n + 1]));
         const int kt = nt >> 1, q = (nt & 1) * 2;
         split_bf16x2(silu_fast(za0), silu_fast(za1), Ah[kt][q], Al[kt][q]);
-        split_bf16x2(silu_fast(zb0), silu_fast(zb1), Ah[kt][q + 1], Al[kt][q + 1]);
+        Ah[kt][q + 1] = Al[kt][q + 1] = 0u;
+        if (upper) {
+            const float zb0 = fmaf(w00, v0b, fmaf(w01, v1b, S.b1[n]));
+            const float zb1 = fmaf(w10, v0b, fmaf(w11, v1b, S.b1[n + 1]));
+            split_bf16x2(silu_fast(zb0), silu_fast(zb1), Ah[kt][q + 1], Al[kt][q + 1]);
+        }
     }
-    mma_hidden(S.W2, S.b2, Ah, Al);
+    mma_hidden(S.W2, S.b2, Ah, Al, upper);
     // layer 3 and the output dot product with w4
     const int g = lane >> 2;
     float C[8][4];
@@ -705,7 +723,13 @@ __device__ __forceinline__ void mma_tile(const SamplerMma& S, float v0a, float v
     for (int nt = 0; nt < 8; ++nt) {
         const float w0 = S.w4[8 * nt + 2 * t], w1 = S.w4[8 * nt + 2 * t + 1];
         pa = fmaf(w0, silu_fast(C[nt][0]), fmaf(w1, silu_fast(C[nt][1]), pa));
-        pb = fmaf(w0, silu_fast(C[nt][2]), fmaf(w1, silu_fast(C[nt][3]), pb));
+    }
+    if (upper) {
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const float w0 = S.w4[8 * nt + 2 * t], w1 = S.w4[8 * nt + 2 * t + 1];
+            pb = fmaf(w0, silu_fast(C[nt][2]), fmaf(w1, silu_fast(C[nt][3]), pb));
+        }
     }
     pa += __shfl_xor_sync(0xffffffffu, pa, 1);
     pa += __shfl_xor_sync(0xffffffffu, pa, 2);
@@ -740,7 +764,7 @@ __device__ __forceinline__ float mlp_infer_mma_some(const SamplerMma& S, MmaBuf&
         const float2 a = ra < n ? buf.in[ra] : make_float2(0.0f, 0.0f);
         const float2 b = rb < n ? buf.in[rb] : make_float2(0.0f, 0.0f);
         float oa, ob;
-        mma_tile(S, a.x, a.y, b.x, b.y, oa, ob);
+        mma_tile(S, a.x, a.y, b.x, b.y, oa, ob, n - 16 * mt > 8);
         if (t == 0) {
             buf.out[ra] = oa;
             buf.out[rb] = ob;
