@@ -746,6 +746,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
 // ---------------------------------------------------------------------------
 constexpr int kPushGroupMax = 16;   // busy lanes of a drained warp that switch to group mode
 constexpr int kPushPlanBatch = 8;   // lanes wanting a plan before the warp plans
+constexpr int kPushClaimBatch = 8;  // free lanes before the warp claims rows
 // A push-mode step.  The push makes every sub-step depend on the one before,
 // so a lane steps one particle through its sub-steps in order; a lane whose
 // particle is done takes the next row (the idle lanes of a warp share one
@@ -834,27 +835,40 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
     while (true) {
         const unsigned int free_lanes = __ballot_sync(kAll, !busy && !waiting);
         if (kStream) {
-            // rows for the free lanes: indices below the rows stored now
+            // rows for the free lanes: indices below the rows stored now.  A
+            // claim is a round trip to the control block: the free lanes wait
+            // until kPushClaimBatch of them want a row (or no lane is busy),
+            // and the stored count is read only for indices past the
+            // initial rows.
             int got = 0;
             unsigned long long base = 0;
-            if (free_lanes) {
+            const bool claim = free_lanes != 0 &&
+                               (__popc(free_lanes) >= kPushClaimBatch ||
+                                __ballot_sync(kAll, busy) == 0u);
+            if (claim) {
                 const int want = __popc(free_lanes);
                 if (lane == 0) {
-                    const unsigned long long lim =
-                        cascade ? stored_rows(P) : (unsigned long long)n_init;
+                    const unsigned long long n0 = (unsigned long long)n_init;
                     if (pend_lo == pend_hi) {
                         const unsigned long long h =
                             *reinterpret_cast<volatile unsigned long long*>(&ctl->push_head);
+                        const unsigned long long lim =
+                            (cascade && h + (unsigned long long)want > n0) ? max(stored_rows(P), n0)
+                                                                           : n0;
                         if (h < lim) {
                             const unsigned long long kk = min((unsigned long long)want, lim - h);
                             pend_lo = atomicAdd(&ctl->push_head, kk);
                             pend_hi = pend_lo + kk;
                         }
                     }
-                    if (pend_lo < pend_hi && pend_lo < lim) {
-                        got = (int)min((unsigned long long)want, min(pend_hi, lim) - pend_lo);
-                        base = pend_lo;
-                        pend_lo += (unsigned long long)got;
+                    if (pend_lo < pend_hi) {
+                        const unsigned long long lim =
+                            (cascade && pend_hi > n0) ? max(stored_rows(P), n0) : n0;
+                        if (pend_lo < lim) {
+                            got = (int)min((unsigned long long)want, min(pend_hi, lim) - pend_lo);
+                            base = pend_lo;
+                            pend_lo += (unsigned long long)got;
+                        }
                     }
                 }
                 got = __shfl_sync(kAll, got, 0);
@@ -865,8 +879,8 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
                     waiting = true;
                 }
             }
-            // no free lane left wanting a row: the warp is not starved
-            drained = free_lanes != 0 && got < __popc(free_lanes);
+            // the warp is starved when a claim left free lanes without a row
+            drained = claim && got < __popc(free_lanes);
             if (waiting) {
                 const uint8_t ty = *reinterpret_cast<volatile uint8_t*>(P.type + i);
                 if (ty != kNotReady) {
