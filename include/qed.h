@@ -113,7 +113,10 @@ typedef struct {
     uint64_t children;         /* rows appended                                 */
     uint64_t guard_hits;       /* plans raised by the validity guard            */
     uint64_t plans;            /* sub-step plans made (1 + one per event)       */
-    uint64_t candidates;       /* sub-steps whose acceptance function was evaluated */
+    uint64_t candidates;       /* sub-steps whose draw passed the squeeze test, so
+                                  that the acceptance function decides (a work
+                                  counter: the warp mode tests whole 64-sub-step
+                                  windows, also past an event)                  */
     uint32_t max_N;            /* largest planned sub-step count                */
     int32_t status;            /* qed_status of the step                        */
     int64_t required_capacity; /* rows needed when status == QED_ERR_CAPACITY   */
