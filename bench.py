@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 N_PARTICLES = 1 << 24
 SWEEP_N = 1 << 28
+SEED_UNIFORM = 20081046 + 1
 SEED_CLUMPED = 20081046 + 3
 SEED_SWEEP = 20081046 + 2
 SEED_CASCADE = 20081046 + 4
@@ -570,11 +571,11 @@ def run_uniform(dev, args):
     from paper_2008_10468_gb300 import inputs as I
     from paper_2008_10468_gb300 import qed
     n = 100_000
-    arr = I.uniform_field_electrons(n, SEED_CLUMPED - 2)
-    cap = 2 * n
-    pristine = qed.ParticleStore.from_numpy(arr, capacity=cap, device=dev)
+    arr = I.uniform_field_electrons(n, SEED_UNIFORM)
+    cap = 16 * n   # about 9.5 photons per electron and step
+    pristine = qed.ParticleStore.from_numpy(arr, capacity=n, device=dev)
     store = qed.ParticleStore(cap, device=dev)
-    ctx = qed.Context(seed=SEED_CLUMPED - 2, process_mask=1, cascade=False)
+    ctx = qed.Context(seed=SEED_UNIFORM, process_mask=1, cascade=False)
     stream = torch.cuda.current_stream()
 
     def restore():
@@ -596,6 +597,8 @@ def run_uniform(dev, args):
         st = ctx.event_step(store, 600 + k)
         e1.record(stream)
         torch.cuda.synchronize()
+        if st["status"] != 0:
+            raise SystemExit("uniform-field step failed with status %d" % st["status"])
         total += e0.elapsed_time(e1)
         subs += st["substeps"]
     return {"workload": "uniform-field electrons: 1e5 e-, gamma log-uniform 1e2..1e4, chi "
@@ -785,6 +788,7 @@ def run_sampler(arr, pristine, store, cap, n, dev, args, restore, plain_value):
     ectx.sampler_evaluate()
     ectx.sampler_process(qed.PROC_EMISSION)
     event = timed(ectx)
+    uniform = run_sampler_uniform(params, dev)
     lo = int((np.log10(0.3) + 2) * 16)
     return {"train_samples": 1 << 26, "train_s": train_s, "final_mse": loss,
             "bins_usable": int(usable.sum()), "bins": int(len(err)),
@@ -798,11 +802,65 @@ def run_sampler(arr, pristine, store, cap, n, dev, args, restore, plain_value):
             "per_sub_step": per_sub_step,
             "event_driven": event,
             "event_driven_emission_only": event_emission_only,
+            "uniform_field_1e6": uniform,
             "note": "event-driven: about 1e9 per-sub-step draws become ~6e6 waiting-time "
                     "draws, but each generation of the cascade ends with its longest chain "
                     "of events (up to ~100 per particle), one network evaluation per event "
                     "on the critical path (a 16-row tensor-core tile, ~4 us on a nearly "
                     "idle warp)"}
+
+
+def run_sampler_uniform(params, dev, n=1_000_000, steps=10):
+    """The event-driven sampler against rejection where the generator is
+    throughput-bound: the uniform-field electrons (the plain generator's
+    recipe) at 1e6 rows, emission only, one step, no cascade."""
+    import torch
+    from paper_2008_10468_gb300 import inputs as I
+    from paper_2008_10468_gb300 import qed
+    arr = I.uniform_field_electrons(n, SEED_UNIFORM)
+    pristine = qed.ParticleStore.from_numpy(arr, capacity=n, device=dev)
+    store = qed.ParticleStore(40 * n, device=dev)
+
+    def restore():
+        for k in qed.FLOAT_FIELDS + ("id", "type"):
+            getattr(store, k)[:n].copy_(getattr(pristine, k)[:n])
+        store.type[n:].fill_(qed.REMOVED)
+        store.count.fill_(n)
+
+    out = {"workload": "uniform-field electrons, 1e6 rows (the plain generator's recipe), "
+                       "emission only, one step"}
+    stream = torch.cuda.current_stream()
+    for mode, name in ((False, "rejection"), ("event", "event_driven")):
+        ctx = qed.Context(seed=SEED_UNIFORM, process_mask=1, cascade=False, sampler=mode,
+                          sampler_max_err=1e-3)
+        if mode:
+            ctx.sampler_load(params)
+            ctx.sampler_evaluate()
+        for w in range(3):
+            restore()
+            ctx.event_step(store, 100 + w)
+        ms, subs, em, se = 0.0, 0, 0, 0
+        for k in range(steps):
+            restore()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = ctx.event_step(store, 200 + k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if st["status"] != 0:
+                raise SystemExit("uniform-field sampler step failed with status %d" % st["status"])
+            ms += e0.elapsed_time(e1)
+            subs += st["substeps"]
+            em += st["emissions"]
+            se += st["sampler_events"]
+        out[name] = {"ms_per_step": ms / steps, "substeps_per_s": subs / (ms / 1e3),
+                     "emissions_per_step": em / steps,
+                     "emissions_from_sampler": se / max(em, 1)}
+    out["speedup_vs_rejection"] = (out["rejection"]["ms_per_step"]
+                                   / out["event_driven"]["ms_per_step"])
+    return out
 
 
 def run_e2e(ctx, arr, cap, dev, args):
