@@ -770,6 +770,14 @@ constexpr int kPushClaimBatch = 8;  // free lanes before the warp claims rows
 // stored.  Every wait is bounded: a warp that sees no progress anywhere
 // (rows stored, rows completed, the beats of long chains) for SP.wait_ns
 // records QED_ERR_TIMEOUT and returns.
+//
+// Divergence control (both forms): a lane that wants a plan (a new row, or
+// after an event) waits until kPushPlanBatch lanes of its warp want one, or
+// until no busy lane is left to step; an accepted event is applied with the
+// lane's next plan; in the persistent form free lanes claim rows only once
+// kPushClaimBatch of them are free (or none is busy).  When the warp finds
+// no row to take and at most kPushGroupMax lanes are busy, it switches to
+// group mode (below).
 constexpr unsigned int kBeatRounds = 1024;   // rounds of a warp between two beats
 template <bool kStream>
 __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParams SP, Scratch S,
