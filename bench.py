@@ -366,7 +366,7 @@ def run_gb300(args):
     sweep = run_sweep(ctx, dev, args, hbm_peak, peak_kind)
 
     # end to end from pinned host buffers through the public API
-    e2e = None if args.no_e2e else run_e2e(ctx, arr, cap, dev, args)
+    e2e = None if args.no_e2e else run_e2e(ctx, arr, cap, dev, args, pg)
 
     # cascade batch: many steps of growing pools in one captured graph
     cascade = None if args.no_cascade else run_cascade(dev, args)
@@ -863,7 +863,7 @@ def run_sampler_uniform(params, dev, n=1_000_000, steps=10):
     return out
 
 
-def run_e2e(ctx, arr, cap, dev, args):
+def run_e2e(ctx, arr, cap, dev, args, pg=None):
     """Same metric through the API with host buffers: qed_event_step_host on a
     page-locked host store, which copies the population to the device, steps
     it and copies back what the step changed (momenta and types of the
@@ -901,9 +901,13 @@ def run_e2e(ctx, arr, cap, dev, args):
         subs += st["substeps"]
         h2d += 49 * n
         d2h += 13 * m + 36 * (m - n)
-    return {"value": subs / (total / 1e3), "unit": UNIT,
-            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps,
-            "ms_per_step": total / steps, "api": "qed_event_step_host (page-locked host store)"}
+    # the whole job: every rank's sub-steps and bytes over the slowest rank's time
+    value, t_max = job_rate(pg, subs, total, dev)
+    h2d = allreduce_sum(pg, h2d, dev)
+    d2h = allreduce_sum(pg, d2h, dev)
+    return {"value": value, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d) // steps, "d2h_bytes_per_step": int(d2h) // steps,
+            "ms_per_step": t_max / steps, "api": "qed_event_step_host (page-locked host store)"}
 
 
 # --------------------------------------------------------------------------
