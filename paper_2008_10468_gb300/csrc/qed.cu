@@ -1753,7 +1753,10 @@ __device__ __forceinline__ void push_long(const Scratch& S, DevCtl* ctl, unsigne
 }
 
 template <int kSampler>
-__global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_step(DevParticles P, StepParams SP,
+// Two resident blocks per SM (128 registers, no spills): the tail pass is
+// bound by latency, not by the number of warps (three blocks at 80 registers
+// spilled 434 bytes a thread and measured 0.8% slower per step).
+__global__ void __launch_bounds__(kLaneThreads, 2) k_step(DevParticles P, StepParams SP,
                                                             Scratch S, DevCtl* ctl) {
     const uint32_t step = step_index(SP);
     __shared__ SharedTables sm;
