@@ -2128,8 +2128,9 @@ __global__ void k_step_init(DevCtl* ctl, long long* count, long long capacity, i
 // sub-step, 2: event-driven), each its own instantiation so that a mode's
 // code carries no other mode's path.
 const void* hot_kernel(int mode) {
-    return mode == 2 ? (const void*)k_hot_lanes<2>
-                     : mode ? (const void*)k_hot_lanes<1> : (const void*)k_hot_lanes<0>;
+    // sampler mode 2 runs its network in k_samp: the hot pass of its
+    // generations is rejection's (loop_hot_mode), so there is no k_hot_lanes<2>
+    return mode == 1 ? (const void*)k_hot_lanes<1> : (const void*)k_hot_lanes<0>;
 }
 const void* step_kernel(int mode) {
     return mode == 2 ? (const void*)k_step<2>
@@ -2782,12 +2783,11 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<0>, kLaneThreads, 0);
         ctx->hot_blocks = ctx->hot_blocks_max = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
-        for (int m = 1; m <= 2; ++m) {
-            cudaFuncSetAttribute(hot_kernel(m), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kNetSmemBytes);
+        cudaFuncSetAttribute(hot_kernel(1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kNetSmemBytes);
+        for (int m = 1; m <= 2; ++m)
             cudaFuncSetAttribute(step_kernel(m), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kNetSmemBytes);
-        }
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<1>, kLaneThreads,
                                                       kNetSmemBytes);
         ctx->net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
