@@ -1545,8 +1545,10 @@ __global__ void __launch_bounds__(kLaneThreads) k_samp(DevParticles P, StepParam
 // take the next queue entries (one atomic per warp).  Persistent: the grid is
 // the resident block count, and a warp leaves when the queue is empty and its
 // lanes are idle.
-// kSampler: the sampler's particles (e+- in a usable bin of its chi range)
-// are queued for the warp mode, which evaluates the network (warp_item).
+// kSampler = 1 (per-sub-step sampler): the sampler's particles (e+- in a
+// usable bin of its chi range) are queued for the warp mode, which evaluates
+// the network (warp_item).  Sampler mode 2 steps its particles in k_samp and
+// runs this kernel's rejection form (kSampler = 0) for the others.
 constexpr uint32_t kWindow = 64;
 
 template <int kSampler>
@@ -1556,19 +1558,13 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
     __shared__ SharedTables sm;
     __shared__ uint32_t first_acc[kLaneThreads];
     extern __shared__ __align__(16) unsigned char dyn_smem[];
+    // sampler mode 2 runs its network in k_samp; its generations use k_hot_lanes<0>
+    static_assert(kSampler == 0 || kSampler == 1, "hot pass: rejection or sampler mode 1");
     stage_tables(sm);
     if (kSampler == 1)
         stage_sampler(*reinterpret_cast<SamplerSmem*>(dyn_smem),
                       reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot, SP.net_rows,
                       SP.net_bins);
-    else if (kSampler == 2) {
-        stage_sampler_mma(*reinterpret_cast<SamplerMma*>(dyn_smem),
-                          reinterpret_cast<const __nv_bfloat16*>(SP.net_w), SP.net_wtot,
-                          SP.net_rows, SP.net_bins);
-        if (SP.pnet_bins)
-            stage_sampler_mma(pair_mma(dyn_smem), reinterpret_cast<const __nv_bfloat16*>(SP.pnet_w),
-                              SP.pnet_wtot, SP.net_rows, SP.pnet_bins);
-    }
     __syncthreads();
     if (ctl->status == (int)QED_ERR_TIMEOUT) return;
     constexpr unsigned int kAll = 0xffffffffu;
