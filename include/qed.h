@@ -224,6 +224,19 @@ qed_status qed_plan_cells(qed_ctx* ctx, const qed_particles* p, int64_t n, const
 qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
                           qed_step_stats* out);
 
+/* qed_event_step with one sub-step per cell for the first plans (Algorithms 1
+ * and 2 start by fixing the sub-step of the particle's cell): the counts of
+ * qed_plan_cells are taken over the rows in use at the start of the step
+ * (cell: device array with a cell index for each of them; rows with
+ * cell[i] >= ncells keep their own count), and each of those rows makes its
+ * first plan with its cell's count when that is larger than its own.
+ * Re-plans after events, and children, plan per particle.  The context owns
+ * the ncells counts (allocated on first use).  Errors: as qed_event_step;
+ * QED_ERR_ARG for a NULL cell, ncells outside [1, 2^32), or a learned
+ * sampler in cfg.sampler_mode (the two do not combine). */
+qed_status qed_event_step_cells(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                                const uint32_t* cell, int64_t ncells, qed_step_stats* out);
+
 /* qed_event_step on a store in host memory (the same step: Sec. 2,
  * Algorithms 1 and 2).  The context keeps a device copy of the store's
  * layout (capacity rows; allocated on first use and when the capacity

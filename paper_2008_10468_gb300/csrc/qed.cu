@@ -625,6 +625,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
     const int first_pass = ctl->first_pass;
     const long long begin = first_pass ? 0 : ctl->pass_begin;
     const long long end = ctl->pass_end;
+    const long long n_init = ctl->n_init;
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -664,6 +665,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                 need_plan = false;
                 pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex, Ey, Ez,
                                    Bx, By, Bz, t_rem, &chi, &eps);
+                apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, n_init, s, t_rem, eps);
                 if (!(eps > 0.0f)) {
                     active = false;
                 } else {
@@ -979,20 +981,9 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
             pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, F.Ex, F.Ey,
                                F.Ez, F.Bx, F.By, F.Bz, t_rem, &chi, &eps);
             if (!(eps > 0.0f)) return true;
-            if (SP.N_cell && s == 0u && i < n_init) {
-                // per-cell counts: an initial row's first plan takes its
-                // cell's count when that is larger (the cell's sub-step)
-                const uint32_t c = SP.cell[i];
-                const uint32_t Nc = (long long)c < SP.ncells ? SP.N_cell[c] : 0u;
-                if (Nc > pl.N) {
-                    pl.N = Nc;
-                    pl.h = time_div(t_rem, Nc);
-                    pl.c_h = PC.K * pl.h.hi * __fdividef(1.0f, eps);
-                    const float b23 = pl.b > 0.0f ? exp2f(__log2f(pl.b) * (2.0f / 3.0f)) : 0.0f;
-                    pl.T = squeeze_threshold(
-                        squeeze_bound(sm.sqz_e, sm.sqz_p, photon, pl.b, pl.c_h, b23));
-                }
-            }
+            // per-cell counts: an initial row's first plan takes its cell's
+            // count when that is larger (the cell's sub-step)
+            apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, n_init, s, t_rem, eps);
             stats.plans++;
             stats.guard += pl.guard ? 1 : 0;
             stats.max_N = max(stats.max_N, pl.N);
@@ -1208,10 +1199,12 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
     ftime t_rem = it.t_rem;
     bool removed = false, changed = false;
     unsigned int rounds = 0;   // publish (persistent pass): beats of a long chain
+    const long long n_init = SP.N_cell ? ctl->n_init : 0;
     while (time_positive(t_rem)) {
         float eps, chi;
-        const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex,
-                                      Ey, Ez, Bx, By, Bz, t_rem, &chi, &eps);
+        Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex, Ey, Ez,
+                                Bx, By, Bz, t_rem, &chi, &eps);
+        apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, n_init, s, t_rem, eps);
         if (!(eps > 0.0f)) break;
         if (lane == 0) {
             stats.plans++;
@@ -1633,6 +1626,9 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
         if (planned) {
             pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex, Ey, Ez,
                                Bx, By, Bz, t_rem, &chi, &eps);
+            if (SP.N_cell)
+                apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, ctl->n_init, s, t_rem,
+                                 eps);
             if (eps > 0.0f) {
                 active = true;
                 k_done = 0;
@@ -1940,6 +1936,9 @@ __global__ void __launch_bounds__(kLaneThreads, 2) k_step(DevParticles P, StepPa
                                        fld[0][threadIdx.x], fld[1][threadIdx.x],
                                        fld[2][threadIdx.x], fld[3][threadIdx.x],
                                        fld[4][threadIdx.x], fld[5][threadIdx.x], t_rem, &chi, &eps);
+                    if (SP.N_cell)
+                        apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, ctl->n_init, s,
+                                         t_rem, eps);
                     work = eps > 0.0f;
                 }
                 if (!work) {
@@ -2938,13 +2937,38 @@ qed_status qed_set_event_log(qed_ctx* ctx, qed_event_record* records, int64_t ca
 }  // extern "C"
 static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& D, StepParams SP,
                                  const Scratch& S, uint32_t step);
-extern "C" {
+// Per-cell counts (reading of Algorithms 1 and 2: one sub-step per cell) over
+// the rows in use, before the step changes them: N_cell[c] = the largest
+// count of cell c's rows (k_plan), then the step's parameters point at them.
+static qed_status cell_counts(qed_ctx* ctx, const DevParticles& D, StepParams* SP,
+                              const uint32_t* cell, int64_t ncells) {
+    if (ncells > ctx->ncell_cap) {
+        if (ctx->d_Ncell) cudaFree(ctx->d_Ncell);
+        ctx->d_Ncell = nullptr;
+        ctx->ncell_cap = 0;
+        QED_CUDA(ctx, cudaMalloc(&ctx->d_Ncell, sizeof(unsigned int) * (size_t)ncells));
+        ctx->ncell_cap = ncells;
+    }
+    QED_CUDA(ctx, cudaMemsetAsync(ctx->d_Ncell, 0, sizeof(unsigned int) * (size_t)ncells,
+                                  ctx->stream));
+    long long blocks = (D.capacity + kColdThreads - 1) / kColdThreads;
+    if (blocks > ctx->cold_blocks) blocks = ctx->cold_blocks;
+    {
+        LaunchScope ls(ctx, QED_KERNEL_PLAN);
+        k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(D, *SP, D.capacity, nullptr,
+                                                              nullptr, cell, (long long)ncells,
+                                                              ctx->d_Ncell, D.count);
+    }
+    QED_CUDA(ctx, cudaGetLastError());
+    SP->cell = cell;
+    SP->N_cell = ctx->d_Ncell;
+    SP->ncells = ncells;
+    return QED_OK;
+}
 
-qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
-                          qed_step_stats* out) {
-    if (!ctx) return QED_ERR_ARG;
-    if (!particles_ok(p) || step_index > 0xffffffffull)
-        return set_err(ctx, QED_ERR_ARG, "qed_event_step: bad argument");
+// The event step, with per-cell first-plan counts when cell != NULL.
+static qed_status plain_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                             qed_step_stats* out, const uint32_t* cell, int64_t ncells) {
     qed_status st = ensure_scratch(ctx, p->capacity);
     if (st != QED_OK) return st;
     StepParams SP = make_params(ctx->cfg, step_index);
@@ -2953,10 +2977,17 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
     SP.wait_ns = ctx->wait_ns;
     st = sampler_params(ctx, &SP);
     if (st != QED_OK) return st;
+    if (cell && SP.sampler)
+        return set_err(ctx, QED_ERR_ARG,
+                       "qed_event_step_cells: per-cell counts do not combine with the sampler");
     const DevParticles D = to_dev(p);
     Scratch S = make_scratch(ctx);
     st = ensure_samp(ctx, p->capacity, SP, &S);
     if (st != QED_OK) return st;
+    if (cell && ncells > 0) {
+        st = cell_counts(ctx, D, &SP, cell, ncells);
+        if (st != QED_OK) return st;
+    }
     const bool cascade = cascade_enabled(ctx->cfg);
     if (cascade && !ctx->prof_on) {
         // the generations run in a device-side loop: no host round trip per
@@ -3038,6 +3069,25 @@ qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_in
     return QED_OK;
 }
 
+extern "C" {
+
+qed_status qed_event_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                          qed_step_stats* out) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!particles_ok(p) || step_index > 0xffffffffull)
+        return set_err(ctx, QED_ERR_ARG, "qed_event_step: bad argument");
+    return plain_step(ctx, p, step_index, out, nullptr, 0);
+}
+
+qed_status qed_event_step_cells(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
+                                const uint32_t* cell, int64_t ncells, qed_step_stats* out) {
+    if (!ctx) return QED_ERR_ARG;
+    if (!particles_ok(p) || step_index > 0xffffffffull || !cell || ncells <= 0 ||
+        ncells > 0xffffffffll)
+        return set_err(ctx, QED_ERR_ARG, "qed_event_step_cells: bad argument");
+    return plain_step(ctx, p, step_index, out, cell, ncells);
+}
+
 }  // extern "C"
 static qed_status push_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_index,
                             qed_step_stats* out, const uint32_t* cell, int64_t ncells) {
@@ -3049,28 +3099,8 @@ static qed_status push_step(qed_ctx* ctx, const qed_particles* p, uint64_t step_
     const Scratch S = make_scratch(ctx);
     const bool cascade = cascade_enabled(ctx->cfg);
     if (cell && ncells > 0) {
-        // the cells' counts over the rows in use, before the step changes them
-        if (ncells > ctx->ncell_cap) {
-            if (ctx->d_Ncell) cudaFree(ctx->d_Ncell);
-            ctx->d_Ncell = nullptr;
-            ctx->ncell_cap = 0;
-            QED_CUDA(ctx, cudaMalloc(&ctx->d_Ncell, sizeof(unsigned int) * (size_t)ncells));
-            ctx->ncell_cap = ncells;
-        }
-        QED_CUDA(ctx, cudaMemsetAsync(ctx->d_Ncell, 0, sizeof(unsigned int) * (size_t)ncells,
-                                      ctx->stream));
-        long long blocks = (p->capacity + kColdThreads - 1) / kColdThreads;
-        if (blocks > ctx->cold_blocks) blocks = ctx->cold_blocks;
-        {
-            LaunchScope ls(ctx, QED_KERNEL_PLAN);
-            k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(
-                D, SP, D.capacity, nullptr, nullptr, cell, (long long)ncells, ctx->d_Ncell,
-                D.count);
-        }
-        QED_CUDA(ctx, cudaGetLastError());
-        SP.cell = cell;
-        SP.N_cell = ctx->d_Ncell;
-        SP.ncells = ncells;
+        st = cell_counts(ctx, D, &SP, cell, ncells);
+        if (st != QED_OK) return st;
     }
     {
         LaunchScope ls(ctx, QED_KERNEL_CONTROL);
@@ -3533,6 +3563,7 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
     put(SPin.net_bins); putp(SPin.net_w); putp(SPin.net_wtot); put(SPin.process_mask);
     put(SPin.pnet_bins); putp(SPin.pnet_w); putp(SPin.pnet_wtot);
     put((uint64_t)SPin.recoil); put((uint64_t)SPin.cascade); put(SPin.wait_ns);
+    putp(SPin.cell); putp(SPin.N_cell); put((uint64_t)SPin.ncells);
     { uint64_t b; memcpy(&b, &SPin.lambda_m, 8); put(b); }
     put((uint64_t)ctx->cold_blocks); put((uint64_t)ctx->hot_blocks); put((uint64_t)ctx->net_blocks);
     put((uint64_t)ctx->cfg.max_passes);

@@ -582,6 +582,33 @@ __device__ __noinline__ Plan plan_slow(PlanConst P, const float* __restrict__ sq
     return pl;
 }
 
+// One sub-step per cell (Algorithms 1 and 2 start by fixing the cell's
+// sub-step): with per-cell counts, the first plan (s = 0) of an initial row
+// (i < n_init) takes its cell's count N_cell when that is larger than its own,
+// i.e. the sub-step T / N_cell; h, c_h and the squeeze threshold follow.  Out
+// of line: the event kernels carry no registers for it.
+__device__ __noinline__ Plan cell_count_plan(Plan pl, const float* __restrict__ sqz_e,
+                                             const float* __restrict__ sqz_p, float K,
+                                             bool photon, uint32_t Nc, ftime T, float eps) {
+    pl.N = Nc;
+    pl.h = time_div(T, Nc);
+    pl.c_h = K * pl.h.hi * __fdividef(1.0f, eps);
+    const float b23 = pl.b > 0.0f ? exp2f(__log2f(pl.b) * (2.0f / 3.0f)) : 0.0f;
+    pl.T = squeeze_threshold(squeeze_bound(sqz_e, sqz_p, photon, pl.b, pl.c_h, b23));
+    return pl;
+}
+
+__device__ __forceinline__ void apply_cell_count(const StepParams& SP, Plan& pl,
+                                                 const float* __restrict__ sqz_e,
+                                                 const float* __restrict__ sqz_p, bool photon,
+                                                 long long i, long long n_init, uint32_t s,
+                                                 ftime T, float eps) {
+    if (!SP.N_cell || s != 0u || i >= n_init || !(eps > 0.0f)) return;
+    const uint32_t c = SP.cell[i];
+    const uint32_t Nc = (long long)c < SP.ncells ? SP.N_cell[c] : 0u;
+    if (Nc > pl.N) pl = cell_count_plan(pl, sqz_e, sqz_p, SP.K, photon, Nc, T, eps);
+}
+
 // chi and the plan of a particle: binary32 chi when it is well conditioned and
 // the plan is safe, otherwise chi in float-float (and the plan again).
 __device__ __forceinline__ Plan plan_particle(const StepParams& SP, const float* __restrict__ sqz_e,

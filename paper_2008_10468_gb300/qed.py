@@ -94,6 +94,9 @@ def lib():
         L.qed_event_step_push.restype = st
         L.qed_event_step_host.argtypes = [vp, C.POINTER(HostParticles), u64, C.POINTER(StepStats)]
         L.qed_event_step_host.restype = st
+        L.qed_event_step_cells.argtypes = [vp, C.POINTER(Particles), u64, vp, i64,
+                                           C.POINTER(StepStats)]
+        L.qed_event_step_cells.restype = st
         L.qed_plan_cells.argtypes = [vp, C.POINTER(Particles), i64, vp, i64, vp]
         L.qed_plan_cells.restype = st
         L.qed_event_step_push_cells.argtypes = [vp, C.POINTER(Particles), u64, vp, i64,
@@ -408,6 +411,18 @@ class Context:
         if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_TIMEOUT):   # step outcomes
             self._check(st)
         hstore.count = int(p.count)
+        return stats_dict(s)
+
+    def event_step_cells(self, store, step, cell, ncells):
+        """The event step with one sub-step per cell for the first plans
+        (qed_event_step_cells; cell: int32 CUDA tensor of a cell index per row
+        in use); returns the statistics dict."""
+        p = store.struct()
+        s = StepStats()
+        st = lib().qed_event_step_cells(self._h, C.byref(p), int(step), _ptr(cell), int(ncells),
+                                        C.byref(s))
+        if st not in (QED_OK, QED_ERR_CAPACITY, QED_ERR_TIMEOUT):   # step outcomes
+            self._check(st)
         return stats_dict(s)
 
     def event_step_push_cells(self, store, step, cell, ncells):
