@@ -614,6 +614,7 @@ __device__ __forceinline__ float draw_x(uint64_t id, uint32_t step, uint32_t s,
 // takes its earliest accepted sub-step, the decision of testing its
 // sub-steps in order and stopping at the first acceptance.  Lanes with an
 // event apply it, re-plan the remaining time and join the next round.
+template <bool kCells = false>
 __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevParticles P, StepParams SP, Scratch S,
                                                        DevCtl* ctl) {
     const uint32_t step = step_index(SP);
@@ -625,7 +626,7 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
     const int first_pass = ctl->first_pass;
     const long long begin = first_pass ? 0 : ctl->pass_begin;
     const long long end = ctl->pass_end;
-    const long long n_init = ctl->n_init;
+    const long long n_init = kCells ? ctl->n_init : 0;
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -665,7 +666,8 @@ __global__ void __launch_bounds__(kColdThreads, QED_COLD_MIN_BLOCKS) k_cold(DevP
                 need_plan = false;
                 pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex, Ey, Ez,
                                    Bx, By, Bz, t_rem, &chi, &eps);
-                apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, n_init, s, t_rem, eps);
+                if (kCells)
+                    apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, n_init, s, t_rem, eps);
                 if (!(eps > 0.0f)) {
                     active = false;
                 } else {
@@ -1179,7 +1181,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_push(DevParticles P, StepParam
 // kSampler: an e+- in a usable bin of the sampler's chi range decides events
 // from the tabulated total probability c_h W(b) and takes the energy fraction
 // from the network at the event's uniform, evaluated by the warp (FP32).
-template <int kSampler>
+template <int kSampler, bool kCells = false>
 __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& S,
                                           const StepParams& SP, DevCtl* ctl,
                                           const SharedTables& sm, unsigned char* net_smem,
@@ -1199,12 +1201,12 @@ __device__ __forceinline__ void warp_item(const DevParticles& P, const Scratch& 
     ftime t_rem = it.t_rem;
     bool removed = false, changed = false;
     unsigned int rounds = 0;   // publish (persistent pass): beats of a long chain
-    const long long n_init = SP.N_cell ? ctl->n_init : 0;
+    const long long n_init = kCells ? ctl->n_init : 0;
     while (time_positive(t_rem)) {
         float eps, chi;
         Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex, Ey, Ez,
                                 Bx, By, Bz, t_rem, &chi, &eps);
-        apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, n_init, s, t_rem, eps);
+        if (kCells) apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, n_init, s, t_rem, eps);
         if (!(eps > 0.0f)) break;
         if (lane == 0) {
             stats.plans++;
@@ -1544,7 +1546,7 @@ __global__ void __launch_bounds__(kLaneThreads) k_samp(DevParticles P, StepParam
 // runs this kernel's rejection form (kSampler = 0) for the others.
 constexpr uint32_t kWindow = 64;
 
-template <int kSampler>
+template <int kSampler, bool kCells = false>
 __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lanes(DevParticles P, StepParams SP,
                                                                  Scratch S, DevCtl* ctl) {
     const uint32_t step = step_index(SP);
@@ -1575,7 +1577,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
             if (lane == 0) q = atomicAdd(&ctl->hot_head, 1u);
             q = __shfl_sync(kAll, q, 0);
             if (q >= long_tail) break;
-            warp_item<kSampler>(P, S, SP, ctl, sm, dyn_smem, S.hot[q], step, k0, k1, wstats, wcand,
+            warp_item<kSampler, kCells>(P, S, SP, ctl, sm, dyn_smem, S.hot[q], step, k0, k1, wstats, wcand,
                                 false);
         }
         if (lane == 0) stats = wstats;
@@ -1626,7 +1628,7 @@ __global__ void __launch_bounds__(kLaneThreads, QED_LANES_MIN_BLOCKS) k_hot_lane
         if (planned) {
             pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, st.px, st.py, st.pz, Ex, Ey, Ez,
                                Bx, By, Bz, t_rem, &chi, &eps);
-            if (SP.N_cell)
+            if (kCells)
                 apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, ctl->n_init, s, t_rem,
                                  eps);
             if (eps > 0.0f) {
@@ -1744,7 +1746,7 @@ __device__ __forceinline__ void push_long(const Scratch& S, DevCtl* ctl, unsigne
     *reinterpret_cast<volatile uint32_t*>(&e->idx) = (uint32_t)i;
 }
 
-template <int kSampler>
+template <int kSampler, bool kCells = false>
 // Two resident blocks per SM (128 registers, no spills): the tail pass is
 // bound by latency, not by the number of warps (three blocks at 80 registers
 // spilled 434 bytes a thread and measured 0.8% slower per step).
@@ -1841,7 +1843,7 @@ __global__ void __launch_bounds__(kLaneThreads, 2) k_step(DevParticles P, StepPa
                 it.s = __shfl_sync(kAll, it.s, 0);
                 it.t_rem.hi = __shfl_sync(kAll, it.t_rem.hi, 0);
                 it.t_rem.lo = __shfl_sync(kAll, it.t_rem.lo, 0);
-                warp_item<kSampler>(P, S, SP, ctl, sm, dyn_smem, it, step, k0, k1, stats, stats.cand,
+                warp_item<kSampler, kCells>(P, S, SP, ctl, sm, dyn_smem, it, step, k0, k1, stats, stats.cand,
                                     true);
                 if (lane == 0) ++done;
                 idle = 0;
@@ -1936,7 +1938,7 @@ __global__ void __launch_bounds__(kLaneThreads, 2) k_step(DevParticles P, StepPa
                                        fld[0][threadIdx.x], fld[1][threadIdx.x],
                                        fld[2][threadIdx.x], fld[3][threadIdx.x],
                                        fld[4][threadIdx.x], fld[5][threadIdx.x], t_rem, &chi, &eps);
-                    if (SP.N_cell)
+                    if (kCells)
                         apply_cell_count(SP, pl, sm.sqz_e, sm.sqz_p, photon, i, ctl->n_init, s,
                                          t_rem, eps);
                     work = eps > 0.0f;
@@ -2122,14 +2124,22 @@ __global__ void k_step_init(DevCtl* ctl, long long* count, long long capacity, i
 // The hot-pass and tail-pass kernels for a sampler mode (0: off, 1: per
 // sub-step, 2: event-driven), each its own instantiation so that a mode's
 // code carries no other mode's path.
-const void* hot_kernel(int mode) {
+// cells: the step takes per-cell counts for the first plans (only without a
+// learned sampler); its kernels are separate instantiations, so that the
+// plain step carries none of that code.
+const void* cold_kernel(bool cells) {
+    return cells ? (const void*)k_cold<true> : (const void*)k_cold<false>;
+}
+const void* hot_kernel(int mode, bool cells = false) {
     // sampler mode 2 runs its network in k_samp: the hot pass of its
     // generations is rejection's (loop_hot_mode), so there is no k_hot_lanes<2>
-    return mode == 1 ? (const void*)k_hot_lanes<1> : (const void*)k_hot_lanes<0>;
+    return mode == 1 ? (const void*)k_hot_lanes<1>
+                     : cells ? (const void*)k_hot_lanes<0, true> : (const void*)k_hot_lanes<0>;
 }
-const void* step_kernel(int mode) {
+const void* step_kernel(int mode, bool cells = false) {
     return mode == 2 ? (const void*)k_step<2>
-                     : mode ? (const void*)k_step<1> : (const void*)k_step<0>;
+                     : mode ? (const void*)k_step<1>
+                            : cells ? (const void*)k_step<0, true> : (const void*)k_step<0>;
 }
 
 // tail_rows > 0: a next generation of fewer rows goes to the tail pass
@@ -2772,7 +2782,7 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
     if (st == QED_OK) st = cuda_check(ctx, cudaMemset(ctx->d_ctl, 0, sizeof(DevCtl)), "memset");
     if (st == QED_OK) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cold, kColdThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cold<false>, kColdThreads, 0);
         ctx->cold_blocks = ctx->cold_blocks_max = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hot_lanes<0>, kLaneThreads, 0);
@@ -3004,7 +3014,8 @@ static qed_status plain_step(qed_ctx* ctx, const qed_particles* p, uint64_t step
     for (int pass = 0; pass < ctx->cfg.max_passes; ++pass) {
         {
             LaunchScope ls(ctx, QED_KERNEL_COLD);
-            k_cold<<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+            if (SP.N_cell) k_cold<true><<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+            else k_cold<false><<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
         }
         if (SP.sampler == 2) {
             LaunchScope ls(ctx, QED_KERNEL_SAMPLER);
@@ -3019,7 +3030,7 @@ static qed_status plain_step(qed_ctx* ctx, const qed_particles* p, uint64_t step
             DevCtl* c = ctx->d_ctl;
             void* a[] = {&d, &sp, &sc, &c};
             const int hm = loop_hot_mode(SP);
-            QED_CUDA(ctx, cudaLaunchKernel(hot_kernel(hm),
+            QED_CUDA(ctx, cudaLaunchKernel(hot_kernel(hm, SP.N_cell != nullptr),
                                            dim3(hm ? ctx->net_blocks : ctx->hot_blocks),
                                            dim3(kLaneThreads), a, hm ? kNetSmemBytes : 0,
                                            ctx->stream));
@@ -3046,7 +3057,8 @@ static qed_status plain_step(qed_ctx* ctx, const qed_particles* p, uint64_t step
     }
     {
         LaunchScope ls(ctx, QED_KERNEL_COLD);
-        k_cold<<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+        if (SP.N_cell) k_cold<true><<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+            else k_cold<false><<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
     }
     {
         LaunchScope ls(ctx, QED_KERNEL_HOT);
@@ -3055,7 +3067,7 @@ static qed_status plain_step(qed_ctx* ctx, const qed_particles* p, uint64_t step
         Scratch sc = S;
         DevCtl* c = ctx->d_ctl;
         void* a[] = {&d, &sp, &sc, &c};
-        QED_CUDA(ctx, cudaLaunchKernel(step_kernel(SP.sampler),
+        QED_CUDA(ctx, cudaLaunchKernel(step_kernel(SP.sampler, SP.N_cell != nullptr),
                                        dim3(SP.sampler ? ctx->step_net_blocks : ctx->step_blocks),
                                        dim3(kLaneThreads), a,
                                        SP.sampler ? kNetSmemBytes : 0, ctx->stream));
@@ -3339,12 +3351,12 @@ qed_status add_tail_nodes(qed_ctx* ctx, cudaGraph_t g, cudaGraphNode_t dep, cons
     }
     if (st == QED_OK) {
         void* a[] = {&D, &SP, &S, &ctl};
-        st = add_kernel(ctx, g, &tc, (const void*)k_cold, dim3(ctx->cold_blocks),
+        st = add_kernel(ctx, g, &tc, cold_kernel(SP.N_cell != nullptr), dim3(ctx->cold_blocks),
                         dim3(kColdThreads), a, &tb, 1);
     }
     if (st == QED_OK) {
         void* a[] = {&D, &SP, &S, &ctl};
-        st = add_kernel(ctx, g, &ts, step_kernel(SP.sampler),
+        st = add_kernel(ctx, g, &ts, step_kernel(SP.sampler, SP.N_cell != nullptr),
                         dim3(SP.sampler ? ctx->step_net_blocks : ctx->step_blocks),
                         dim3(kLaneThreads), a, &tc, 1, SP.sampler ? kNetSmemBytes : 0);
     }
@@ -3443,7 +3455,7 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         int use_handle = 1;
         {
             void* a[] = {&D, &SP, &S, &ctl};
-            st = add_kernel(ctx, body, &bc, (const void*)k_cold, dim3(ctx->cold_blocks),
+            st = add_kernel(ctx, body, &bc, cold_kernel(SP.N_cell != nullptr), dim3(ctx->cold_blocks),
                             dim3(kColdThreads), a, nullptr, 0);
         }
         bs = bc;
@@ -3455,7 +3467,7 @@ qed_status qed_graph_capture(qed_ctx* ctx, const qed_particles* p, uint64_t firs
         if (st == QED_OK) {
             void* a[] = {&D, &SP, &S, &ctl};
             const int hm = loop_hot_mode(SP);
-            st = add_kernel(ctx, body, &bh, hot_kernel(hm),
+            st = add_kernel(ctx, body, &bh, hot_kernel(hm, SP.N_cell != nullptr),
                             dim3(hm ? ctx->net_blocks : ctx->hot_blocks), dim3(kLaneThreads), a,
                             &bs, 1, hm ? kNetSmemBytes : 0);
         }
@@ -3609,7 +3621,7 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
         if (st == QED_OK) {
             cudaGraph_t body = cp.conditional.phGraph_out[0];
             void* a[] = {&D, &SP, &S, &ctl};
-            st = add_kernel(ctx, body, &bc, (const void*)k_cold, dim3(ctx->cold_blocks),
+            st = add_kernel(ctx, body, &bc, cold_kernel(SP.N_cell != nullptr), dim3(ctx->cold_blocks),
                             dim3(kColdThreads), a, nullptr, 0);
             bs = bc;
             if (st == QED_OK && SP.sampler == 2)
@@ -3617,7 +3629,7 @@ static qed_status run_step_graph(qed_ctx* ctx, const DevParticles& Din, StepPara
                                 dim3(kLaneThreads), a, &bc, 1, kMmaSmemBytes);
             const int hm = loop_hot_mode(SP);
             if (st == QED_OK)
-                st = add_kernel(ctx, body, &bh, hot_kernel(hm),
+                st = add_kernel(ctx, body, &bh, hot_kernel(hm, SP.N_cell != nullptr),
                                 dim3(hm ? ctx->net_blocks : ctx->hot_blocks), dim3(kLaneThreads),
                                 a, &bs, 1, hm ? kNetSmemBytes : 0);
             if (st == QED_OK) {
@@ -4270,7 +4282,7 @@ qed_status noalloc_setup(int dev, NoAllocDevice* out) {
         int sms = 0, per_cold = 0, per_hot = 0, per_step = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return QED_ERR_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_cold, k_cold, kColdThreads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_cold, k_cold<false>, kColdThreads, 0) !=
                 cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_hot, k_hot_lanes<0>, kLaneThreads, 0) !=
                 cudaSuccess ||
@@ -4337,7 +4349,7 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     k_step_init<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, 0);
     DevCtl h;
     for (int pass = 0; pass < max_passes; ++pass) {
-        k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
+        k_cold<false><<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
         k_hot_lanes<0><<<nd.hot_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
         k_advance<<<1, 1, 0, s>>>(ctl, D.count, D.capacity, cascade ? 1 : 0, max_passes,
                                   kTailRowsDefault, 0ull, 0);
@@ -4350,7 +4362,7 @@ extern "C" qed_status qed_event_step_noalloc(const qed_config* cfg, const qed_pa
     }
     // the tail pass (its kernels do nothing when the generations ran to the end)
     k_tail_begin<<<nd.sms * 8, 256, 0, s>>>(D, S, ctl);
-    k_cold<<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
+    k_cold<false><<<nd.cold_blocks, kColdThreads, 0, s>>>(D, SP, S, ctl);
     k_step<0><<<nd.step_blocks, kLaneThreads, 0, s>>>(D, SP, S, ctl);
     k_tail_end<<<nd.sms * 8, 256, 0, s>>>(D, S, ctl);
     if (cudaGetLastError() != cudaSuccess) return noalloc_fail(dev, QED_ERR_CUDA);

@@ -585,9 +585,11 @@ __device__ __noinline__ Plan plan_slow(PlanConst P, const float* __restrict__ sq
 // One sub-step per cell (Algorithms 1 and 2 start by fixing the cell's
 // sub-step): with per-cell counts, the first plan (s = 0) of an initial row
 // (i < n_init) takes its cell's count N_cell when that is larger than its own,
-// i.e. the sub-step T / N_cell; h, c_h and the squeeze threshold follow.  Out
-// of line: the event kernels carry no registers for it.
-__device__ __noinline__ Plan cell_count_plan(Plan pl, const float* __restrict__ sqz_e,
+// i.e. the sub-step T / N_cell; h, c_h and the squeeze threshold follow.
+// The plain step's kernels call it only in their cell-count instantiations
+// (kCells): with the test at run time, the kernels' register allocation
+// changed and the step without cell counts took 2-3% longer.
+__device__ __forceinline__ Plan cell_count_plan(Plan pl, const float* __restrict__ sqz_e,
                                              const float* __restrict__ sqz_p, float K,
                                              bool photon, uint32_t Nc, ftime T, float eps) {
     pl.N = Nc;
