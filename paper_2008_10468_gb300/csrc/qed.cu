@@ -3058,7 +3058,7 @@ static qed_status plain_step(qed_ctx* ctx, const qed_particles* p, uint64_t step
     {
         LaunchScope ls(ctx, QED_KERNEL_COLD);
         if (SP.N_cell) k_cold<true><<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
-            else k_cold<false><<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
+        else k_cold<false><<<ctx->cold_blocks, kColdThreads, 0, ctx->stream>>>(D, SP, S, ctx->d_ctl);
     }
     {
         LaunchScope ls(ctx, QED_KERNEL_HOT);
