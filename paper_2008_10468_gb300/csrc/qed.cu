@@ -257,7 +257,9 @@ __global__ void __launch_bounds__(kSweepThreads) k_generate(uint32_t k0, uint32_
 // cell / N_cell (optional): per-cell planning (Algorithm 1 and 2 fix one
 // sub-step per cell): N_cell[c] becomes the largest N of the rows of cell c
 // (N_cell zeroed by the caller; rows whose cell index is >= ncells are left
-// out of it).
+// out of it).  Rows of a cell usually sit together in the store: when the 32
+// rows of a warp share one cell, their largest count goes to it in one
+// atomic.
 __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParams SP, long long n,
                                                        float* chi_out, uint32_t* N_out,
                                                        const uint32_t* __restrict__ cell,
@@ -284,9 +286,19 @@ __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParam
         if (active && eps > 0.0f) N = pl.N;
         if (chi_out) chi_out[i] = chi;
         if (N_out) N_out[i] = N;
-        if (N_cell && N > 0u) {
+        if (N_cell) {
             const uint32_t c = cell[i];
-            if ((long long)c < ncells) atomicMax(N_cell + c, N);
+            const bool in = (long long)c < ncells;
+            const uint32_t key = in ? c : 0xffffffffu;
+            bool one_cell = false;
+            if (__activemask() == 0xffffffffu)
+                one_cell = __all_sync(0xffffffffu, __shfl_sync(0xffffffffu, key, 0) == key);
+            if (one_cell) {
+                const uint32_t m = __reduce_max_sync(0xffffffffu, N);
+                if ((threadIdx.x & 31) == 0 && in && m > 0u) atomicMax(N_cell + c, m);
+            } else if (in && N > 0u) {
+                atomicMax(N_cell + c, N);
+            }
         }
     }
 }
@@ -2474,6 +2486,7 @@ struct qed_ctx {
     long long tail_rows;        // cascade generations below this size go to the tail pass
     unsigned long long wait_ns; // longest bounded wait of the tail pass
     int step_blocks, step_net_blocks;   // resident blocks of the tail pass's kernel
+    int plan_blocks;                    // resident blocks of the planner (k_plan)
     int samp_blocks;            // resident blocks of the event-driven sampler kernel
     HotItem* d_samp;            // its queue (capacity entries), allocated on first use
     long long samp_cap;
@@ -2800,6 +2813,9 @@ qed_status qed_init(qed_ctx** out, const qed_config* cfg, void* stream) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<0>, kLaneThreads, 0);
         ctx->step_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
         per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plan, kColdThreads, 0);
+        ctx->plan_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
+        per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<1>, kLaneThreads,
                                                       kNetSmemBytes);
         ctx->step_net_blocks = ctx->sms * (per_sm > 0 ? per_sm : 1);
@@ -2906,7 +2922,7 @@ qed_status qed_plan(qed_ctx* ctx, const qed_particles* p, int64_t n, float* chi,
     if (n == 0) return QED_OK;
     const StepParams SP = make_params(ctx->cfg, 0);
     long long blocks = (n + kColdThreads - 1) / kColdThreads;
-    if (blocks > ctx->cold_blocks) blocks = ctx->cold_blocks;
+    if (blocks > ctx->plan_blocks) blocks = ctx->plan_blocks;
     LaunchScope ls(ctx, QED_KERNEL_PLAN);
     k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(to_dev(p), SP, n, chi, N, nullptr, 0ll,
                                                           nullptr, nullptr);
@@ -2924,7 +2940,7 @@ qed_status qed_plan_cells(qed_ctx* ctx, const qed_particles* p, int64_t n, const
     if (n == 0) return QED_OK;
     const StepParams SP = make_params(ctx->cfg, 0);
     long long blocks = (n + kColdThreads - 1) / kColdThreads;
-    if (blocks > ctx->cold_blocks) blocks = ctx->cold_blocks;
+    if (blocks > ctx->plan_blocks) blocks = ctx->plan_blocks;
     LaunchScope ls(ctx, QED_KERNEL_PLAN);
     k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(to_dev(p), SP, n, nullptr, nullptr, cell,
                                                           (long long)ncells,
@@ -2962,7 +2978,7 @@ static qed_status cell_counts(qed_ctx* ctx, const DevParticles& D, StepParams* S
     QED_CUDA(ctx, cudaMemsetAsync(ctx->d_Ncell, 0, sizeof(unsigned int) * (size_t)ncells,
                                   ctx->stream));
     long long blocks = (D.capacity + kColdThreads - 1) / kColdThreads;
-    if (blocks > ctx->cold_blocks) blocks = ctx->cold_blocks;
+    if (blocks > ctx->plan_blocks) blocks = ctx->plan_blocks;
     {
         LaunchScope ls(ctx, QED_KERNEL_PLAN);
         k_plan<<<(int)blocks, kColdThreads, 0, ctx->stream>>>(D, *SP, D.capacity, nullptr,
