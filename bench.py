@@ -682,8 +682,9 @@ def run_push(store, dev, args, restore, plain_value):
 
 def run_plan_cells(ctx, store, n, dev, hbm_peak, peak_kind):
     """qed_plan_cells over the 2^24 store, 64 consecutive rows per cell: rows/s
-    and the pass's algorithmic bytes (the row's 45 B and its 4 B cell index
-    read; the counts are atomics on 256K words) against HBM."""
+    and the pass's algorithmic bytes (the fields the planner reads, 37 B: type,
+    momentum, E and B; and the row's 4 B cell index; the counts are atomics on
+    256K words) against HBM."""
     import torch
     ncells = (n + 63) // 64
     cell = (torch.arange(n, device=dev, dtype=torch.int64) // 64).to(torch.int32)
@@ -705,11 +706,11 @@ def run_plan_cells(ctx, store, n, dev, hbm_peak, peak_kind):
         torch.cuda.synchronize()
         total += e0.elapsed_time(e1)
     ms = total / reps
-    gbs = 49.0 * n / (ms / 1e3) / 1e9
+    gbs = 41.0 * n / (ms / 1e3) / 1e9
     return {"rows": n, "cells": ncells, "ms": ms, "rows_per_s": n / (ms / 1e3),
             "max_cell_N": int(N_cell.max().item()),
             "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                    "peak_kind": peak_kind, "bytes_per_row": 49}}
+                    "peak_kind": peak_kind, "bytes_per_row": 41}}
 
 
 def run_sampler(arr, pristine, store, cap, n, dev, args, restore, plain_value):

@@ -254,12 +254,57 @@ __global__ void __launch_bounds__(kSweepThreads) k_generate(uint32_t k0, uint32_
 // ---------------------------------------------------------------------------
 // Planner
 // ---------------------------------------------------------------------------
+// The fields the planner reads from a row.
+struct PlanRow {
+    uint8_t type;
+    float px, py, pz, Ex, Ey, Ez, Bx, By, Bz;
+};
+
+__device__ __forceinline__ PlanRow load_plan_row(const DevParticles& P, long long i) {
+    return PlanRow{P.type[i], P.px[i], P.py[i], P.pz[i], P.Ex[i],
+                   P.Ey[i],   P.Ez[i], P.Bx[i], P.By[i], P.Bz[i]};
+}
+
+// One row of k_plan: its plan, the outputs, and its cell's count.
+__device__ __forceinline__ void plan_row(const StepParams& SP, const SharedTables& sm,
+                                         const PlanRow& r, long long i, uint32_t c,
+                                         float* chi_out, uint32_t* N_out, long long ncells,
+                                         unsigned int* N_cell) {
+    const bool photon = r.type == QED_PHOTON;
+    float chi = 0.0f;
+    uint32_t N = 0;
+    const bool active = r.type <= QED_PHOTON &&
+                        (photon ? (SP.process_mask & QED_PROC_PAIR)
+                                : (SP.process_mask & QED_PROC_EMISSION));
+    float eps;
+    const ftime T0{(float)SP.dt, (float)(SP.dt - (double)(float)SP.dt)};
+    const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, r.px, r.py, r.pz, r.Ex, r.Ey,
+                                  r.Ez, r.Bx, r.By, r.Bz, T0, &chi, &eps);
+    if (active && eps > 0.0f) N = pl.N;
+    if (chi_out) chi_out[i] = chi;
+    if (N_out) N_out[i] = N;
+    if (N_cell) {
+        const bool in = (long long)c < ncells;
+        const uint32_t key = in ? c : 0xffffffffu;
+        bool one_cell = false;
+        if (__activemask() == 0xffffffffu)
+            one_cell = __all_sync(0xffffffffu, __shfl_sync(0xffffffffu, key, 0) == key);
+        if (one_cell) {
+            const uint32_t m = __reduce_max_sync(0xffffffffu, N);
+            if ((threadIdx.x & 31) == 0 && in && m > 0u) atomicMax(N_cell + c, m);
+        } else if (in && N > 0u) {
+            atomicMax(N_cell + c, N);
+        }
+    }
+}
+
 // cell / N_cell (optional): per-cell planning (Algorithm 1 and 2 fix one
 // sub-step per cell): N_cell[c] becomes the largest N of the rows of cell c
 // (N_cell zeroed by the caller; rows whose cell index is >= ncells are left
 // out of it).  Rows of a cell usually sit together in the store: when the 32
 // rows of a warp share one cell, their largest count goes to it in one
-// atomic.
+// atomic.  Each thread loads its next row (one grid stride on) before it
+// plans the current one, so that twice the loads are in flight.
 __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParams SP, long long n,
                                                        float* chi_out, uint32_t* N_out,
                                                        const uint32_t* __restrict__ cell,
@@ -270,36 +315,22 @@ __global__ void __launch_bounds__(kColdThreads) k_plan(DevParticles P, StepParam
     __syncthreads();
     if (n_dev && *n_dev < n) n = *n_dev;   // rows in use (the store's count)
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint8_t type = P.type[i];
-        const bool photon = type == QED_PHOTON;
-        float chi = 0.0f;
-        uint32_t N = 0;
-        const bool active = type <= QED_PHOTON &&
-                            (photon ? (SP.process_mask & QED_PROC_PAIR)
-                                    : (SP.process_mask & QED_PROC_EMISSION));
-        float eps;
-        const ftime T0{(float)SP.dt, (float)(SP.dt - (double)(float)SP.dt)};
-        const Plan pl = plan_particle(SP, sm.sqz_e, sm.sqz_p, photon, P.px[i], P.py[i], P.pz[i],
-                                      P.Ex[i], P.Ey[i], P.Ez[i], P.Bx[i], P.By[i], P.Bz[i], T0,
-                                      &chi, &eps);
-        if (active && eps > 0.0f) N = pl.N;
-        if (chi_out) chi_out[i] = chi;
-        if (N_out) N_out[i] = N;
-        if (N_cell) {
-            const uint32_t c = cell[i];
-            const bool in = (long long)c < ncells;
-            const uint32_t key = in ? c : 0xffffffffu;
-            bool one_cell = false;
-            if (__activemask() == 0xffffffffu)
-                one_cell = __all_sync(0xffffffffu, __shfl_sync(0xffffffffu, key, 0) == key);
-            if (one_cell) {
-                const uint32_t m = __reduce_max_sync(0xffffffffu, N);
-                if ((threadIdx.x & 31) == 0 && in && m > 0u) atomicMax(N_cell + c, m);
-            } else if (in && N > 0u) {
-                atomicMax(N_cell + c, N);
-            }
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    PlanRow cur = load_plan_row(P, i);
+    uint32_t c_cur = N_cell ? cell[i] : 0u;
+    for (; i < n; i += stride) {
+        // the next row's loads go out before this row is planned
+        const long long nx = i + stride;
+        PlanRow nxt = cur;
+        uint32_t c_nxt = 0u;
+        if (nx < n) {
+            nxt = load_plan_row(P, nx);
+            c_nxt = N_cell ? cell[nx] : 0u;
         }
+        plan_row(SP, sm, cur, i, c_cur, chi_out, N_out, ncells, N_cell);
+        cur = nxt;
+        c_cur = c_nxt;
     }
 }
 

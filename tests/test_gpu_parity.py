@@ -199,6 +199,50 @@ def test_plan_cells_parity():
     ctx.plan_cells(store, n, cd, 0)
 
 
+def test_plan_cells_grouped_rows():
+    """Per-cell counts with the rows of each cell together in the store (a PIC
+    code's cell-sorted particles): there the 32 rows of a warp often share one
+    cell and fold their counts into a single atomic.  Cells of 1 to 4096 rows
+    (power law), a run of removed rows inside a cell, a cell whose indices are
+    out of range, and a row count that is not a multiple of 32.  Every count
+    equals the maximum of qed_plan's counts over the cell's rows, and the
+    oracle's count outside near-ties."""
+    arr, cell = I.cascade_cells(400, 20081051, n_max=4096)
+    n = len(cell)
+    n -= 3 if (n - 3) % 32 else 4
+    arr = {k: np.ascontiguousarray(v[:n]) for k, v in arr.items()}
+    cell = cell[:n].astype(np.uint32)
+    ncells = int(cell.max()) + 1
+    big = int(np.argmax(np.bincount(cell)))
+    rows_big = np.nonzero(cell == big)[0]
+    arr["type"][rows_big[40:100]] = I.TYPE_REMOVED      # removed rows inside a cell
+    other = int(cell[rows_big[-1] + 1]) if rows_big[-1] + 1 < n else int(cell[0])
+    cell = np.where(cell == other, ncells + 7, cell).astype(np.uint32)   # out of range
+    sizes = np.bincount(cell[cell < ncells], minlength=ncells)
+    assert sizes.max() >= 64 and (sizes[sizes > 0] < 32).any()
+    ctx = _ctx(process_mask=3)
+    store = qed.ParticleStore.from_numpy(arr)
+    cd = torch.from_numpy(cell.view(np.int32)).cuda()
+    g = ctx.plan_cells(store, n, cd, ncells).cpu().numpy().view(np.uint32).astype(np.int64)
+    N = torch.empty(n, dtype=torch.int32, device="cuda")
+    ctx.plan(store, n, None, N)
+    Nh = N.cpu().numpy().view(np.uint32).astype(np.int64)
+    want = np.zeros(ncells, dtype=np.int64)
+    inr = cell < ncells
+    np.maximum.at(want, cell[inr].astype(np.int64), Nh[inr])
+    assert np.array_equal(g, want), np.nonzero(g != want)[0][:5]
+    assert g[other] == 0
+    cf = O.make_config(1, process_mask=3)
+    o = O.plan_cells(cf, arr, cell, ncells)
+    _, _, tie = _oracle_plans(cf, arr, np.arange(n))
+    tied = set(cell[tie & inr & (arr["type"] <= 2)].tolist())
+    ok = np.array([c not in tied for c in range(ncells)])
+    print("plan_cells grouped: %d rows, %d cells (largest %d rows), %d exempt" %
+          (n, ncells, sizes.max(), (~ok).sum()))
+    assert (~ok).sum() < 0.02 * ncells
+    assert np.array_equal(g[ok], o[ok]), np.nonzero((g != o) & ok)[0][:5]
+
+
 # --------------------------------------------------------------------------
 # Event step (Algorithms 1 and 2)
 # --------------------------------------------------------------------------
