@@ -387,6 +387,7 @@ def run_gb300(args):
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "particles_per_s": world * n * args.steps / (t_max / 1e3),
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD if n == N_PARTICLES else WORKLOAD + " (reduced: %d rows)" % n,
                    "particles": n, "capacity": cap,
